@@ -1,0 +1,645 @@
+"""Pins for the FP64 oracle: what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (Eqs. Md2q9, meqd2q9, meqd2q9-HL, Md2q9-1..3, meqd2q9-1, 5-9,
+5-10, 5-8-1), exact textbook special cases (standard D2Q9/D3Q19/D3Q27 weights,
+BGK and Lallemand-Luo MRT steps), invariants (Eqs. 3-3-1..3-3-11, 3-5, 3-9,
+4-18-1) and closed-form flow solutions (Taylor-Green, shear and sound waves,
+Poiseuille, advected Gaussian hill, Cole-Hopf Burgers).
+"""
+import numpy as np
+import pytest
+
+import oracle.rmrt as R
+import workloads as W
+
+RNG = np.random.default_rng(1234)
+
+
+def rand_lattice(name, rng):
+    d = 2 if name == "D2Q9" else 3
+    dx = rng.uniform(0.5, 1.5, size=3)
+    c = dx[:d]
+    cs2 = float(np.min(c * c)) / 3.0 * rng.uniform(0.6, 1.0)
+    return R.make_lattice(name, tuple(dx), 1.0, cs2)
+
+
+# ---------------------------------------------------------------- lattices
+@pytest.mark.parametrize("name,expect", [
+    ("D2Q9", {0: 4 / 9, 1: 1 / 9, 2: 1 / 36}),
+    ("D3Q19", {0: 1 / 3, 1: 1 / 18, 2: 1 / 36}),
+    ("D3Q27", {0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}),
+])
+def test_standard_weights(name, expect):
+    """On the standard lattice with c_s^2 = c^2/3 the weights are the classic
+    ones (Sec. V: the popular models are the special case)."""
+    lat = R.make_lattice(name, (1.0, 1.0, 1.0), 1.0, 1.0 / 3.0)
+    speed2 = (lat.e ** 2).sum(axis=1)
+    for s2, w in expect.items():
+        np.testing.assert_allclose(lat.w[speed2 == s2], w, rtol=0, atol=5e-15)
+
+
+@pytest.mark.parametrize("name", R.LATTICES)
+def test_velocity_set_structure(name):
+    e = R.velocity_indices(name)
+    q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}[name]
+    assert e.shape[0] == q
+    assert len({tuple(v) for v in e}) == q                       # distinct
+    assert {tuple(-v) for v in e} == {tuple(v) for v in e}        # symmetric
+    if name == "D3Q19":
+        assert (e == 0).any(axis=1).all()                         # no corners
+    if name != "D2Q9":
+        assert (e[:19] == R.velocity_indices("D3Q19")).all()
+
+
+@pytest.mark.parametrize("name", R.LATTICES)
+def test_velocity_moments(name):
+    """Eqs. (3-3-1), (3-3-2), (3-3-11): Delta0 = 1, odd moments 0,
+    Delta2 = c_s^2 I, Delta4_aaaa = c_a^2 c_s^2, Delta4_aabb = c_s^4, else 0."""
+    for _ in range(5):
+        lat = rand_lattice(name, RNG)
+        w, cv, cs2, d = lat.w, lat.cv, lat.cs2, lat.d
+        assert (w >= 0).all()
+        assert abs(w.sum() - 1) < 1e-15
+        np.testing.assert_allclose(np.einsum("j,ja->a", w, cv), 0, atol=1e-15)
+        D2 = np.einsum("j,ja,jb->ab", w, cv, cv)
+        np.testing.assert_allclose(D2, cs2 * np.eye(d), atol=1e-15)
+        np.testing.assert_allclose(np.einsum("j,ja,jb,jc->abc", w, cv, cv, cv), 0, atol=1e-15)
+        D4 = np.einsum("j,ja,jb,jc,jd->abcd", w, cv, cv, cv, cv)
+        for a in range(d):
+            for b in range(d):
+                for c in range(d):
+                    for e in range(d):
+                        idx = sorted([a, b, c, e])
+                        if idx[0] == idx[3]:
+                            want = lat.c[a] ** 2 * cs2
+                        elif idx[0] == idx[1] and idx[2] == idx[3]:
+                            want = cs2 * cs2
+                        else:
+                            want = 0.0
+                        assert abs(D4[a, b, c, e] - want) < 1e-14
+
+
+def test_no_rd3q15_rd3q13():
+    """Eqs. (3-3-9), (3-3-10): dropping the edge (rD3Q15) or axis+corner
+    (rD3Q13) velocities forces c_1 = c_2 = c_3.  On a rectangular lattice the
+    rD3Q27 weight solution therefore keeps the edge and axis weights
+    nonzero for every admissible omega_19."""
+    lat = R.make_lattice("D3Q27", (1.0, 0.8, 0.6))
+    c2 = lat.c ** 2
+    cs2 = lat.cs2
+    for w19 in np.linspace(0, cs2 / (8 * c2.max()), 5):
+        w7 = cs2 ** 2 / (4 * c2[0] * c2[1]) - 2 * w19
+        w11 = cs2 ** 2 / (4 * c2[0] * c2[2]) - 2 * w19
+        w15 = cs2 ** 2 / (4 * c2[1] * c2[2]) - 2 * w19
+        # rD3Q15 needs w7 = w11 = w15 = 0 at once: impossible with unequal c
+        assert not (abs(w7) < 1e-14 and abs(w11) < 1e-14 and abs(w15) < 1e-14)
+
+
+# ---------------------------------------------------------------- REDF
+@pytest.mark.parametrize("name", R.LATTICES)
+def test_redf_moments(name):
+    """Eqs. (3-5), (3-9): the REDF moments up to third order."""
+    lat = rand_lattice(name, RNG)
+    d, n = lat.d, 7
+    A = RNG.uniform(0.5, 1.5, n)
+    B = RNG.normal(size=(n, d))
+    Mt = RNG.normal(size=(n, d, d))
+    Mt = Mt + Mt.transpose(0, 2, 1)
+    g = R.geq(lat, A, B, Mt)
+    cv, cs2 = lat.cv, lat.cs2
+    np.testing.assert_allclose(g.sum(0), A, rtol=1e-13)
+    np.testing.assert_allclose(np.einsum("ja,jn->na", cv, g), B, atol=1e-13)
+    np.testing.assert_allclose(np.einsum("ja,jb,jn->nab", cv, cv, g),
+                               A[:, None, None] * cs2 * np.eye(d) + Mt, atol=1e-13)
+    third = np.einsum("ja,jb,jc,jn->nabc", cv, cv, cv, g)
+    I = np.eye(d)
+    want = cs2 * (np.einsum("ab,nc->nabc", I, B) + np.einsum("ac,nb->nabc", I, B)
+                  + np.einsum("bc,na->nabc", I, B))
+    for a in range(d):   # delta4_aaaa = c_s^2 (c_a^2 - 3 c_s^2), B~ = B / c_s^2
+        want[:, a, a, a] += cs2 * (lat.c[a] ** 2 - 3 * cs2) * B[:, a] / cs2
+    np.testing.assert_allclose(third, want, atol=1e-12)
+
+
+# ---------------------------------------------------------------- rD2Q9 printed forms
+MTILDE_D2Q9 = np.array([
+    [1, 1, 1, 1, 1, 1, 1, 1, 1],
+    [0, 1, 0, -1, 0, 1, -1, -1, 1],
+    [0, 0, 1, 0, -1, 1, 1, -1, -1],
+    [0, 1, 0, 1, 0, 1, 1, 1, 1],
+    [0, 0, 1, 0, 1, 1, 1, 1, 1],
+    [0, 0, 0, 0, 0, 1, -1, 1, -1],
+    [0, 0, 0, 0, 0, 1, -1, -1, 1],
+    [0, 0, 0, 0, 0, 1, 1, -1, -1],
+    [0, 0, 0, 0, 0, 1, 1, 1, 1]], dtype=float)
+
+
+def test_d2q9_M_equals_D_Mtilde():
+    """Eq. (Md2q9): M = D M~ with the printed integer M~ and
+    D = diag(1, c1, c2, c1^2, c2^2, c1c2, c1c2^2, c1^2c2, c1^2c2^2)."""
+    lat = R.make_lattice("D2Q9", (1.3, 0.7))
+    c1, c2 = lat.c
+    D = np.diag([1, c1, c2, c1 ** 2, c2 ** 2, c1 * c2, c1 * c2 ** 2, c1 ** 2 * c2, c1 ** 2 * c2 ** 2])
+    np.testing.assert_allclose(R.moment_matrix(lat), D @ MTILDE_D2Q9, rtol=1e-15)
+
+
+def test_d2q9_meq_printed():
+    """Eqs. (meqd2q9) and (meqd2q9-HL): M f^eq in closed form."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.6))
+    cs2 = lat.cs2
+    rho = np.array([1.02, 0.97])
+    u = np.array([[0.03, -0.02], [-0.05, 0.01]])
+    M = R.moment_matrix(lat)
+    S = np.eye(9)
+    feq, _, _ = R.equilibrium_and_sources(lat, R.Model(R.NSE), S, rho, u)
+    ux, uy = u[:, 0], u[:, 1]
+    want = rho * np.array([np.ones(2), ux, uy, cs2 + ux ** 2, cs2 + uy ** 2, ux * uy,
+                           cs2 * ux, cs2 * uy, cs2 * (ux ** 2 + uy ** 2 + cs2)])
+    np.testing.assert_allclose(M @ feq, want, atol=1e-15)
+    r0 = 1.0
+    feq, _, _ = R.equilibrium_and_sources(lat, R.Model(R.NSE_HELUO, rho0=r0), S, rho, u)
+    want = np.array([rho, r0 * ux, r0 * uy, cs2 * rho + r0 * ux ** 2, cs2 * rho + r0 * uy ** 2,
+                     r0 * ux * uy, cs2 * r0 * ux, cs2 * r0 * uy,
+                     cs2 * (r0 * (ux ** 2 + uy ** 2) + cs2 * rho)])
+    np.testing.assert_allclose(M @ feq, want, atol=1e-15)
+
+
+def test_bhll_relation():
+    """Eqs. (Md2q9-1..3), (meqd2q9-1), (5-9), (5-10): the Bouzidi et al.
+    orthogonal matrix is N_BHLL M_a, and N_BHLL M f^eq is the printed
+    equilibrium with C_1..C_3."""
+    for a in (0.5, 0.8, 1.0, 1.7):
+        lat = R.make_lattice("D2Q9", (1.0, a), 1.0, 0.9 * min(1.0, a * a) / 3.0)
+        r1, r2, r3, r4, r5, r6 = 1 + a * a, 1 - 2 * a * a, -2 + a * a, -1 + a * a, 2 + a * a, -1 - 2 * a * a
+        Mb = np.array([
+            [1, 1, 1, 1, 1, 1, 1, 1, 1],
+            [0, 1, 0, -1, 0, 1, -1, -1, 1],
+            [0, 0, a, 0, -a, a, a, -a, -a],
+            [-2 * r1, r2, r3, r2, r3, r1, r1, r1, r1],
+            [-2 * r4, r5, r6, r5, r6, r4, r4, r4, r4],
+            [0, 0, 0, 0, 0, a, -a, a, -a],
+            [0, -2, 0, 2, 0, 1, -1, -1, 1],
+            [0, 0, -2 * a, 0, 2 * a, a, a, -a, -a],
+            [4, -2, -2, -2, -2, 1, 1, 1, 1]], dtype=float)
+        a2 = a * a
+        N = np.zeros((9, 9))
+        N[0, 0] = N[1, 1] = N[2, 2] = N[5, 5] = 1
+        N[3, [0, 3, 4]] = [-2 * a2 - 2, 3, 3]
+        N[4, [0, 3, 4]] = [-2 * a2 + 2, 3 * a2, -3 / a2]
+        N[6, [1, 6]] = [-2, 3 / a2]
+        N[7, [2, 7]] = [-2, 3]
+        N[8, [0, 3, 4, 8]] = [4, -6, -6 / a2, 9 / a2]
+        M = R.moment_matrix(lat)
+        np.testing.assert_allclose(N @ M, Mb, atol=1e-13)
+        rho = np.array([1.01])
+        u = np.array([[0.04, -0.03]])
+        feq, _, _ = R.equilibrium_and_sources(lat, R.Model(), np.eye(9), rho, u)
+        cs2 = lat.cs2
+        uu, vv = u[0, 0], u[0, 1]
+        C1 = 2 * (3 * cs2 - 2 * a2) / a2
+        C2 = 2 * (3 * cs2 - 2)
+        C3 = (9 * cs2 ** 2 + 9 * cs2 * uu ** 2 + 9 * cs2 * vv ** 2 - 6 * cs2 - 6 * vv ** 2) / a2 \
+            - (6 * uu ** 2 + 6 * cs2 - 4)
+        e_eq = 3 * (uu ** 2 + vv ** 2) + 2 * (3 * cs2 - r1)
+        pxx = r4 * (3 * r1 * cs2 - 2 * a2) / a2 + 3 * (a2 * uu ** 2 - vv ** 2 / a2)
+        want = rho[0] * np.array([1, uu, vv, e_eq, pxx, uu * vv, C1 * uu / 2, C2 * vv / 2, C3])
+        np.testing.assert_allclose((Mb @ feq)[:, 0], want, atol=1e-13)
+        assert abs(C1 - (C2 + 4 * (1 - a2)) / a2) < 1e-13
+
+
+def test_sherman_morrison_block():
+    """Eq. (5-8-1): the numerically inverted S_2^(1) (Eq. 4-27-1) equals
+    A - A abar b^T A / (1 + b^T A abar), A = diag(s_s), abar = a/d."""
+    for name in R.LATTICES:
+        lat = rand_lattice(name, RNG)
+        r = R.rates_from_viscosity(lat, 0.013, 0.07, 1.1)
+        c2 = lat.c ** 2 - lat.cs2
+        a = (1 / r.s_bulk - 1 / r.s_shear) * c2
+        b = 1 / c2
+        A = np.diag(r.s_shear)
+        ab = a / lat.d
+        sm = A - (A @ np.outer(ab, b) @ A) / (1 + b @ A @ ab)
+        np.testing.assert_allclose(R.s2_diag_block(lat, r), sm, rtol=1e-13)
+
+
+def test_viscosity_relations():
+    """Eq. (4-31) inverted: the rates reproduce nu and nu_b."""
+    lat = R.make_lattice("D3Q19", (1.0, 0.8, 0.5))
+    nu, nub = 0.011, 0.05
+    r = R.rates_from_viscosity(lat, nu, nub, 1.1)
+    cs2, c2, d = lat.cs2, lat.c ** 2, lat.d
+    np.testing.assert_allclose((1 / r.s_off[0, 1] - 0.5) * cs2, nu, rtol=1e-14)
+    np.testing.assert_allclose(0.5 * (1 / r.s_shear - 0.5) * (c2 - cs2), nu, rtol=1e-14)
+    np.testing.assert_allclose((1 / d) * (1 / r.s_bulk - 0.5) * (c2 - cs2), nub, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- standard reductions
+def bgk_feq_standard(e, w, rho, u):
+    """Textbook second-order equilibrium with c_s^2 = 1/3 on a unit lattice."""
+    cu = e @ u.T
+    usq = (u * u).sum(axis=1)
+    return w[:, None] * rho[None, :] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * usq[None, :])
+
+
+@pytest.mark.parametrize("name", R.LATTICES)
+@pytest.mark.parametrize("basis", [R.RAW, R.CENTRAL])
+def test_reduces_to_bgk(name, basis):
+    """Standard lattice, c_s^2 = 1/3, every rate s: the collision is the
+    textbook BGK step f* = f - s (f - f^eq) (Sec. V: the popular models are
+    special cases; with S = s I the basis does not matter, Eq. 5-1-2)."""
+    lat = R.make_lattice(name, (1, 1, 1), 1.0, 1.0 / 3.0)
+    s = 1.37
+    r = R.Rates(s, np.full(lat.d, s), np.full(lat.d, s), np.full(lat.d, s),
+                np.full((lat.d, lat.d), s), s)
+    S = R.relaxation_matrix(lat, r)
+    np.testing.assert_allclose(S, s * np.eye(lat.q), atol=1e-14)
+    f = W.random_populations(lat.q, (40,), seed=3)
+    rho = f.sum(0)
+    u = (lat.cv.T @ f / rho).T
+    want = f - s * (f - bgk_feq_standard(lat.e.astype(float), lat.w, rho, u))
+    got = R.collide(lat, R.Model(R.NSE, basis=basis), S, f)
+    np.testing.assert_allclose(got, want, atol=2e-15)
+
+
+def test_reduces_to_lallemand_luo_mrt():
+    """Standard D2Q9 with c_s^2 = 1/3: with S = N^-1 Sbar N (Eq. 5-1-2), N
+    taking raw moments to the Lallemand-Luo orthogonal moments, one oracle
+    collision equals the textbook Lallemand-Luo MRT collision."""
+    lat = R.make_lattice("D2Q9", (1, 1), 1.0, 1.0 / 3.0)
+    MLL = np.array([
+        [1, 1, 1, 1, 1, 1, 1, 1, 1],
+        [-4, -1, -1, -1, -1, 2, 2, 2, 2],
+        [4, -2, -2, -2, -2, 1, 1, 1, 1],
+        [0, 1, 0, -1, 0, 1, -1, -1, 1],
+        [0, -2, 0, 2, 0, 1, -1, -1, 1],
+        [0, 0, 1, 0, -1, 1, 1, -1, -1],
+        [0, 0, -2, 0, 2, 1, 1, -1, -1],
+        [0, 1, -1, 1, -1, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 1, -1, 1, -1]], dtype=float)
+    s_e, s_eps, s_q, s_nu = 1.2, 1.4, 1.15, 1.8
+    Sbar = np.diag([0.9, s_e, s_eps, 0.9, s_q, 0.9, s_q, s_nu, s_nu])
+    f = W.random_populations(9, (50,), seed=5)
+    rho = f.sum(0)
+    jx, jy = MLL[3] @ f, MLL[5] @ f
+    u2 = (jx ** 2 + jy ** 2) / rho ** 2
+    meq = np.array([rho, -2 * rho + 3 * rho * u2, rho - 3 * rho * u2, jx, -jx, jy, -jy,
+                    (jx ** 2 - jy ** 2) / rho, jx * jy / rho])
+    want = f - np.linalg.solve(MLL, Sbar @ (MLL @ f - meq))
+    N = MLL @ np.linalg.inv(R.moment_matrix(lat))
+    S = np.linalg.solve(N, Sbar @ N)
+    got = R.collide(lat, R.Model(), S, f)
+    np.testing.assert_allclose(got, want, atol=2e-15)
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("name", R.LATTICES)
+@pytest.mark.parametrize("basis", [R.RAW, R.CENTRAL])
+def test_collision_invariants(name, basis):
+    """Eq. (4-18-1): mass and momentum are collision invariants; with
+    forcing the increments are exactly dt Sbar and dt Fbar (Eq. 2-4-2)."""
+    lat = rand_lattice(name, RNG)
+    r = R.rates_from_viscosity(lat, 0.02, 0.05, 1.1)
+    S = R.relaxation_matrix(lat, r)
+    f = W.random_populations(lat.q, (30,), seed=7)
+    for force, src in [((0, 0, 0), 0.0), ((1e-4, -2e-4, 3e-4), 2e-5)]:
+        m = R.Model(R.NSE, basis=basis, force=force, source=src)
+        fs = R.collide(lat, m, S, f)
+        np.testing.assert_allclose(fs.sum(0), f.sum(0) + src, rtol=0, atol=5e-15)
+        np.testing.assert_allclose(lat.cv.T @ fs, lat.cv.T @ f + np.array(force[:lat.d])[:, None],
+                                   rtol=0, atol=5e-15)
+    for kind in (R.NCDE_LINEAR, R.NCDE_QUAD):
+        m = R.Model(kind, basis=basis, adv=(0.05, 0.02, -0.01), source=3e-5)
+        S1 = R.relaxation_matrix(lat, R.Rates(1.0, np.full(lat.d, 1.6), np.full(lat.d, 1.1),
+                                              np.full(lat.d, 1.1), np.full((lat.d, lat.d), 1.1), 1.1))
+        fs = R.collide(lat, m, S1, f)
+        np.testing.assert_allclose(fs.sum(0), f.sum(0) + 3e-5, rtol=0, atol=5e-15)
+
+
+def test_s0_s1_irrelevant_for_nse():
+    """The unforced NSE result does not depend on s_0 and S_1 (their moments
+    are conserved, Eq. 4-18-1)."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.6))
+    f = W.random_populations(9, (20,), seed=9)
+    outs = []
+    for s01 in (0.7, 1.3, 1.9):
+        r = R.rates_from_viscosity(lat, 0.02, 0.04, 1.1, s0=s01, s1=s01)
+        outs.append(R.collide(lat, R.Model(), R.relaxation_matrix(lat, r), f))
+    np.testing.assert_allclose(outs[0], outs[1], atol=1e-16)
+    np.testing.assert_allclose(outs[0], outs[2], atol=1e-16)
+
+
+@pytest.mark.parametrize("name", R.LATTICES)
+def test_central_basis_structure(name):
+    """Eqs. (5-1-1), (5-1-2): Mbar(u) = N(u) M with N unit lower-triangular
+    in moment order, so S = N^-1 Sbar N is block-lower-triangular with the
+    diagonal blocks of Sbar.  The central moments of f^eq have zero first
+    order and c_s^2 rho I second order for any u."""
+    lat = rand_lattice(name, RNG)
+    u = np.array([[0.04, -0.03, 0.02][: lat.d]])
+    M = R.moment_matrix(lat)
+    N = R.central_moment_matrices(lat, u)[0] @ np.linalg.inv(M)
+    order = R.moment_order(lat.name)
+    for k in range(lat.q):
+        for l in range(lat.q):
+            if order[l] > order[k] or (order[l] == order[k] and l != k):
+                assert abs(N[k, l]) < 1e-12
+        assert abs(N[k, k] - 1) < 1e-12
+    r = R.rates_from_viscosity(lat, 0.02, 0.04, 1.1)
+    Sbar = R.relaxation_matrix(lat, r)
+    S = np.linalg.solve(N, Sbar @ N)
+    for k in range(lat.q):
+        for l in range(lat.q):
+            if order[l] > order[k]:
+                assert abs(S[k, l]) < 1e-12
+            if order[l] == order[k]:
+                assert abs(S[k, l] - Sbar[k, l]) < 1e-12
+    rho = np.array([1.03])
+    feq, _, _ = R.equilibrium_and_sources(lat, R.Model(), Sbar, rho, u)
+    cc = lat.cv - u[0][None, :]
+    np.testing.assert_allclose(cc.T @ feq[:, 0], 0, atol=1e-15)
+    np.testing.assert_allclose(np.einsum("ja,jb,j->ab", cc, cc, feq[:, 0]),
+                               lat.cs2 * rho[0] * np.eye(lat.d), atol=1e-15)
+
+
+def test_central_equals_raw_at_rest_and_unit_rates():
+    """At u = 0, N = I so central and raw coincide; with every rate 1 both
+    give f^eq."""
+    lat = R.make_lattice("D3Q27", (1.0, 0.9, 0.6))
+    f = W.random_populations(lat.q, (12,), seed=11)
+    # remove the momentum so that u = 0 at every node
+    rho = f.sum(0)
+    u = (lat.cv.T @ f) / rho
+    f0 = f - R.geq(lat, np.zeros(12), (rho * u).T, np.zeros((12, 3, 3)))
+    r = R.rates_from_viscosity(lat, 0.02, 0.04, 1.1)
+    S = R.relaxation_matrix(lat, r)
+    a = R.collide(lat, R.Model(basis=R.RAW), S, f0)
+    b = R.collide(lat, R.Model(basis=R.CENTRAL), S, f0)
+    np.testing.assert_allclose(a, b, atol=1e-15)
+    one = R.relaxation_matrix(lat, R.Rates(1, np.ones(3), np.ones(3), np.ones(3), np.ones((3, 3)), 1))
+    a = R.collide(lat, R.Model(basis=R.RAW), one, f)
+    b = R.collide(lat, R.Model(basis=R.CENTRAL), one, f)
+    rho, u = R.macroscopic(lat, R.Model(), f)
+    feq, _, _ = R.equilibrium_and_sources(lat, R.Model(), one, rho, u)
+    np.testing.assert_allclose(a, feq, atol=1e-15)
+    np.testing.assert_allclose(b, feq, atol=1e-15)
+
+
+def test_streaming_direction():
+    """Eq. (2-2b): a population at x moves to x + c_j dt (one node along e_j)."""
+    for name in R.LATTICES:
+        lat = R.make_lattice(name, (1.0, 0.7, 0.5))
+        shp = (5, 6, 7) if lat.d == 3 else (1, 6, 7)
+        for j in range(lat.q):
+            f = np.zeros((lat.q,) + shp)
+            z, y, x = (2 if lat.d == 3 else 0), 3, 4
+            f[j, z, y, x] = 1.0
+            g = R.stream(lat, f)
+            ez = int(lat.e[j, 2]) if lat.d == 3 else 0
+            assert g[j, (z + ez) % shp[0], (y + lat.e[j, 1]) % shp[1], (x + lat.e[j, 0]) % shp[2]] == 1.0
+            assert g.sum() == 1.0
+
+
+def test_f_form_equivalence():
+    """Eq. (2-1) with the implicit scheme for D_j F_j and Eq. (2-3) in the
+    transformed variable fbar = f - dt F/2 give the same f (Sec. II)."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.6))
+    r = R.rates_from_viscosity(lat, 0.03, 0.05, 1.2)
+    S = R.relaxation_matrix(lat, r)
+    shp = (1, 8, 10)
+    n = int(np.prod(shp))
+    rng = np.random.default_rng(2)
+    force = 1e-4 * rng.normal(size=(2, n))
+    src = 1e-5 * rng.normal(size=n)
+    m = R.Model(R.NSE, force=force, source=src)
+    fbar = W.random_populations(9, shp, seed=4)
+    # F_j does not depend on u (Eq. NSEFeq), so it is known at t + dt
+    Fj = R.geq(lat, src, force.T, -lat.cs2 * src[:, None, None] * np.eye(2)[None])
+    f = fbar + 0.5 * Fj.reshape(fbar.shape)
+    M = R.moment_matrix(lat)
+    Lam = np.linalg.solve(M, S @ M)
+    for _ in range(3):
+        fb_next = R.step(lat, m, S, fbar, 1)
+        # f-form: f(x+c, t+1) = f - Lam f^ne + G + F + (F(x+c) - F(x))/2
+        fl = f.reshape(9, -1)
+        rho = fl.sum(0)
+        u = ((lat.cv.T @ fl) / rho).T
+        feq, G, F = R.equilibrium_and_sources(lat, m, S, rho, u)
+        post = fl - Lam @ (fl - feq) + G + F - 0.5 * F
+        f = R.stream(lat, post.reshape(fbar.shape)) + 0.5 * F.reshape(fbar.shape)
+        fbar = fb_next
+        np.testing.assert_allclose(fbar + 0.5 * Fj.reshape(fbar.shape), f, atol=1e-15)
+
+
+# ---------------------------------------------------------------- flows
+def mode_amp(field, basis):
+    return (field * basis).sum() / (basis * basis).sum()
+
+
+def test_taylor_green_decay_rectangular():
+    """rD2Q9, 64 x 32 with dx = 1, dy = 0.5, c_s^2 = 1/12, nu = 0.01, bulk
+    rate 1.2 on x, free rates 1.1, 2000 steps: the kinetic energy decays as
+    exp(-2 nu k^2 t), k^2 = kx^2 + ky^2 (rate within 1%).  Eq. (4-31)."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.5))
+    nu = 0.01
+    r = R.rates_from_viscosity(lat, nu, R.nu_bulk_from_rate(lat, 1.2), 1.1)
+    S = R.relaxation_matrix(lat, r)
+    m = R.Model()
+    rho, u = W.taylor_green_2d(64, 32, 1.0, 0.5, 0.01, 1.0, lat.cs2)
+    f = R.init_equilibrium(lat, m, S, rho, u)
+    f = R.step(lat, m, S, f, 200)
+    E0 = (R.fields(lat, m, f)[1] ** 2).sum()
+    f = R.step(lat, m, S, f, 1800)
+    E1 = (R.fields(lat, m, f)[1] ** 2).sum()
+    k2 = (2 * np.pi / 64) ** 2 + (2 * np.pi / 16) ** 2
+    rate = -np.log(E1 / E0) / 1800
+    assert abs(rate / (2 * nu * k2) - 1) < 0.01
+
+
+def shear_wave_rate(lat, S, nx, ny, kvec_idx, steps=600):
+    """Decay rate of a divergence-free plane shear wave."""
+    kx = 2 * np.pi * kvec_idx[0] / (nx * lat.dx[0])
+    ky = 2 * np.pi * kvec_idx[1] / (ny * lat.dx[1])
+    X, Y, _ = W.grid((1, ny, nx), lat.dx)
+    kk = np.hypot(kx, ky)
+    ph = kx * X + ky * Y
+    amp = 1e-3
+    u = np.stack([-ky / kk * amp * np.sin(ph), kx / kk * amp * np.sin(ph)])
+    m = R.Model()
+    f = R.init_equilibrium(lat, m, S, np.ones((1, ny, nx)), u)
+    basis = np.sin(ph)
+    pol = (-ky / kk, kx / kk)
+
+    def amp_of(f):
+        uu = R.fields(lat, m, f)[1]
+        return mode_amp(pol[0] * uu[0] + pol[1] * uu[1], basis)
+    f = R.step(lat, m, S, f, 100)
+    a0 = amp_of(f)
+    f = R.step(lat, m, S, f, steps)
+    a1 = amp_of(f)
+    return -np.log(a1 / a0) / steps / (kk * kk)
+
+
+def test_shear_wave_isotropy():
+    """On a rectangular lattice (dx = 1, dy = 0.6) shear waves along x, along
+    y and along the physical diagonal decay with the same nu (Eqs. 4-27,
+    4-31); the diagonal one involves the dense S_2 block."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.6))
+    nu = 0.02
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, 0.03, 1.1))
+    for nx, ny, kk in [(32, 2, (1, 0)), (2, 48, (0, 1)), (30, 50, (1, 1))]:
+        assert abs(shear_wave_rate(lat, S, nx, ny, kk) / nu - 1) < 0.01
+
+
+def test_shear_wave_detects_single_rate_s2():
+    """Planted mistake: relaxing the normal stresses at the off-diagonal rate
+    (a single viscous rate, Remark II of Sec. IV) makes the diagonal shear
+    wave decay at the wrong rate, so the isotropy pin does see the S_2
+    block."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.6))
+    nu = 0.02
+    r = R.rates_from_viscosity(lat, nu, 0.03, 1.1)
+    r.s_shear = np.full(2, r.s_off[0, 1])
+    r.s_bulk = np.full(2, r.s_off[0, 1])
+    S = R.relaxation_matrix(lat, r)
+    assert abs(shear_wave_rate(lat, S, 30, 50, (1, 1)) / nu - 1) > 0.05
+
+
+def test_sound_wave_speed_and_bulk_attenuation():
+    """A plane sound wave along x propagates at c_s and its energy decays at
+    k^2 [2 nu (1 - 1/d) + nu_b] (Eqs. 4-24-3, 4-31b; linear acoustics)."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.6))
+    nu, nub = 0.01, 0.04
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, nub, 1.1))
+    nx, ny = 64, 2
+    k = 2 * np.pi / (nx * lat.dx[0])
+    X, _, _ = W.grid((1, ny, nx), lat.dx)
+    amp = 1e-4
+    u = np.stack([amp * np.sin(k * X), np.zeros_like(X)])
+    m = R.Model()
+    f = R.init_equilibrium(lat, m, S, np.ones((1, ny, nx)), u)
+    cs = np.sqrt(lat.cs2)
+    period = 2 * np.pi / (cs * k)
+    nsteps = int(round(4 * period))
+    E, A = [], []
+    for t in range(nsteps + 1):
+        rho, uu = R.fields(lat, m, f)
+        a = mode_amp(uu[0], np.sin(k * X))
+        b = mode_amp(rho - 1, np.cos(k * X))
+        E.append(a * a + lat.cs2 * b * b)
+        A.append(a)
+        f = R.step(lat, m, S, f, 1)
+    t = np.arange(nsteps + 1)
+    slope = np.polyfit(t, np.log(E), 1)[0]
+    nuL = 2 * nu * (1 - 1 / 2) + nub
+    assert abs(-slope / (nuL * k * k) - 1) < 0.03
+    A = np.array(A)
+    zc = np.where(np.diff(np.sign(A)) != 0)[0]
+    half = np.mean(np.diff(zc))
+    assert abs(2 * half / period - 1) < 0.02
+
+
+def test_poiseuille_profile():
+    """Force-driven channel between resting walls (y axis, half-way
+    bounce-back): the steady profile is u = F/(2 rho nu) (y+dy/2)(H-y-dy/2)
+    to within 1% on the rectangular lattice (forcing per Eq. 2-3)."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.5))
+    nu = 0.05
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, 0.05, 1.1))
+    ny, nx = 24, 2
+    H = ny * lat.dx[1]
+    F = 1e-6
+    m = R.Model(force=(F, 0.0))
+    f = R.init_equilibrium(lat, m, S, np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx)))
+    f = R.step(lat, m, S, f, 4000, walls=(1,))
+    ux = R.fields(lat, m, f)[1][0][0, :, 0]
+    y = (np.arange(ny) + 0.5) * lat.dx[1]
+    want = F / (2 * nu) * y * (H - y)
+    assert np.max(np.abs(ux - want)) / want.max() < 0.01
+
+
+def hill_error(n_scale, kind=R.NCDE_LINEAR):
+    """Relative L2 error of the advected-diffusing Gaussian hill at t = T."""
+    nx, ny = 32 * n_scale, 40 * n_scale
+    L = (32.0, 24.0)
+    dx = (L[0] / nx, L[1] / ny)
+    dt = 1.0 / (n_scale * n_scale)
+    lat = R.make_lattice("D2Q9", dx, dt)
+    D = 0.05
+    tau = D / (lat.cs2 * dt) + 0.5
+    s1 = 1 / tau
+    rr = R.Rates(1.0, np.full(2, s1), np.full(2, 1.1), np.full(2, 1.1), np.full((2, 2), 1.1), 1.1)
+    S = R.relaxation_matrix(lat, rr)
+    adv = (0.05, 0.02)
+    m = R.Model(kind, adv=adv)
+    sig = 3.0
+    phi0 = W.gaussian_hill((1, ny, nx), dx, sig, peak=1.0, adv=adv, diff=D, t=0.0)
+    f = R.init_equilibrium(lat, m, S, phi0, np.zeros((2, 1, ny, nx)))
+    T = 40.0
+    f = R.step(lat, m, S, f, int(round(T / dt)))
+    phi = R.fields(lat, m, f)[0]
+    ref = W.gaussian_hill((1, ny, nx), dx, sig, peak=1.0, adv=adv, diff=D, t=T)
+    return np.sqrt(((phi - ref) ** 2).sum() / (ref ** 2).sum())
+
+
+def test_gaussian_hill_second_order():
+    """Linear NCDE (B = u phi, D = phi I, Eqs. 4-10, 4-14): the advected,
+    diffusing Gaussian hill matches its closed form, and the error falls
+    at second order under diffusive refinement (dx/2, dt/4)."""
+    e1, e2 = hill_error(1), hill_error(2)
+    assert e1 < 1e-2
+    assert np.log2(e1 / e2) > 1.8
+
+
+def burgers_error(n_scale):
+    nx, ny = 48 * n_scale, 2
+    dx = (1.0 / n_scale, 0.6)
+    dt = 1.0 / (n_scale * n_scale)
+    lat = R.make_lattice("D2Q9", dx, dt, cs2=0.1 * n_scale * n_scale)
+    D = 0.08
+    tau = D / (lat.cs2 * dt) + 0.5
+    rr = R.Rates(1.0, np.full(2, 1 / tau), np.full(2, 1.1), np.full(2, 1.1), np.full((2, 2), 1.1), 1.1)
+    S = R.relaxation_matrix(lat, rr)
+    U = 0.2
+    m = R.Model(R.NCDE_QUAD, adv=(U, 0.0))
+    phi0 = W.burgers_cole_hopf(nx, dx[0], U, D, 0.0)
+    phi0 = np.broadcast_to(phi0[None, None, :], (1, ny, nx)).copy()
+    f = R.init_equilibrium(lat, m, S, phi0, np.zeros((2, 1, ny, nx)))
+    T = 150.0
+    f = R.step(lat, m, S, f, int(round(T / dt)))
+    phi = R.fields(lat, m, f)[0][0, 0]
+    ref = W.burgers_cole_hopf(nx, dx[0], U, D, T)
+    return np.sqrt(((phi - ref) ** 2).sum() / (ref ** 2).sum())
+
+
+def test_burgers_cole_hopf_second_order():
+    """Quadratic NCDE (B = u phi^2/2, C = u u phi^3/3, D = phi I) along x is
+    viscous Burgers for w = U phi; the oracle follows the exact Cole-Hopf
+    solution and converges at second order."""
+    e1, e2 = burgers_error(1), burgers_error(2)
+    assert e1 < 2e-2
+    assert np.log2(e1 / e2) > 1.8
+
+
+@pytest.mark.slow
+def test_taylor_green_second_order():
+    """The decayed Taylor-Green field converges at second order under
+    diffusive refinement on the rectangular lattice."""
+    errs = []
+    for s in (1, 2):
+        nx, ny = 16 * s, 16 * s
+        dx = (1.0 / s, 0.5 / s)
+        dt = 1.0 / (s * s)
+        lat = R.make_lattice("D2Q9", dx, dt)
+        nu = 0.02
+        S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, 0.02, 1.1))
+        m = R.Model()
+        u0 = 0.01 / s
+        rho, u = W.taylor_green_2d(nx, ny, dx[0], dx[1], u0, 1.0, lat.cs2)
+        f = R.init_equilibrium(lat, m, S, rho, u)
+        T = 300.0
+        f = R.step(lat, m, S, f, int(round(T / dt)))
+        uu = R.fields(lat, m, f)[1]
+        k2 = (2 * np.pi / 16) ** 2 + (2 * np.pi / 8) ** 2
+        _, ue = W.taylor_green_2d(nx, ny, dx[0], dx[1], u0 * np.exp(-nu * k2 * T), 1.0, lat.cs2)
+        errs.append(np.sqrt(((uu - ue) ** 2).sum() / (ue ** 2).sum()))
+    assert np.log2(errs[0] / errs[1]) > 1.7
