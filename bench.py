@@ -1,0 +1,408 @@
+"""Throughput of the fused RMRT-LB collide-and-stream step on GB300.
+
+Workload (default): rD2Q9 Navier-Stokes on a periodic 4096 x 2048 grid,
+dx = 1, dy = 0.6, c_s^2 = 0.12, four seeded Taylor-Green modes with
+amplitudes in [0.005, 0.02], nu = 0.01, bulk viscosity 0.02, free rates
+1.1, FP32 compute and storage, FP64 check every 100 steps.  One bench step
+is one lattice time step over the whole grid.  The working set (two FP32
+population lattices, 604 MB) is larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  Extra per-lattice lines are measured in the
+same run and reported under "variants".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(lattice="D2Q9", shape=(4096, 2048, 1), spacing=(1.0, 0.6, 1.0), storage="f32", basis="raw",
+                kind="nse", nu=0.01, nu_bulk=0.02, s_free=1.1, rho0=1.0, seed=1)
+VARIANTS = [
+    # (name, lattice, shape, spacing, storage, basis, kind)
+    ("rD2Q9-f16", "D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "f16", "raw", "nse"),
+    ("rD2Q9-bf16", "D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "bf16", "raw", "nse"),
+    ("rD2Q9-ncde-quad-f32", "D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "f32", "raw", "ncde_quad"),
+    ("rD3Q19-raw-f32", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "raw", "nse"),
+    ("rD3Q19-central-f32", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "central", "nse"),
+    ("rD3Q19-raw-f16", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "raw", "nse"),
+    ("rD3Q27-raw-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "raw", "nse"),
+    ("rD3Q27-central-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "central", "nse"),
+    ("rD3Q27-raw-f16", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "raw", "nse"),
+]
+Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
+ESIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+CHECK_EVERY = 100
+FALLBACK_HBM_GBS = 6800.0
+
+
+def kernel_source_hash() -> str:
+    csrc = os.path.join(ROOT, "paper_2206_00366_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d and d[k]:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("workloads", {}).get(name)
+    return ent.get("dram_bytes_per_launch") if ent else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        import shutil
+        import tempfile
+        if shutil.which("nvidia-smi") is None:
+            return self
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_solver(lattice, shape, spacing, storage, basis, kind, check_every):
+    from paper_2206_00366_gb300.rmrtlb import Solver
+    p = dict(rho0=1.0 if kind.startswith("nse") else 0.0, nu=0.01 if lattice == "D2Q9" else 0.005,
+             nu_bulk=0.02 if lattice == "D2Q9" else 0.01, s_free=1.1, diffusivity=0.005,
+             adv=(0.05, 0.02, 0.0), check_every=check_every)
+    return Solver(lattice, shape, spacing, 1.0, p, kind, basis, storage)
+
+
+def initial_fields(lattice, shape, spacing, kind, seed):
+    import workloads as W
+    nx, ny, nz = shape
+    if kind.startswith("ncde"):
+        phi = W.gaussian_hill((nz, ny, nx), spacing[:2], sigma0=40.0, peak=1.0)
+        return phi, np.zeros((2, nz, ny, nx))
+    if lattice == "D2Q9":
+        cs2 = min(spacing[0], spacing[1]) ** 2 / 3
+        return W.taylor_green_2d_modes(nx, ny, spacing[0], spacing[1], 1.0, cs2, seed=seed)
+    return W.taylor_green_3d(nx, ny, nz, spacing[0], spacing[1], spacing[2], 0.02, 1.0)
+
+
+def time_solver(solver, steps, warmup):
+    """Device time of `steps` steps (no periodic check) with CUDA events on the
+    solver's stream: (total ms, mean per-step ms)."""
+    import torch
+    stream = solver.stream
+    for _ in range(warmup):
+        solver.step(1)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for i in range(steps):
+        solver.step(1)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    durs = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[steps]), statistics.mean(durs)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2206_00366_gb300 import build as _build
+    if rank == 0 or local == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+
+    wl = WORKLOAD
+    nx, ny, nz = wl["shape"]
+    nodes = nx * ny * nz
+    rho, u = initial_fields(wl["lattice"], wl["shape"], wl["spacing"], wl["kind"], wl["seed"])
+    solver = make_solver(wl["lattice"], wl["shape"], wl["spacing"], wl["storage"], wl["basis"], wl["kind"],
+                         CHECK_EVERY)
+    solver.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        solver.step(1)
+    torch.cuda.synchronize()
+    # timed region: barrier + synchronize on both sides, events on the solver's stream
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = solver.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for i in range(args.steps):
+            solver.step(1)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    durs = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    plain = [d for i, d in enumerate(durs) if (args.warmup + i + 1) % CHECK_EVERY != 0]
+    kern_ms = statistics.mean(plain) if plain else total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    chk = solver.last_check()
+    ms_per_step = total_ms / args.steps
+    mlups = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with pinned host buffers
+    rho_h = torch.from_numpy(rho).pin_memory()
+    u_h = torch.from_numpy(u).pin_memory()
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    e2e_solver = make_solver(wl["lattice"], wl["shape"], wl["spacing"], wl["storage"], wl["basis"], wl["kind"],
+                             CHECK_EVERY)
+    e2e_solver.init_equilibrium(rho_h, u_h)
+    e2e_solver.step(3)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_solver.init_equilibrium(rho_h, u_h)           # host -> device inside the call
+    e2e_solver.step(args.steps)
+    e2e_solver.moments(rho_o, u_o)                     # device -> host inside the call
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    d = 2 if wl["lattice"] == "D2Q9" else 3
+    e2e = {"value": world * nodes * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": (1 + d) * nodes * 8 / args.steps,
+           "d2h_bytes_per_step": (1 + d) * nodes * 8 / args.steps,
+           "note": "init_equilibrium from pinned host rho,u + K steps + moments to pinned host"}
+    del e2e_solver
+
+    q = Q[wl["lattice"]]
+    bytes_per_launch = 2 * q * ESIZE[wl["storage"]] * nodes
+    peak, peak_kind = hbm_peak()
+    achieved = bytes_per_launch / (kern_ms * 1e-3) / 1e9
+    traffic = profiled_traffic("rD2Q9-f32")
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "step_kernel<D2Q9, f32, raw>", "algorithmic_bytes_per_launch": bytes_per_launch,
+                "kernel_ms": round(kern_ms, 5)}
+
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        del solver
+        torch.cuda.empty_cache()
+        for name, lat, shape, sp, st, basis, kind in VARIANTS:
+            try:
+                s = make_solver(lat, shape, sp, st, basis, kind, 0)
+                r_, u_ = initial_fields(lat, shape, sp, kind, 1)
+                s.init_equilibrium(torch.from_numpy(r_).cuda(), torch.from_numpy(u_).cuda())
+                nsteps = max(20, min(200, args.steps))
+                tot, km = time_solver(s, nsteps, 5)
+                n = shape[0] * shape[1] * shape[2]
+                b = 2 * Q[lat] * ESIZE[st] * n
+                ach = b / (km * 1e-3) / 1e9
+                variants[name] = {"mlups": round(n * nsteps / (tot * 1e-3) / 1e6, 1),
+                                  "kernel_ms": round(km, 5), "achieved_gbs": round(ach, 1),
+                                  "frac_hbm": round(ach / peak, 4), "bytes_per_node": 2 * Q[lat] * ESIZE[st],
+                                  "traffic": profiled_traffic(name)}
+                del s
+                torch.cuda.empty_cache()
+            except Exception as ex:  # report, do not hide
+                variants[name] = {"error": str(ex)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(budget_s=20.0)
+
+    if rank == 0:
+        launches = args.steps + 2 * (sum(1 for i in range(args.steps) if (args.warmup + i + 1) % CHECK_EVERY == 0))
+        line = {
+            "metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "rD2Q9 NSE Taylor-Green modes 4096x2048 dx=1 dy=0.6 FP32 storage",
+                       "lattice": "rD2Q9", "nx": nx, "ny": ny, "storage": "f32", "basis": "raw",
+                       "check_every": CHECK_EVERY,
+                       "l2": "working set 604 MB > L2 (129 MB); no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "cpu_baseline": cpu, "variants": variants,
+            "last_check": {"mass": chk[0], "residual": chk[5], "step": chk[6], "flags": chk[7]},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- oracle timing
+def _oracle_worker(nx, ny, steps):
+    """Runs in a child process with one BLAS thread: oracle steps on an
+    nx x ny band of the workload; prints seconds."""
+    import oracle.rmrt as R
+    import workloads as W
+    lat = R.make_lattice("D2Q9", (1.0, 0.6))
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, 0.01, 0.02, 1.1))
+    m = R.Model()
+    rho, u = W.taylor_green_2d_modes(4096, 2048, 1.0, 0.6, 1.0, lat.cs2, seed=1)
+    f = R.init_equilibrium(lat, m, S, rho[:, :ny, :nx].copy(), u[:, :, :ny, :nx].copy())
+    f = R.step(lat, m, S, f, 1)
+    t0 = time.perf_counter()
+    R.step(lat, m, S, f, steps)
+    print(json.dumps({"seconds": time.perf_counter() - t0}))
+
+
+def _oracle_child(nx, ny, steps):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(nx), str(ny), str(steps)],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+
+
+def cpu_baseline(budget_s=20.0):
+    nx, ny = 1024, 512
+    probe = _oracle_child(nx, ny, 1)
+    steps = max(1, int(budget_s / max(probe, 1e-3)))
+    secs = _oracle_child(nx, ny, steps)
+    return {"value": round(nx * ny * steps / secs / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle steps on a {nx}x{ny} periodic band of the 4096x2048 workload "
+                      f"(FP64 numpy, one BLAS thread), {secs:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores: each bench step is one
+    oracle step on a band of the workload sized so that the K steps take
+    about a minute."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    nx = 512
+    probe = _oracle_child(nx, 256, 1)
+    t_node = probe / (nx * 256)
+    ny = int(max(8, min(256, 60.0 / max(args.steps, 1) / t_node / nx)))
+    secs = _oracle_child(nx, ny, args.steps)     # one untimed warm-up step inside
+    mlups = nx * ny * args.steps / secs / 1e6
+    line = {
+        "metric": "MLUPS", "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "rD2Q9 NSE Taylor-Green modes 4096x2048 dx=1 dy=0.6 FP32 storage",
+                   "lattice": "rD2Q9", "nx": 4096, "ny": 2048},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one FP64 oracle step on a {nx}x{ny} periodic band of the "
+                                   f"4096x2048 workload, one BLAS thread"},
+        "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--oracle-worker":
+        _oracle_worker(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * rmrtlb.h -- C ABI of the GB300 rectangular MRT lattice Boltzmann step.
+ *
+ * The library advances populations of the rectangular multiple-relaxation-
+ * time lattice Boltzmann method (RMRT-LB) of Chai, Yuan & Shi (arXiv
+ * 2206.00366) on rD2Q9, rD3Q19 and rD3Q27 lattices with unequal spacings
+ * dx, dy, dz.  One time step is the forced moment-space collision of
+ * Eq. (2-2-3),
+ *
+ *     fbar(x + c_j dt, t + dt) = M^-1 [ mbar - S (mbar - m^eq)
+ *                                       + dt (m_G + (I - S/2) m_F) ],
+ *
+ * with m = M f the raw moments of Eq. (5-2), the rectangular equilibrium
+ * g^eq(A, B, M) of Eqs. (3-3)/(3-4), the block relaxation matrix S of
+ * Eq. (5-1) whose second-order block comes from the shear and bulk
+ * viscosities (Eqs. 4-27, 4-31, 5-8-1), and periodic propagation (Eq. 2-2b).
+ * The central-moment variant relaxes N(u) m with the same block rates
+ * (Eqs. 5-1-1, 5-1-2).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns RMRTLB_OK (0) or a negative status; no C++
+ *     exception crosses the ABI.  rmrtlb_strerror() names a status.
+ *   - Fields are FP64, structure-of-arrays, x fastest: a scalar field has
+ *     nx*ny*nz values at index (z*ny + y)*nx + x; a vector field stores its
+ *     d components as d consecutive scalar planes; populations store q
+ *     planes in the velocity order given by rmrtlb_lattice_info().  2-D
+ *     lattices take nz = 1.
+ *   - Field and population pointers may be host or device memory; the
+ *     library finds out which (cudaPointerGetAttributes).  Host data is
+ *     staged through the workspace with cudaMemcpyAsync on the handle's
+ *     stream, and the call returns after the host buffer is no longer
+ *     needed (it synchronises the stream for host pointers only).
+ *   - Device work is issued on the CUDA stream given at creation; calls
+ *     with device pointers return without synchronising.
+ *   - The library allocates no device memory: the caller passes one
+ *     device workspace of rmrtlb_workspace_bytes() bytes, which it owns,
+ *     keeps alive until rmrtlb_destroy(), and frees afterwards.
+ *   - Lattice units: c_alpha = dx_alpha / dt is the lattice speed along
+ *     axis alpha; discrete velocities are c_j = e_j * c with
+ *     e_j in {-1, 0, 1}^d.
+ */
+#ifndef RMRTLB_H
+#define RMRTLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define RMRTLB_OK         0
+#define RMRTLB_EINVAL    (-1)  /* bad argument: lattice, size, negative weight,
+                                  c_s^2 >= min c_a^2, rate outside (0, 2) */
+#define RMRTLB_ENOMEM    (-2)  /* workspace smaller than rmrtlb_workspace_bytes */
+#define RMRTLB_ECUDA     (-3)  /* a CUDA runtime call failed */
+#define RMRTLB_EUNSTABLE (-4)  /* NaN/Inf, density <= 0 or |u| >= c_s seen by
+                                  the last check step */
+
+/* --------------------------------------------------------------- choices */
+enum rmrtlb_lattice { RMRTLB_D2Q9 = 0, RMRTLB_D3Q19 = 1, RMRTLB_D3Q27 = 2 };
+
+/* Equilibrium kind (which conservation law the step solves).
+ *  NSE          f^eq = g^eq(rho, rho u, rho u u)              Eq. (NSEfeq)
+ *  NSE_HELUO    f^eq = g^eq(rho, rho0 u, rho0 u u)            Sec. IV Remark IV
+ *  NCDE_LINEAR  f^eq = g^eq(phi, u phi, u u phi)              Eq. (4-14) with
+ *                                                             D = phi I, beta = 1,
+ *                                                             C = int B'B' dphi
+ *  NCDE_QUAD    f^eq = g^eq(phi, u phi^2/2, u u phi^3/3)      same, B = u phi^2/2
+ * For the NCDE kinds u is the constant advection velocity params.adv. */
+enum rmrtlb_eq_kind {
+    RMRTLB_EQ_NSE = 0,
+    RMRTLB_EQ_NSE_HELUO = 1,
+    RMRTLB_EQ_NCDE_LINEAR = 2,
+    RMRTLB_EQ_NCDE_QUAD = 3
+};
+
+/* Moment basis of the relaxation: raw moments (Eq. 5-2) or central moments
+ * about the local velocity (Eq. 5-1-2 with N = N(u)). */
+enum rmrtlb_basis { RMRTLB_BASIS_RAW = 0, RMRTLB_BASIS_CENTRAL = 1 };
+
+/* Population storage.  All kinds store the scaled deviation
+ * (fbar_j - omega_j rho0) / omega_j; F64 computes in FP64, the others in
+ * FP32.  F16 and BF16 round to nearest even on every store. */
+enum rmrtlb_storage {
+    RMRTLB_ST_F64 = 0,
+    RMRTLB_ST_F32 = 1,
+    RMRTLB_ST_F16 = 2,
+    RMRTLB_ST_BF16 = 3
+};
+
+/* ------------------------------------------------------------ parameters */
+typedef struct {
+    double cs2;          /* c_s^2 (Sec. III, c_{s alpha} = c_s); <= 0 selects
+                            min_alpha c_alpha^2 / 3 */
+    double rho0;         /* reference density (NSE) or phi (NCDE) of the stored
+                            deviation; also rho0 of the He-Luo equilibrium */
+    double nu;           /* NSE kinematic viscosity: gives s_{alpha beta} and
+                            s_{s alpha} through Eq. (4-31a) */
+    double nu_bulk;      /* NSE bulk viscosity: gives s_{b alpha}, Eq. (4-31b) */
+    double s_free;       /* rate of every moment not fixed by the model (order
+                            >= 3 for the NSE, order >= 2 for the NCDE) */
+    double s0, s1;       /* NSE rates of orders 0 and 1 (they do not enter the
+                            unforced NSE); <= 0 selects s_free */
+    double s_shear[3];   /* > 0 overrides s_{s alpha} from nu */
+    double s_bulk[3];    /* > 0 overrides s_{b alpha} from nu_bulk */
+    double s_off[3];     /* > 0 overrides s_xy, s_xz, s_yz from nu */
+    double diffusivity;  /* NCDE: K = diffusivity * I through S_1 = I / tau,
+                            tau = diffusivity / (c_s^2 dt) + 1/2 (Eq. 4-10) */
+    double adv[3];       /* NCDE constant advection velocity */
+    double force[3];     /* NSE body force Fbar (uniform), Eq. (NSE) */
+    double source;       /* NSE mass source Sbar or NCDE source S (uniform) */
+    int check_every;     /* rmrtlb_step runs the FP64 check (mass, momentum,
+                            residual, stability flags) every check_every
+                            steps; 0 disables it */
+} rmrtlb_params;
+
+typedef struct rmrtlb_solver* rmrtlb_t;   /* opaque, library-owned */
+
+/* Name of a status code (static string, never NULL). */
+const char* rmrtlb_strerror(int status);
+
+/* Velocity set of a lattice.  Writes q and d; when e is not NULL it
+ * receives q*3 integers e_j = (e_x, e_y, e_z) in {-1,0,1}, in the order
+ * used for population planes: rD2Q9 as Eq. (3-1), rD3Q27 as Eq. (3-2) (the
+ * xz block read as (1,0,1), (-1,0,1), (-1,0,-1), (1,0,-1)), rD3Q19 as the
+ * first 19 of rD3Q27 (Sec. III).  Host only; touches no GPU. */
+int rmrtlb_lattice_info(int lattice, int* q, int* d, int* e);
+
+/* Bytes of device workspace rmrtlb_create needs for this grid and storage:
+ * two population lattices, a staging area for host transfers, the residual
+ * snapshot and the reduction scratch.  Host only. */
+int rmrtlb_workspace_bytes(int lattice, int nx, int ny, int nz, int storage,
+                           size_t* bytes);
+
+/* Derive every constant of the step on the host and bind a solver to the
+ * caller's workspace.  Constants: c_alpha = d_alpha / dt, c_s^2, weights
+ * (Eq. 3-3-5 for rD2Q9; Eq. 3-3-8 for rD3Q27 with omega_19 =
+ * c_s^6 / (8 c1^2 c2^2 c3^2); omega_19 = 0 for rD3Q19), rates from nu and
+ * nu_bulk (Eq. 4-31), the dense S_2 block by Sherman-Morrison (Eq. 5-8-1).
+ * Fails with RMRTLB_EINVAL for a negative weight, c_s^2 >= min c_alpha^2 or
+ * a rate outside (0, 2); RMRTLB_ENOMEM if workspace_bytes is too small.
+ * workspace: device pointer, 256-byte aligned, owned by the caller.
+ * stream: a cudaStream_t (NULL = legacy default stream).  The populations
+ * are left undefined: call rmrtlb_init_equilibrium or
+ * rmrtlb_set_populations next.  Launches nothing. */
+int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz,
+                  double dx, double dy, double dz, double dt,
+                  const rmrtlb_params* params, int eq_kind, int basis,
+                  int storage, void* workspace, size_t workspace_bytes,
+                  void* stream);
+
+/* Release the handle (not the workspace).  NULL is accepted. */
+int rmrtlb_destroy(rmrtlb_t solver);
+
+/* Host copy of the derived constants, for inspection:
+ * out[0] = c_s^2, out[1..3] = c_alpha, out[4..30] = omega_j (q used),
+ * out[31] = s0, out[32..34] = S_1 diagonal, out[35..43] = S_2 diagonal
+ * block (row major, d x d used), out[44..46] = s_xy, s_xz, s_yz,
+ * out[47] = s_free.  n is the capacity of out (>= 48). */
+int rmrtlb_get_constants(rmrtlb_t solver, double* out, int n);
+
+/* fbar = f^eq(rho, u) at every node (Eq. NSEfeq / Eq. 4-14; no
+ * non-equilibrium part).  rho: scalar field (phi for the NCDE);
+ * u: d planes (ignored for the NCDE).  Resets the step counter. */
+int rmrtlb_init_equilibrium(rmrtlb_t solver, const double* rho, const double* u);
+
+/* Set / read the populations fbar_j(x, t) of the current time (after
+ * propagation, before collision), q planes in rmrtlb_lattice_info order.
+ * set rounds to the storage type. */
+int rmrtlb_set_populations(rmrtlb_t solver, const double* f);
+int rmrtlb_get_populations(rmrtlb_t solver, double* f);
+
+/* Advance n time steps (n >= 0), each one fused kernel: pull-propagation
+ * gather (Eq. 2-2b), moments, macroscopic fields (Eq. 2-4-1/2-4-2),
+ * equilibrium and forcing moments, relaxation (Eq. 2-2-3), inverse
+ * transform, store.  Asynchronous on the solver's stream.  When
+ * params.check_every > 0 the FP64 check runs after every multiple of it. */
+int rmrtlb_step(rmrtlb_t solver, int n);
+
+/* Macroscopic fields of the current populations (Eq. 2-4-1 / 2-4-2):
+ * rho (or phi) one plane, u d planes (the advection velocity for the
+ * NCDE).  Either pointer may be NULL. */
+int rmrtlb_moments(rmrtlb_t solver, double* rho, double* u);
+
+/* Run the FP64 check on the current populations now and return, after
+ * synchronising the stream:
+ *   out[0] total mass sum rho (or sum phi)     out[1..3] total momentum
+ *   out[4] kinetic energy sum rho |u|^2 / 2    out[5] residual
+ *          ||u - u_prev||_2 / ||u||_2 against the previous check (-1 if
+ *          there was none)                     out[6] step counter
+ *   out[7] flags: 1 NaN/Inf, 2 density <= 0, 4 |u| >= c_s.
+ * Returns RMRTLB_EUNSTABLE when a flag is set (out is still filled). */
+int rmrtlb_stats(rmrtlb_t solver, double out[8]);
+
+/* Result of the last check that rmrtlb_step ran (same layout as
+ * rmrtlb_stats; out[6] = -1 if none ran yet).  Synchronises the stream. */
+int rmrtlb_last_check(rmrtlb_t solver, double out[8]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RMRTLB_H */

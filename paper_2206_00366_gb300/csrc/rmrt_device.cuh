@@ -1,0 +1,604 @@
+// Device code of the fused RMRT-LB collide-and-stream step.
+//
+// One thread owns one lattice node.  The populations of a node are held as a
+// 3 x 3 (x 3) cube g[ix][iy][iz], ix = e_x + 1, so that the raw-moment
+// transform m = M f of Eq. (5-2) factors into one 3-point transform per
+// axis (the rD2Q9 and rD3Q27 monomial bases are tensor products of
+// {1, c, c^2}).  rD3Q19 uses the same cube with its eight corners held at
+// zero: the eight monomials with every exponent >= 1 vanish on it, and
+// zeroing them before the inverse transform keeps the corners empty.
+//
+// Storage holds the scaled deviation s_j = (fbar_j - omega_j rho0)/omega_j;
+// every moment below is a moment of delta_j = fbar_j - omega_j rho0, so the
+// rest state never enters the arithmetic (m(omega rho0) = m^eq(rho0, 0, 0)).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "rmrt_params.h"
+
+namespace rmrt {
+
+// ------------------------------------------------------------------ lattices
+// Velocity order: rD2Q9 as Eq. (3-1); rD3Q27 as Eq. (3-2) with the xz block
+// read as (1,0,1), (-1,0,1), (-1,0,-1), (1,0,-1); rD3Q19 = first 19.
+template <int LAT> struct Lat;
+template <> struct Lat<LAT_D2Q9> {
+  static constexpr int D = 2, Q = 9, NZ = 1;
+  static constexpr int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  static constexpr int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  static constexpr int EZ[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+};
+struct Dirs27 {
+  static constexpr int EX[27] = {0, 1, 0, 0, -1, 0, 0, 1, -1, -1, 1, 1, -1, -1,
+                                 1, 0, 0, 0, 0, 1, 1, 1, -1, -1, -1, -1, 1};
+  static constexpr int EY[27] = {0, 0, 1, 0, 0, -1, 0, 1, 1, -1, -1, 0, 0, 0,
+                                 0, 1, -1, -1, 1, 1, 1, -1, 1, -1, -1, 1, -1};
+  static constexpr int EZ[27] = {0, 0, 0, 1, 0, 0, -1, 0, 0, 0, 0, 1, 1, -1,
+                                 -1, 1, 1, -1, -1, 1, -1, 1, 1, -1, 1, -1, -1};
+};
+template <> struct Lat<LAT_D3Q27> : Dirs27 {
+  static constexpr int D = 3, Q = 27, NZ = 3;
+};
+template <> struct Lat<LAT_D3Q19> : Dirs27 {
+  static constexpr int D = 3, Q = 19, NZ = 3;
+};
+
+// compile-time loop: f(std::integral_constant<int, i>) for i = 0..N-1
+template <typename F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, Is...>) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// ------------------------------------------------------------------ storage
+template <typename ST, typename CT> __device__ __forceinline__ CT load_st(const ST* p) {
+  return static_cast<CT>(__ldg(p));
+}
+template <> __device__ __forceinline__ float load_st<__half, float>(const __half* p) {
+  return __half2float(__ldg(p));
+}
+template <> __device__ __forceinline__ float load_st<__nv_bfloat16, float>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+template <typename ST, typename CT> __device__ __forceinline__ void store_st(ST* p, CT v) {
+  *p = static_cast<ST>(v);
+}
+template <> __device__ __forceinline__ void store_st<__half, float>(__half* p, float v) {
+  *p = __float2half_rn(v);
+}
+template <> __device__ __forceinline__ void store_st<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
+
+// ------------------------------------------------------------------ node geometry
+// Source node of the pull gather for direction e: x - e with periodic wrap.
+struct Nbr {
+  int xm, x0, xp, ym, y0, yp, zm, z0, zp;
+  __device__ __forceinline__ Nbr(int x, int y, int z, int nx, int ny, int nz) {
+    x0 = x; y0 = y; z0 = z;
+    xm = x == 0 ? nx - 1 : x - 1; xp = x == nx - 1 ? 0 : x + 1;
+    ym = y == 0 ? ny - 1 : y - 1; yp = y == ny - 1 ? 0 : y + 1;
+    zm = z == 0 ? nz - 1 : z - 1; zp = z == nz - 1 ? 0 : z + 1;
+  }
+  // coordinate of x - e along one axis
+  __device__ __forceinline__ static int up(int e, int m, int c, int p) { return e > 0 ? m : (e < 0 ? p : c); }
+  // coordinate of x + e along one axis
+  __device__ __forceinline__ static int dn(int e, int m, int c, int p) { return e > 0 ? p : (e < 0 ? m : c); }
+};
+
+// ------------------------------------------------------------------ 1-D transforms
+// (f_{-1}, f_0, f_{+1}) -> (sum f, c sum e f, c^2 sum e^2 f) in place.
+template <typename CT>
+__device__ __forceinline__ void fwd3(CT& a, CT& b, CT& c, CT cc, CT cc2) {
+  const CT s = a + c, t = c - a;
+  a = b + s; b = cc * t; c = cc2 * s;
+}
+// inverse of fwd3
+template <typename CT>
+__device__ __forceinline__ void inv3(CT& a, CT& b, CT& c, CT ic, CT ic2) {
+  const CT r = c * ic2, t = b * ic, m0 = a;
+  a = CT(0.5) * (r - t); c = CT(0.5) * (r + t); b = m0 - r;
+}
+// raw -> central moments along one axis: kappa_k = sum (c - u)^k f
+template <typename CT>
+__device__ __forceinline__ void shift3(CT& m0, CT& m1, CT& m2, CT u) {
+  m2 = m2 - CT(2) * u * m1 + u * u * m0;
+  m1 = m1 - u * m0;
+}
+template <typename CT>
+__device__ __forceinline__ void unshift3(CT& k0, CT& k1, CT& k2, CT u) {
+  k2 = k2 + CT(2) * u * k1 + u * u * k0;
+  k1 = k1 + u * k0;
+}
+
+template <int LAT, typename CT> struct Cube {
+  static constexpr int NZ = Lat<LAT>::NZ;
+  CT v[3][3][NZ];
+
+  __device__ __forceinline__ void forward(const KParams<CT>& p) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) fwd3(v[0][b][c], v[1][b][c], v[2][b][c], p.c[0], p.c2[0]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) fwd3(v[a][0][c], v[a][1][c], v[a][2][c], p.c[1], p.c2[1]);
+    if constexpr (NZ == 3) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) fwd3(v[a][b][0], v[a][b][1], v[a][b][2], p.c[2], p.c2[2]);
+    }
+  }
+  __device__ __forceinline__ void inverse(const KParams<CT>& p) {
+    if constexpr (NZ == 3) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) inv3(v[a][b][0], v[a][b][1], v[a][b][2], p.ic[2], p.ic2[2]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) inv3(v[a][0][c], v[a][1][c], v[a][2][c], p.ic[1], p.ic2[1]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) inv3(v[0][b][c], v[1][b][c], v[2][b][c], p.ic[0], p.ic2[0]);
+  }
+  __device__ __forceinline__ void shift(const CT u[3], bool back) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c)
+        back ? unshift3(v[0][b][c], v[1][b][c], v[2][b][c], u[0]) : shift3(v[0][b][c], v[1][b][c], v[2][b][c], u[0]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c)
+        back ? unshift3(v[a][0][c], v[a][1][c], v[a][2][c], u[1]) : shift3(v[a][0][c], v[a][1][c], v[a][2][c], u[1]);
+    if constexpr (NZ == 3) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          back ? unshift3(v[a][b][0], v[a][b][1], v[a][b][2], u[2]) : shift3(v[a][b][0], v[a][b][1], v[a][b][2], u[2]);
+    }
+  }
+};
+
+// True for the eight rD3Q27 monomials that vanish on rD3Q19.
+template <int LAT>
+__device__ __forceinline__ constexpr bool absent(int a, int b, int c) {
+  return LAT == LAT_D3Q19 && a > 0 && b > 0 && c > 0;
+}
+
+// Raw moment (a, b, c) of g^eq(A, B, M) (Eqs. 3-3/3-4).  With
+// mu(0) = 1, mu(1) = 0, mu(2) = c_s^2 (the 1-D weight moments):
+//   m = A mu_a mu_b mu_c + sum_al [a_al = 1] B_al prod_{be != al} mu
+//     + sum_al [a_al = 2] M_alal prod_{be != al} mu
+//     + sum_{al < be} [a_al = a_be = 1] M_albe prod_{ga} mu.
+// Exact for the tensor-product weights of rD2Q9 and of rD3Q27 with the
+// omega_19 chosen on the host; rD3Q19 (omega_19 = 0) adds
+// -c_s^4 M_gg / (c_g^2 - c_s^2) to the three (2,2,0)-type moments, g the
+// axis with exponent 0.  M is packed xx, yy, zz, xy, xz, yz.
+template <int LAT, typename CT>
+__device__ __forceinline__ CT meq_moment(int a, int b, int c, CT A, const CT B[3], const CT M[6],
+                                         const KParams<CT>& p) {
+  auto mu = [&](int k) -> CT { return k == 0 ? CT(1) : (k == 1 ? CT(0) : p.cs2); };
+  CT r = A * mu(a) * mu(b) * mu(c);
+  if (a == 1) r += B[0] * mu(b) * mu(c);
+  if (b == 1) r += B[1] * mu(a) * mu(c);
+  if (c == 1) r += B[2] * mu(a) * mu(b);
+  if (a == 2) r += M[0] * mu(b) * mu(c);
+  if (b == 2) r += M[1] * mu(a) * mu(c);
+  if (c == 2) r += M[2] * mu(a) * mu(b);
+  if (a == 1 && b == 1) r += M[3] * mu(c);
+  if (a == 1 && c == 1) r += M[4] * mu(b);
+  if (b == 1 && c == 1) r += M[5] * mu(a);
+  if (LAT == LAT_D3Q19) {
+    if (a == 2 && b == 2 && c == 0) r -= p.q19k[2] * M[2];
+    if (a == 2 && b == 0 && c == 2) r -= p.q19k[1] * M[1];
+    if (a == 0 && b == 2 && c == 2) r -= p.q19k[0] * M[0];
+  }
+  return r;
+}
+
+// Relaxation of one moment class (Eq. 5-1 block structure): returns S x for
+// the entry (a, b, c); the order-2 diagonal entries use the dense block.
+template <int LAT, typename CT>
+__device__ __forceinline__ CT relax(int a, int b, int c, const CT (&X)[3][3][Lat<LAT>::NZ],
+                                    const KParams<CT>& p) {
+  const int o = a + b + c;
+  if (absent<LAT>(a, b, c)) return CT(0);
+  if (o == 0) return p.s0 * X[0][0][0];
+  if (o == 1) return p.s1[a == 1 ? 0 : (b == 1 ? 1 : 2)] * X[a][b][c];
+  if (o == 2 && (a == 2 || b == 2 || c == 2)) {
+    const int r = a == 2 ? 0 : (b == 2 ? 1 : 2);
+    CT s = p.s2[r][0] * X[2][0][0] + p.s2[r][1] * X[0][2][0];
+    if constexpr (Lat<LAT>::NZ == 3) s += p.s2[r][2] * X[0][0][2];
+    return s;
+  }
+  if (o == 2) return p.soff[(a == 1 && b == 1) ? 0 : ((a == 1) ? 1 : 2)] * X[a][b][c];
+  return p.sfree * X[a][b][c];
+}
+
+// Equilibrium arguments (A - rho0, B, M) of the model and the velocity
+// about which central moments are taken.
+template <typename CT>
+struct Macro {
+  CT dA;      // A - rho0 (density or phi deviation)
+  CT B[3];
+  CT M[6];    // xx yy zz xy xz yz
+  CT u[3];    // fluid (NSE) or advection (NCDE) velocity
+  CT rho;     // density or phi
+};
+
+template <int D, typename CT>
+__device__ __forceinline__ Macro<CT> macroscopic(CT m000, const CT j[3], const KParams<CT>& p) {
+  Macro<CT> r;
+  const CT half_dt = CT(0.5) * p.dt;
+  const CT drho = m000 + half_dt * p.source;        // Eqs. (2-4-1)/(2-4-2a)
+  r.dA = drho;
+  r.rho = p.rho0 + drho;
+  if (p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO) {
+    CT jj[3];
+#pragma unroll
+    for (int al = 0; al < 3; ++al) jj[al] = (al < D) ? j[al] + half_dt * p.force[al] : CT(0);
+    const CT den = p.kind == KIND_NSE ? r.rho : p.rho0;   // Eq. (2-4-2b); He-Luo
+    const CT inv = CT(1) / den;
+#pragma unroll
+    for (int al = 0; al < 3; ++al) { r.u[al] = jj[al] * inv; r.B[al] = jj[al]; }
+    r.M[0] = jj[0] * r.u[0]; r.M[1] = jj[1] * r.u[1]; r.M[2] = jj[2] * r.u[2];
+    r.M[3] = jj[0] * r.u[1]; r.M[4] = jj[0] * r.u[2]; r.M[5] = jj[1] * r.u[2];
+  } else {
+    const CT phi = r.rho;
+    const CT fb = p.kind == KIND_NCDE_LINEAR ? phi : CT(0.5) * phi * phi;           // B = u fb
+    const CT fc = p.kind == KIND_NCDE_LINEAR ? phi : phi * phi * phi * CT(1.0 / 3.0); // C = u u fc
+#pragma unroll
+    for (int al = 0; al < 3; ++al) { r.u[al] = p.adv[al]; r.B[al] = p.adv[al] * fb; }
+    r.M[0] = fc * p.adv[0] * p.adv[0]; r.M[1] = fc * p.adv[1] * p.adv[1]; r.M[2] = fc * p.adv[2] * p.adv[2];
+    r.M[3] = fc * p.adv[0] * p.adv[1]; r.M[4] = fc * p.adv[0] * p.adv[2]; r.M[5] = fc * p.adv[1] * p.adv[2];
+  }
+  return r;
+}
+
+// Collision of one node in moment space, Eq. (2-2-3):
+//   m* - m0 = m(delta) + dt (m_G + m_F) - S (m^ne + dt m_F / 2),
+// central variant: S replaced by N(u)^-1 Sbar N(u) (Eq. 5-1-2).
+template <int LAT, typename CT, bool CENTRAL>
+__device__ __forceinline__ void collide(Cube<LAT, CT>& q, const KParams<CT>& p) {
+  constexpr int D = Lat<LAT>::D, NZ = Lat<LAT>::NZ;
+  q.forward(p);
+  const CT j[3] = {q.v[1][0][0], q.v[0][1][0], NZ == 3 ? q.v[0][0][NZ == 3 ? 1 : 0] : CT(0)};
+  const Macro<CT> mc = macroscopic<D>(q.v[0][0][0], j, p);
+
+  // forcing moments: F = g^eq(Sbar, Fbar, -c_s^2 Sbar I) (NSE) or omega S (NCDE);
+  // G = g^eq(0, 0, M_2G) with M_2G = (I - S_2/2)(u F + F u + c_s^2 Sbar I) (NSE),
+  // or g^eq(0, (I - S_1/2) B' S, 0) (NCDE).
+  CT FA = CT(0), FB[3] = {CT(0), CT(0), CT(0)}, FM[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+  CT GB[3] = {CT(0), CT(0), CT(0)}, GM[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+  const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
+  if (p.forced) {
+    FA = p.source;
+    if (nse) {
+#pragma unroll
+      for (int al = 0; al < 3; ++al) FB[al] = p.force[al];
+      FM[0] = FM[1] = FM[2] = -p.cs2 * p.source;
+      CT Y[6];
+      Y[0] = CT(2) * mc.u[0] * p.force[0] + p.cs2 * p.source;
+      Y[1] = CT(2) * mc.u[1] * p.force[1] + p.cs2 * p.source;
+      Y[2] = CT(2) * mc.u[2] * p.force[2] + p.cs2 * p.source;
+      Y[3] = mc.u[0] * p.force[1] + p.force[0] * mc.u[1];
+      Y[4] = mc.u[0] * p.force[2] + p.force[0] * mc.u[2];
+      Y[5] = mc.u[1] * p.force[2] + p.force[1] * mc.u[2];
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        CT s = CT(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += p.s2[r][k] * Y[k];
+        GM[r] = Y[r] - CT(0.5) * s;
+      }
+      GM[3] = (CT(1) - CT(0.5) * p.soff[0]) * Y[3];
+      GM[4] = (CT(1) - CT(0.5) * p.soff[1]) * Y[4];
+      GM[5] = (CT(1) - CT(0.5) * p.soff[2]) * Y[5];
+    } else {
+      const CT bp = p.kind == KIND_NCDE_LINEAR ? CT(1) : mc.rho;   // B' = u bp
+#pragma unroll
+      for (int al = 0; al < 3; ++al) GB[al] = (CT(1) - CT(0.5) * p.s1[al]) * p.adv[al] * bp * p.source;
+    }
+  }
+  const CT zero3[3] = {CT(0), CT(0), CT(0)};
+  const CT zero6[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+  const CT hdt = CT(0.5) * p.dt;
+
+  // X = m^ne + dt m_F / 2 ; keep m(delta) + dt (m_G + m_F) in q
+  CT X[3][3][NZ];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) {
+        if (absent<LAT>(a, b, c)) { X[a][b][c] = CT(0); continue; }
+        const CT meq = meq_moment<LAT>(a, b, c, mc.dA, mc.B, mc.M, p);
+        CT mF = CT(0), mG = CT(0);
+        if (p.forced) {
+          mF = meq_moment<LAT>(a, b, c, FA, FB, FM, p);
+          mG = nse ? meq_moment<LAT>(a, b, c, CT(0), zero3, GM, p)
+                   : meq_moment<LAT>(a, b, c, CT(0), GB, zero6, p);
+        }
+        X[a][b][c] = q.v[a][b][c] - meq + hdt * mF;
+        q.v[a][b][c] += p.dt * (mG + mF);
+      }
+  if constexpr (CENTRAL) {
+    Cube<LAT, CT> k;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) k.v[a][b][c] = X[a][b][c];
+    k.shift(mc.u, false);
+    CT SX[3][3][NZ];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) SX[a][b][c] = relax<LAT>(a, b, c, k.v, p);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) k.v[a][b][c] = SX[a][b][c];
+    k.shift(mc.u, true);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) q.v[a][b][c] -= k.v[a][b][c];
+  } else {
+    CT SX[3][3][NZ];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) SX[a][b][c] = relax<LAT>(a, b, c, X, p);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) q.v[a][b][c] -= SX[a][b][c];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c)
+        if (absent<LAT>(a, b, c)) q.v[a][b][c] = CT(0);
+  q.inverse(p);
+}
+
+template <int LAT>
+__device__ __forceinline__ constexpr int zi(int ez) { return Lat<LAT>::NZ == 3 ? ez + 1 : 0; }
+
+// ------------------------------------------------------------------ kernels
+// One time step: pull gather from fin (post-collision of the previous step,
+// x - e_j), collide, store the post-collision state of node x in fout.
+template <int LAT, typename ST, typename CT, bool CENTRAL>
+__global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, ST* __restrict__ fout,
+                                                   const KParams<CT> p) {
+  using L = Lat<LAT>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.nx) return;
+  const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
+  const size_t N = p.N;
+  Cube<LAT, CT> q;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < L::NZ; ++c) q.v[a][b][c] = CT(0);
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    const int sx = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
+    const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
+    const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
+    const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
+    q.v[ex + 1][ey + 1][zi<LAT>(ez)] = load_st<ST, CT>(fin + j * N + idx) * p.w[j];
+  });
+  collide<LAT, CT, CENTRAL>(q, p);
+  const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    store_st<ST, CT>(fout + j * N + own, q.v[ex + 1][ey + 1][zi<LAT>(ez)] * p.iw[j]);
+  });
+}
+
+// fbar = f^eq(rho, u) at node x, stored where the next pull gather reads it
+// (slot of x - e_j).
+template <int LAT, typename ST, typename CT>
+__global__ void init_eq_kernel(ST* __restrict__ f, const double* __restrict__ rho,
+                               const double* __restrict__ u, const KParams<CT> p) {
+  using L = Lat<LAT>;
+  constexpr int D = L::D, NZ = L::NZ;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.nx) return;
+  const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
+  const size_t N = p.N;
+  const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
+  // equilibrium arguments from the given fields
+  Macro<CT> mc;
+  const CT r = CT(rho[own]);
+  mc.dA = r - p.rho0;
+  mc.rho = r;
+  const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
+  CT uu[3] = {CT(0), CT(0), CT(0)};
+  for (int al = 0; al < D; ++al) uu[al] = nse ? CT(u[al * N + own]) : p.adv[al];
+  const CT den = p.kind == KIND_NSE ? r : p.rho0;
+  CT fb = den, fc = den;
+  if (!nse) {
+    fb = p.kind == KIND_NCDE_LINEAR ? r : CT(0.5) * r * r;
+    fc = p.kind == KIND_NCDE_LINEAR ? r : r * r * r * CT(1.0 / 3.0);
+  }
+  for (int al = 0; al < 3; ++al) mc.B[al] = fb * uu[al];
+  mc.M[0] = fc * uu[0] * uu[0]; mc.M[1] = fc * uu[1] * uu[1]; mc.M[2] = fc * uu[2] * uu[2];
+  mc.M[3] = fc * uu[0] * uu[1]; mc.M[4] = fc * uu[0] * uu[2]; mc.M[5] = fc * uu[1] * uu[2];
+  Cube<LAT, CT> q;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c)
+        q.v[a][b][c] = absent<LAT>(a, b, c) ? CT(0) : meq_moment<LAT>(a, b, c, mc.dA, mc.B, mc.M, p);
+  q.inverse(p);
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    const int dx_ = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
+    const int dy_ = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
+    const int dz_ = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
+    const size_t idx = (size_t(dz_) * p.ny + dy_) * p.nx + dx_;
+    store_st<ST, CT>(f + j * N + idx, q.v[ex + 1][ey + 1][zi<LAT>(ez)] * p.iw[j]);
+  });
+}
+
+// Canonical populations <-> storage (one plane j at a time).
+// to_storage: f[j][x - e_j] = encode(src[x]); from_storage: dst[x] = decode(f[j][x - e_j]).
+template <int LAT, typename ST, typename CT>
+__global__ void plane_kernel(ST* __restrict__ f, double* __restrict__ plane, int j, int to_storage,
+                             const KParams<CT> p) {
+  using L = Lat<LAT>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.nx) return;
+  const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
+  int ex = 0, ey = 0, ez = 0;
+  static_for<L::Q>([&](auto J) {
+    constexpr int jj = decltype(J)::value;
+    constexpr int cx = L::EX[jj], cy = L::EY[jj], cz = L::EZ[jj];
+    if (jj == j) { ex = cx; ey = cy; ez = cz; }
+  });
+  const int sx = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
+  const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
+  const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
+  const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
+  const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
+  ST* fj = f + size_t(j) * p.N;
+  const double w = double(p.w[j]);
+  if (to_storage) {
+    const double dev = (plane[own] - w * double(p.rho0)) / w;
+    store_st<ST, CT>(fj + idx, CT(dev));
+  } else {
+    plane[own] = double(load_st<ST, CT>(fj + idx)) * w + w * double(p.rho0);
+  }
+}
+
+// Macroscopic fields and FP64 check sums of the current populations.
+// sums per block: [0] sum drho, [1..3] momentum, [4] kinetic energy,
+// [5] sum |u - u_prev|^2, [6] sum |u|^2, [7] unused.
+template <int LAT, typename ST, typename CT>
+__global__ void __launch_bounds__(128) check_kernel(const ST* __restrict__ fin, double* __restrict__ rho_out,
+                                                    double* __restrict__ u_out, double* __restrict__ uprev,
+                                                    int use_prev, int write_prev, double* __restrict__ partials,
+                                                    int* __restrict__ flags, const KParams<CT> p) {
+  using L = Lat<LAT>;
+  constexpr int D = L::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  int flag = 0;
+  if (x < p.nx) {
+    const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
+    const size_t N = p.N;
+    double s0 = 0, s1[3] = {0, 0, 0};
+    static_for<L::Q>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+      const int sx = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
+      const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
+      const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
+      const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
+      const double dj = double(load_st<ST, CT>(fin + j * N + idx)) * double(p.w[j]);
+      s0 += dj;
+      if (ex) s1[0] += ex * dj;
+      if (ey) s1[1] += ey * dj;
+      if (ez) s1[2] += ez * dj;
+    });
+    const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
+    const double hdt = 0.5 * double(p.dt);
+    const double drho = s0 + hdt * double(p.source);
+    const double rho = double(p.rho0) + drho;
+    const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
+    double u[3] = {0, 0, 0}, jm[3] = {0, 0, 0};
+    for (int al = 0; al < D; ++al) {
+      jm[al] = s1[al] * double(p.c[al]) + hdt * double(p.force[al]);
+      u[al] = nse ? jm[al] / (p.kind == KIND_NSE ? rho : double(p.rho0)) : double(p.adv[al]);
+    }
+    if (!nse) for (int al = 0; al < D; ++al) jm[al] = rho * u[al];
+    if (rho_out) rho_out[own] = rho;
+    double u2 = 0, du2 = 0;
+    for (int al = 0; al < D; ++al) {
+      if (u_out) u_out[al * N + own] = u[al];
+      u2 += u[al] * u[al];
+      if (uprev) {
+        const double d = u[al] - (use_prev ? uprev[al * N + own] : 0.0);
+        du2 += d * d;
+        if (write_prev) uprev[al * N + own] = u[al];
+      }
+    }
+    acc[0] = drho;
+    acc[1] = jm[0]; acc[2] = jm[1]; acc[3] = jm[2];
+    acc[4] = 0.5 * rho * u2;
+    acc[5] = du2;
+    acc[6] = u2;
+    if (!(drho == drho) || !(u2 == u2) || isinf(drho) || isinf(u2)) flag |= 1;
+    if (rho <= 0.0) flag |= 2;
+    if (nse && u2 >= double(p.cs2)) flag |= 4;
+  }
+  if (partials) {
+    // warp then block reduction in FP64, fixed order (deterministic)
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    __shared__ double sm[4][7];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) sm[warp][k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < 7) {
+      double s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][threadIdx.x];
+      const size_t blk = (size_t(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      partials[blk * 8 + threadIdx.x] = s;
+    }
+  }
+  if (flag) atomicOr(flags, flag);
+}
+
+}  // namespace rmrt

@@ -1,0 +1,61 @@
+// Parameter block passed by value to every kernel of the RMRT-LB step, and
+// the launch interface between the host library and the per-lattice
+// translation units.  Internal header: not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace rmrt {
+
+enum { LAT_D2Q9 = 0, LAT_D3Q19 = 1, LAT_D3Q27 = 2 };
+enum { KIND_NSE = 0, KIND_NSE_HELUO = 1, KIND_NCDE_LINEAR = 2, KIND_NCDE_QUAD = 3 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+// Constants of one solver in the compute type CT (double for FP64 storage,
+// float otherwise).  Derived once on the host in FP64 and rounded.
+template <typename CT>
+struct KParams {
+  int nx, ny, nz;
+  int kind;        // KIND_*
+  int forced;      // nonzero when force or source is nonzero
+  int pad_;
+  size_t N;        // nodes = nx * ny * nz
+  CT rho0, cs2, dt, source;
+  CT c[3], c2[3], ic[3], ic2[3];       // c_a, c_a^2, 1/c_a, 1/c_a^2
+  CT w[27], iw[27];                    // omega_j, 1/omega_j
+  CT s0, s1[3], s2[3][3], soff[3], sfree;
+  CT force[3], adv[3];
+  CT q19k[3];                          // c_s^4 / (c_g^2 - c_s^2), rD3Q19 only
+};
+
+enum Op { OP_STEP = 0, OP_INIT_EQ = 1, OP_PLANE = 2, OP_CHECK = 3 };
+
+struct LaunchArgs {
+  Op op;
+  int storage;     // ST_*
+  int central;     // 1: central-moment relaxation
+  const void* fin;
+  void* fout;
+  const double* rho;       // OP_INIT_EQ
+  const double* u;
+  double* plane;           // OP_PLANE
+  int j, to_storage;
+  double* rho_out;         // OP_CHECK
+  double* u_out;
+  double* uprev;
+  int use_prev, write_prev;
+  double* partials;
+  int* flags;
+  const KParams<double>* kp64;
+  const KParams<float>* kp32;
+  dim3 grid, block;
+  cudaStream_t stream;
+};
+
+cudaError_t launch_d2q9(const LaunchArgs& a);
+cudaError_t launch_d3q19(const LaunchArgs& a);
+cudaError_t launch_d3q27(const LaunchArgs& a);
+cudaError_t launch_finalize(const double* partials, size_t nblk, double* out, cudaStream_t s);
+
+}  // namespace rmrt

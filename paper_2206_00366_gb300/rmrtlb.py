@@ -1,0 +1,274 @@
+"""Thin ctypes binding of the rmrtlb C ABI (include/rmrtlb.h).
+
+The functions below carry the C names and only marshal arguments: every step
+of the collide-and-stream path runs in the CUDA kernels of librmrtlb.so.
+Pointers are plain integers (host or device addresses, e.g.
+``tensor.data_ptr()`` or ``array.ctypes.data``).  A nonzero status raises
+RmrtlbError.  There is no fallback: if the library is missing, loading it
+raises.
+
+``Solver`` is a convenience wrapper that takes its device workspace and its
+stream from PyTorch.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "librmrtlb.so")
+
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
+EQ_NSE, EQ_NSE_HELUO, EQ_NCDE_LINEAR, EQ_NCDE_QUAD = 0, 1, 2, 3
+BASIS_RAW, BASIS_CENTRAL = 0, 1
+ST_F64, ST_F32, ST_F16, ST_BF16 = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE = 0, -1, -2, -3, -4
+
+LATTICE_NAMES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}
+STORAGE_NAMES = {"f64": ST_F64, "f32": ST_F32, "f16": ST_F16, "bf16": ST_BF16}
+EQ_NAMES = {"nse": EQ_NSE, "nse_heluo": EQ_NSE_HELUO, "ncde_linear": EQ_NCDE_LINEAR,
+            "ncde_quad": EQ_NCDE_QUAD}
+BASIS_NAMES = {"raw": BASIS_RAW, "central": BASIS_CENTRAL}
+
+
+class RmrtlbError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {rmrtlb_strerror(status)} ({status})")
+
+
+class rmrtlb_params(ctypes.Structure):
+    _fields_ = [
+        ("cs2", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("nu_bulk", ctypes.c_double),
+        ("s_free", ctypes.c_double),
+        ("s0", ctypes.c_double),
+        ("s1", ctypes.c_double),
+        ("s_shear", ctypes.c_double * 3),
+        ("s_bulk", ctypes.c_double * 3),
+        ("s_off", ctypes.c_double * 3),
+        ("diffusivity", ctypes.c_double),
+        ("adv", ctypes.c_double * 3),
+        ("force", ctypes.c_double * 3),
+        ("source", ctypes.c_double),
+        ("check_every", ctypes.c_int),
+    ]
+
+
+def make_params(**kw) -> rmrtlb_params:
+    """rmrtlb_params from keyword arguments (missing fields are zero)."""
+    p = rmrtlb_params()
+    for k, v in kw.items():
+        if isinstance(getattr(p, k), ctypes.Array):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = float(x)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Load librmrtlb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(paper_2206_00366_gb300.build.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    i, d, sz = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "rmrtlb_strerror": (ctypes.c_char_p, [i]),
+        "rmrtlb_lattice_info": (i, [i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "rmrtlb_workspace_bytes": (i, [i, i, i, i, i, ctypes.POINTER(sz)]),
+        "rmrtlb_create": (i, [ctypes.POINTER(_vp), i, i, i, i, d, d, d, d, ctypes.POINTER(rmrtlb_params),
+                              i, i, i, _vp, sz, _vp]),
+        "rmrtlb_destroy": (i, [_vp]),
+        "rmrtlb_get_constants": (i, [_vp, ctypes.POINTER(d), i]),
+        "rmrtlb_init_equilibrium": (i, [_vp, _vp, _vp]),
+        "rmrtlb_set_populations": (i, [_vp, _vp]),
+        "rmrtlb_get_populations": (i, [_vp, _vp]),
+        "rmrtlb_step": (i, [_vp, i]),
+        "rmrtlb_moments": (i, [_vp, _vp, _vp]),
+        "rmrtlb_stats": (i, [_vp, ctypes.POINTER(d)]),
+        "rmrtlb_last_check": (i, [_vp, ctypes.POINTER(d)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list:
+    return ["rmrtlb_strerror", "rmrtlb_lattice_info", "rmrtlb_workspace_bytes", "rmrtlb_create",
+            "rmrtlb_destroy", "rmrtlb_get_constants", "rmrtlb_init_equilibrium",
+            "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
+            "rmrtlb_stats", "rmrtlb_last_check"]
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise RmrtlbError(status, where)
+
+
+# ------------------------------------------------------------------ C names
+def rmrtlb_strerror(status: int) -> str:
+    return lib().rmrtlb_strerror(status).decode()
+
+
+def rmrtlb_lattice_info(lattice: int):
+    q, d = ctypes.c_int(), ctypes.c_int()
+    e = (ctypes.c_int * 81)()
+    _check(lib().rmrtlb_lattice_info(lattice, ctypes.byref(q), ctypes.byref(d), e), "rmrtlb_lattice_info")
+    return q.value, d.value, np.array(e[: 3 * q.value], dtype=np.int64).reshape(q.value, 3)
+
+
+def rmrtlb_workspace_bytes(lattice: int, nx: int, ny: int, nz: int, storage: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().rmrtlb_workspace_bytes(lattice, nx, ny, nz, storage, ctypes.byref(b)), "rmrtlb_workspace_bytes")
+    return b.value
+
+
+def rmrtlb_create(lattice, nx, ny, nz, dx, dy, dz, dt, params: rmrtlb_params, eq_kind, basis, storage,
+                  workspace: int, workspace_bytes: int, stream: int):
+    h = _vp()
+    _check(lib().rmrtlb_create(ctypes.byref(h), lattice, nx, ny, nz, dx, dy, dz, dt, ctypes.byref(params),
+                               eq_kind, basis, storage, workspace, workspace_bytes, stream), "rmrtlb_create")
+    return h
+
+
+def rmrtlb_destroy(h):
+    _check(lib().rmrtlb_destroy(h), "rmrtlb_destroy")
+
+
+def rmrtlb_get_constants(h) -> np.ndarray:
+    out = (ctypes.c_double * 48)()
+    _check(lib().rmrtlb_get_constants(h, out, 48), "rmrtlb_get_constants")
+    return np.array(out[:])
+
+
+def rmrtlb_init_equilibrium(h, rho: int, u: int):
+    _check(lib().rmrtlb_init_equilibrium(h, rho, u), "rmrtlb_init_equilibrium")
+
+
+def rmrtlb_set_populations(h, f: int):
+    _check(lib().rmrtlb_set_populations(h, f), "rmrtlb_set_populations")
+
+
+def rmrtlb_get_populations(h, f: int):
+    _check(lib().rmrtlb_get_populations(h, f), "rmrtlb_get_populations")
+
+
+def rmrtlb_step(h, n: int):
+    _check(lib().rmrtlb_step(h, n), "rmrtlb_step")
+
+
+def rmrtlb_moments(h, rho: int, u: int):
+    _check(lib().rmrtlb_moments(h, rho, u), "rmrtlb_moments")
+
+
+def rmrtlb_stats(h, allow_unstable: bool = False) -> np.ndarray:
+    out = (ctypes.c_double * 8)()
+    st = lib().rmrtlb_stats(h, out)
+    if not (allow_unstable and st == EUNSTABLE):
+        _check(st, "rmrtlb_stats")
+    return np.array(out[:])
+
+
+def rmrtlb_last_check(h, allow_unstable: bool = False) -> np.ndarray:
+    out = (ctypes.c_double * 8)()
+    st = lib().rmrtlb_last_check(h, out)
+    if not (allow_unstable and st == EUNSTABLE):
+        _check(st, "rmrtlb_last_check")
+    return np.array(out[:])
+
+
+# ------------------------------------------------------------------ convenience
+def _ptr(x) -> int:
+    """Address of a torch tensor or numpy array (must be contiguous float64)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("numpy arrays must be contiguous float64")
+        return x.ctypes.data
+    if not x.is_contiguous() or str(x.dtype) != "torch.float64":
+        raise ValueError("tensors must be contiguous float64")
+    return x.data_ptr()
+
+
+class Solver:
+    """One RMRT-LB solver whose workspace is a torch CUDA tensor.
+
+    lattice, storage, eq_kind, basis: names ("D3Q19", "f32", "nse", "raw") or
+    the integer codes.  shape = (nx, ny, nz); spacing = (dx, dy, dz).
+    params: keyword dict for rmrtlb_params.
+    """
+
+    def __init__(self, lattice, shape, spacing, dt=1.0, params=None, eq_kind="nse", basis="raw",
+                 storage="f32", device="cuda", stream=None):
+        import torch
+        self.lattice = LATTICE_NAMES.get(lattice, lattice)
+        self.storage = STORAGE_NAMES.get(storage, storage)
+        self.eq_kind = EQ_NAMES.get(eq_kind, eq_kind)
+        self.basis = BASIS_NAMES.get(basis, basis)
+        nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+        self.shape = (nx, ny, nz)
+        self.q, self.d, self.e = rmrtlb_lattice_info(self.lattice)
+        self.N = nx * ny * nz
+        nbytes = rmrtlb_workspace_bytes(self.lattice, nx, ny, nz, self.storage)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
+        sp = (tuple(spacing) + (1.0, 1.0))[:3]
+        self.params = make_params(**(params or {}))
+        self.h = rmrtlb_create(self.lattice, nx, ny, nz, float(sp[0]), float(sp[1]), float(sp[2]), float(dt),
+                               self.params, self.eq_kind, self.basis, self.storage,
+                               self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.rmrtlb_destroy(h)
+            self.h = None
+
+    def constants(self):
+        return rmrtlb_get_constants(self.h)
+
+    def init_equilibrium(self, rho, u=None):
+        rmrtlb_init_equilibrium(self.h, _ptr(rho), _ptr(u))
+
+    def set_populations(self, f):
+        rmrtlb_set_populations(self.h, _ptr(f))
+
+    def get_populations(self, out=None):
+        if out is None:
+            out = np.empty((self.q, self.shape[2], self.shape[1], self.shape[0]))
+        rmrtlb_get_populations(self.h, _ptr(out))
+        return out
+
+    def step(self, n=1):
+        rmrtlb_step(self.h, n)
+
+    def moments(self, rho=None, u=None):
+        if rho is None and u is None:
+            rho = np.empty((self.shape[2], self.shape[1], self.shape[0]))
+            u = np.empty((self.d, self.shape[2], self.shape[1], self.shape[0]))
+        rmrtlb_moments(self.h, _ptr(rho), _ptr(u))
+        return rho, u
+
+    def stats(self, allow_unstable=False):
+        return rmrtlb_stats(self.h, allow_unstable)
+
+    def last_check(self, allow_unstable=False):
+        return rmrtlb_last_check(self.h, allow_unstable)

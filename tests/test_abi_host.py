@@ -1,0 +1,124 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every declared symbol, and its host parameter derivation
+(weights of Sec. III, rates of Eq. 4-31, the S_2 block of Eq. 5-8-1, the
+NCDE S_1 of Eq. 4-10) agrees with the oracle.  rmrtlb_create touches no GPU,
+so a placeholder workspace address is enough here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle.rmrt as R
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2206_00366_gb300 import build
+    build.build()
+    from paper_2206_00366_gb300 import rmrtlb
+    return rmrtlb
+
+
+def test_header_symbols_exported(B):
+    hdr = open(os.path.join(ROOT, "include", "rmrtlb.h")).read()
+    declared = set(re.findall(r"^\s*(?:const char\*|int)\s+(rmrtlb_\w+)\s*\(", hdr, re.M))
+    assert declared == set(B.exported_symbols())
+    lib = ctypes.CDLL(B.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_lattice_info_matches_paper_order(B):
+    for name, code in B.LATTICE_NAMES.items():
+        q, d, e = B.rmrtlb_lattice_info(code)
+        eo = R.velocity_indices(name)
+        assert (q, d) == eo.shape
+        assert (e[:, :d] == eo).all()
+        if d == 2:
+            assert (e[:, 2] == 0).all()
+    with pytest.raises(B.RmrtlbError):
+        B.rmrtlb_lattice_info(7)
+
+
+def test_strerror(B):
+    for st in (0, -1, -2, -3, -4, -99):
+        assert isinstance(B.rmrtlb_strerror(st), str) and B.rmrtlb_strerror(st)
+
+
+def test_workspace_bytes(B):
+    n = B.rmrtlb_workspace_bytes(B.D3Q19, 256, 256, 128, B.ST_F32)
+    assert n >= 2 * 19 * 256 * 256 * 128 * 4
+    assert B.rmrtlb_workspace_bytes(B.D3Q19, 256, 256, 128, B.ST_F16) < n
+    for bad in [(B.D2Q9, 0, 4, 1), (B.D2Q9, 4, 4, 2), (B.D3Q27, 4, -1, 4), (5, 4, 4, 4)]:
+        with pytest.raises(B.RmrtlbError):
+            B.rmrtlb_workspace_bytes(*bad, B.ST_F32)
+
+
+def create(B, lat, shape, spacing, kind=0, **kw):
+    p = B.make_params(**kw)
+    nbytes = B.rmrtlb_workspace_bytes(lat, *shape, B.ST_F32)
+    return B.rmrtlb_create(lat, *shape, *spacing, 1.0, p, kind, 0, B.ST_F32, 256, nbytes, 0)
+
+
+@pytest.mark.parametrize("name", R.LATTICES)
+def test_constants_match_oracle(B, name):
+    spacing = (1.0, 0.7, 0.5)
+    shape = (8, 8, 1 if name == "D2Q9" else 8)
+    nu, nub, sf = 0.013, 0.06, 1.15
+    h = create(B, B.LATTICE_NAMES[name], shape, spacing, nu=nu, nu_bulk=nub, s_free=sf, rho0=1.0)
+    c = B.rmrtlb_get_constants(h)
+    B.rmrtlb_destroy(h)
+    lat = R.make_lattice(name, spacing)
+    r = R.rates_from_viscosity(lat, nu, nub, sf)
+    d = lat.d
+    assert abs(c[0] - lat.cs2) < 1e-15
+    np.testing.assert_allclose(c[1:1 + d], lat.c, rtol=1e-15)
+    np.testing.assert_allclose(c[4:4 + lat.q], lat.w, rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(c[35:44].reshape(3, 3)[:d, :d], R.s2_diag_block(lat, r), rtol=1e-12)
+    np.testing.assert_allclose(c[44], r.s_off[0, 1], rtol=1e-14)
+    assert c[47] == sf
+
+
+def test_ncde_constants(B):
+    lat = R.make_lattice("D2Q9", (1.0, 0.6))
+    D = 0.005
+    h = create(B, B.D2Q9, (16, 8, 1), (1.0, 0.6, 1.0), kind=B.EQ_NCDE_QUAD, diffusivity=D, s_free=1.1,
+               adv=(0.05, 0.02, 0.0))
+    c = B.rmrtlb_get_constants(h)
+    B.rmrtlb_destroy(h)
+    tau = D / lat.cs2 + 0.5
+    np.testing.assert_allclose(c[32:34], 1 / tau, rtol=1e-14)
+    # K = dt c_s^2 (1/s_1 - 1/2) recovers D (Eq. 4-10)
+    np.testing.assert_allclose(lat.cs2 * (1 / c[32] - 0.5), D, rtol=1e-13)
+
+
+def test_create_rejects_invalid(B):
+    ok = dict(nu=0.01, nu_bulk=0.05, s_free=1.1, rho0=1.0)
+    with pytest.raises(B.RmrtlbError):      # c_s^2 above min c^2
+        create(B, B.D2Q9, (8, 8, 1), (1.0, 0.5, 1.0), cs2=0.3, **{k: v for k, v in ok.items()})
+    with pytest.raises(B.RmrtlbError):      # negative weight on rD3Q19
+        create(B, B.D3Q19, (8, 8, 8), (1.0, 1.0, 0.5), cs2=0.22, **ok)
+    with pytest.raises(B.RmrtlbError):      # rate outside (0, 2)
+        create(B, B.D2Q9, (8, 8, 1), (1.0, 1.0, 1.0), nu=0.01, nu_bulk=0.05, s_free=2.5, rho0=1.0)
+    with pytest.raises(B.RmrtlbError):      # unaligned workspace
+        p = B.make_params(**ok)
+        B.rmrtlb_create(B.D2Q9, 8, 8, 1, 1.0, 1.0, 1.0, 1.0, p, 0, 0, B.ST_F32, 257, 1 << 30, 0)
+    with pytest.raises(B.RmrtlbError) as ei:   # workspace too small
+        p = B.make_params(**ok)
+        B.rmrtlb_create(B.D2Q9, 8, 8, 1, 1.0, 1.0, 1.0, 1.0, p, 0, 0, B.ST_F32, 256, 16, 0)
+    assert ei.value.status == B.ENOMEM
+
+
+def test_bgk_limit_constants(B):
+    """Standard lattice, c_s^2 = 1/3 and equal rates: the S_2 block is s I."""
+    s = 1.3
+    nu = (1 / s - 0.5) / 3
+    nub = (1 / 2) * (1 / s - 0.5) * (1 - 1 / 3)
+    h = create(B, B.D2Q9, (8, 8, 1), (1.0, 1.0, 1.0), nu=nu, nu_bulk=nub, s_free=s, cs2=1 / 3, rho0=1.0)
+    c = B.rmrtlb_get_constants(h)
+    B.rmrtlb_destroy(h)
+    np.testing.assert_allclose(c[35:44].reshape(3, 3)[:2, :2], s * np.eye(2), atol=1e-14)

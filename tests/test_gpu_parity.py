@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (normwise max|gpu - oracle| / max|oracle| per field):
+  FP64 storage/compute  1e-12  (rho, u, phi after the run)
+  FP32                  1e-5
+  FP16 / BF16 shifted   2e-3 of max|u| (max|phi| for the NCDE)
+Populations are compared element by element at the same tolerances scaled
+to the population magnitude.
+"""
+import numpy as np
+import pytest
+
+import oracle.rmrt as R
+import workloads as W
+from cases import Case, gpu_run, gpu_solver, normwise, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 2e-3, "bf16": 2e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available(), "the -m gpu tests need a CUDA device"
+    from paper_2206_00366_gb300 import build
+    build.build()
+
+
+def small_shape(lattice):
+    return (37, 23, 1) if lattice == "D2Q9" else (13, 11, 7)
+
+
+# ---------------------------------------------------------------- config 1 in full
+def test_taylor_green_rd2q9_f64_2000_steps():
+    """rD2Q9 NSE Taylor-Green, 64 x 32, dx = 1, dy = 0.5, FP64, rho0 = 1,
+    u0 = 0.01, nu = 0.01, bulk rate 1.2, free rates 1.1, 2000 steps: the
+    GPU matches the oracle to 1e-12 and decays at exp(-2 nu k^2 t)."""
+    cs2 = 0.25 / 3
+    nub = 0.5 * (1 / 1.2 - 0.5) * (1.0 - cs2)     # bulk rate 1.2 read on the x axis
+    case = Case("D2Q9", (64, 32, 1), (1.0, 0.5, 1.0), nu=0.01, nu_bulk=nub, s_free=1.1)
+    rho, u = W.taylor_green_2d(64, 32, 1.0, 0.5, 0.01, 1.0, cs2)
+    _, ro, uo = oracle_run(case, 2000, fields=(rho, u))
+    _, rg, ug = gpu_run(case, "f64", 2000, fields=(rho, u))
+    assert normwise(rg, ro) <= 1e-12
+    assert normwise(ug, uo) <= 1e-12
+    assert normwise(rg - 1.0, ro - 1.0) <= 1e-9
+    k2 = (2 * np.pi / 64) ** 2 + (2 * np.pi / 16) ** 2
+    e0 = (u ** 2).sum()
+    e1 = (ug ** 2).sum()
+    assert abs(-np.log(e1 / e0) / 2000 / (2 * 0.01 * k2) - 1) < 0.02
+
+
+# ---------------------------------------------------------------- every variant, random populations
+KINDS = ["nse", "nse_heluo", "ncde_linear", "ncde_quad"]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("forced", [False, True])
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("basis", ["raw", "central"])
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19", "D3Q27"])
+def test_random_populations(lattice, basis, kind, forced, storage):
+    shape = small_shape(lattice)
+    case = Case(lattice, shape, (1.0, 0.7, 0.55), kind=kind, basis=basis,
+                force=(2e-5, -1e-5, 1.5e-5) if forced else (0, 0, 0),
+                source=3e-6 if forced else 0.0)
+    q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}[lattice]
+    pops = W.random_populations(q, case.field_shape, seed=17, level=1.0, amp=0.05)
+    steps = 6
+    fo, ro, uo = oracle_run(case, steps, pops=pops, key="random-pops-seed17")
+    fg, rg, ug = gpu_run(case, storage, steps, pops=pops)
+    tol = TOL[storage]
+    assert normwise(fg, fo) <= tol
+    assert normwise(rg, ro) <= tol
+    if kind.startswith("nse"):
+        assert normwise(ug, uo) <= 10 * tol
+
+
+def test_set_get_roundtrip():
+    """set_populations then get_populations returns the input (FP64)."""
+    case = Case("D3Q27", (9, 5, 4), (1.0, 0.8, 0.6))
+    pops = W.random_populations(27, case.field_shape, seed=3)
+    s = gpu_solver(case, "f64")
+    s.set_populations(pops)
+    back = s.get_populations()
+    np.testing.assert_allclose(back, pops, rtol=1e-15, atol=1e-16)
+
+
+# ---------------------------------------------------------------- smooth flows, all storages
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+def test_taylor_green_modes_rd2q9(storage):
+    """Downscaled rD2Q9 workload: 256 x 128, dy = 0.6, four seeded TGV modes."""
+    nx, ny = 256, 128
+    case = Case("D2Q9", (nx, ny, 1), (1.0, 0.6, 1.0), nu=0.01, nu_bulk=0.02, s_free=1.1)
+    cs2 = 0.36 / 3
+    rho, u = W.taylor_green_2d_modes(nx, ny, 1.0, 0.6, 1.0, cs2, seed=1)
+    steps = 300
+    _, ro, uo = oracle_run(case, steps, fields=(rho, u), key="tgv-modes-seed1")
+    _, rg, ug = gpu_run(case, storage, steps, fields=(rho, u))
+    assert normwise(ug, uo) <= TOL[storage]
+    assert normwise(rg, ro) <= TOL[storage]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("kind", ["ncde_linear", "ncde_quad"])
+def test_gaussian_hill_rd2q9(storage, kind):
+    nx, ny = 160, 96
+    case = Case("D2Q9", (nx, ny, 1), (1.0, 0.6, 1.0), kind=kind, diffusivity=0.005, adv=(0.05, 0.02, 0.0),
+                rho0=0.0, s_free=1.1)
+    phi = W.gaussian_hill((1, ny, nx), (1.0, 0.6), sigma0=8.0, peak=1.0)
+    u = np.zeros((2, 1, ny, nx))
+    steps = 300
+    _, po, _ = oracle_run(case, steps, fields=(phi, u), key="hill-sigma8")
+    _, pg, _ = gpu_run(case, storage, steps, fields=(phi, u))
+    assert normwise(pg, po) <= TOL[storage]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("basis", ["raw", "central"])
+@pytest.mark.parametrize("lattice", ["D3Q19", "D3Q27"])
+def test_taylor_green_3d(lattice, basis, storage):
+    """Downscaled 3-D workload: 32 x 32 x 16, dz = 0.5, u0 = 0.02, nu = 0.005."""
+    nx, ny, nz = 32, 32, 16
+    case = Case(lattice, (nx, ny, nz), (1.0, 1.0, 0.5), basis=basis, nu=0.005, nu_bulk=0.01, s_free=1.1)
+    rho, u = W.taylor_green_3d(nx, ny, nz, 1.0, 1.0, 0.5, 0.02, 1.0)
+    steps = 60
+    _, ro, uo = oracle_run(case, steps, fields=(rho, u), key="tgv3d-u0.02")
+    _, rg, ug = gpu_run(case, storage, steps, fields=(rho, u))
+    assert normwise(ug, uo) <= TOL[storage]
+    assert normwise(rg, ro) <= TOL[storage]
+
+
+# ---------------------------------------------------------------- full-size, sampled
+def sampled_oracle(case, rho, u, nodes):
+    """One step of the oracle at sampled nodes from the equilibrium state
+    f^eq(rho, u): collide each upstream node x - e_j, take direction j."""
+    lat, m, S = case.oracle_setup()
+    nz, ny, nx = rho.shape
+    n = nodes.shape[0]
+    out = np.empty((lat.q, n))
+    for j in range(lat.q):
+        ez = int(lat.e[j, 2]) if lat.d == 3 else 0
+        z = (nodes[:, 0] - ez) % nz
+        y = (nodes[:, 1] - lat.e[j, 1]) % ny
+        x = (nodes[:, 2] - lat.e[j, 0]) % nx
+        r = rho[z, y, x].reshape(1, 1, n)
+        uu = u[:, z, y, x].reshape(lat.d, 1, 1, n)
+        f0 = R.init_equilibrium(lat, m, S, r, uu).reshape(lat.q, n)
+        out[j] = R.collide(lat, m, S, f0)[j]
+    return out
+
+
+@pytest.mark.parametrize("lattice,basis", [("D2Q9", "raw"), ("D3Q19", "raw"), ("D3Q19", "central"),
+                                           ("D3Q27", "raw"), ("D3Q27", "central")])
+def test_full_size_one_step_sampled(lattice, basis):
+    """Full workload sizes (4096 x 2048 rD2Q9, 256 x 256 x 128 rD3Q19/27),
+    FP32, the launch configuration the bench times: one step from seeded
+    fields, 3000 sampled nodes against the oracle."""
+    import torch
+    if lattice == "D2Q9":
+        shape, sp = (4096, 2048, 1), (1.0, 0.6, 1.0)
+        rho, u = W.taylor_green_2d_modes(4096, 2048, 1.0, 0.6, 1.0, 0.12, seed=2)
+    else:
+        shape, sp = (256, 256, 128), (1.0, 1.0, 0.5)
+        rho, u = W.random_fields((128, 256, 256), 3, seed=5, umax=0.02)
+    case = Case(lattice, shape, sp, basis=basis, nu=0.005, nu_bulk=0.01, s_free=1.1)
+    s = gpu_solver(case, "f32")
+    s.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    s.step(1)
+    fg = torch.empty((s.q,) + rho.shape, dtype=torch.float64, device="cuda")
+    s.get_populations(fg)
+    rng = np.random.default_rng(11)
+    nz, ny, nx = rho.shape
+    nodes = np.stack([rng.integers(0, nz, 3000), rng.integers(0, ny, 3000), rng.integers(0, nx, 3000)], axis=1)
+    # always include the wrap corners
+    nodes[:4] = [[0, 0, 0], [nz - 1, ny - 1, nx - 1], [0, ny - 1, 0], [nz - 1, 0, nx - 1]]
+    idx = torch.from_numpy(nodes).cuda()
+    got = fg[:, idx[:, 0], idx[:, 1], idx[:, 2]].cpu().numpy()
+    want = sampled_oracle(case, rho, u, nodes)
+    assert normwise(got, want) <= 1e-6
+
+
+# ---------------------------------------------------------------- edge cases and API
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 1, 1), (1, 3, 1), (3, 2, 1)])
+def test_degenerate_2d_grids(shape):
+    case = Case("D2Q9", shape, (1.0, 0.6, 1.0))
+    pops = W.random_populations(9, case.field_shape, seed=1)
+    fo, _, _ = oracle_run(case, 4, pops=pops)
+    fg, _, _ = gpu_run(case, "f64", 4, pops=pops)
+    assert normwise(fg, fo) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 1, 3), (1, 2, 1)])
+def test_degenerate_3d_grids(shape):
+    case = Case("D3Q27", shape, (1.0, 0.8, 0.6), basis="central")
+    pops = W.random_populations(27, case.field_shape, seed=2)
+    fo, _, _ = oracle_run(case, 3, pops=pops)
+    fg, _, _ = gpu_run(case, "f64", 3, pops=pops)
+    assert normwise(fg, fo) <= 1e-12
+
+
+def test_zero_steps_and_host_device_pointers():
+    import torch
+    case = Case("D3Q19", (13, 11, 7), (1.0, 0.7, 0.55))
+    pops = W.random_populations(19, case.field_shape, seed=4)
+    s = gpu_solver(case, "f64")
+    s.set_populations(torch.from_numpy(pops).cuda())
+    s.step(0)
+    back = s.get_populations()
+    np.testing.assert_allclose(back, pops, rtol=1e-15, atol=1e-16)
+    s.step(3)
+    host_f = s.get_populations()
+    dev_f = torch.empty_like(torch.from_numpy(pops)).cuda()
+    s.get_populations(dev_f)
+    np.testing.assert_array_equal(host_f, dev_f.cpu().numpy())
+    rho_h, u_h = s.moments()
+    rho_d = torch.empty(case.field_shape, dtype=torch.float64, device="cuda")
+    u_d = torch.empty((3,) + case.field_shape, dtype=torch.float64, device="cuda")
+    s.moments(rho_d, u_d)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(rho_h, rho_d.cpu().numpy())
+    np.testing.assert_array_equal(u_h, u_d.cpu().numpy())
+
+
+def test_stats_conservation_and_residual():
+    """FP64 check: totals equal the field sums; mass and momentum are
+    conserved (Eq. 4-18-1); the residual is ||u(t) - u(t-k)|| / ||u(t)||."""
+    nx, ny, nz = 48, 40, 24
+    case = Case("D3Q27", (nx, ny, nz), (1.0, 1.0, 0.5), nu=0.01, nu_bulk=0.02)
+    rho, u = W.taylor_green_3d(nx, ny, nz, 1.0, 1.0, 0.5, 0.02, 1.0)
+    s = gpu_solver(case, "f64", check_every=10)
+    s.init_equilibrium(rho, u)
+    st0 = s.stats()
+    r0, u0 = s.moments()
+    assert abs(st0[0] - r0.sum()) < 1e-9
+    np.testing.assert_allclose(st0[1:4], (r0[None] * u0).reshape(3, -1).sum(1), atol=1e-12)
+    s.step(10)
+    r1, u1 = s.moments()
+    s.step(10)
+    r2, u2 = s.moments()
+    chk = s.last_check()
+    assert chk[6] == 20
+    want = np.sqrt(((u2 - u1) ** 2).sum() / (u2 ** 2).sum())
+    assert abs(chk[5] / want - 1) < 1e-10
+    assert abs(chk[0] - st0[0]) / st0[0] < 1e-13
+    np.testing.assert_allclose(chk[1:4], st0[1:4], atol=1e-13)
+    assert chk[7] == 0
+
+
+def test_unstable_flag_from_nan_input():
+    """A NaN planted in the host-side initial field is reported as
+    RMRTLB_EUNSTABLE by the check (no GPU fault is involved)."""
+    from paper_2206_00366_gb300 import rmrtlb as B
+    case = Case("D2Q9", (32, 16, 1), (1.0, 0.6, 1.0))
+    rho = np.ones(case.field_shape)
+    u = np.zeros((2,) + case.field_shape)
+    rho[0, 3, 5] = np.nan
+    s = gpu_solver(case, "f32")
+    s.init_equilibrium(rho, u)
+    s.step(2)
+    with pytest.raises(B.RmrtlbError) as ei:
+        s.stats()
+    assert ei.value.status == B.EUNSTABLE
+    st = s.stats(allow_unstable=True)
+    assert int(st[7]) & 1
