@@ -384,6 +384,26 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_only(args):
+    """One workload by name, no e2e / variants / oracle: the command the ncu
+    summaries under profiles/ were taken with."""
+    import torch
+    from paper_2206_00366_gb300 import build as _build
+    _build.build()
+    table = {"rD2Q9-f32": ("D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "f32", "raw", "nse")}
+    table.update({v[0]: v[1:] for v in VARIANTS})
+    lat, shape, sp, st, basis, kind = table[args.only]
+    s = make_solver(lat, shape, sp, st, basis, kind, 0)
+    r_, u_ = initial_fields(lat, shape, sp, kind, 1)
+    s.init_equilibrium(torch.from_numpy(r_).cuda(), torch.from_numpy(u_).cuda())
+    tot, km = time_solver(s, args.steps, args.warmup)
+    n = shape[0] * shape[1] * shape[2]
+    b = 2 * Q[lat] * ESIZE[st] * n
+    print(json.dumps({"only": args.only, "steps": args.steps, "mlups": round(n * args.steps / (tot * 1e-3) / 1e6, 1),
+                      "kernel_ms": round(km, 5), "achieved_gbs": round(b / (km * 1e-3) / 1e9, 1),
+                      "bytes_per_launch": b}))
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--oracle-worker":
         _oracle_worker(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
@@ -395,10 +415,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None, help="time one named workload only (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.only:
+        run_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

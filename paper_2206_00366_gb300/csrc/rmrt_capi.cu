@@ -67,6 +67,12 @@ int block_x(int nx) {
   return ((nx + 31) / 32) * 32;
 }
 
+// Blocks of the grid-stride check kernel (one partial row each).
+size_t check_blocks(size_t N) {
+  const size_t b = (N + CHECK_THREADS - 1) / CHECK_THREADS;
+  return b < size_t(CHECK_MAX_BLOCKS) ? b : size_t(CHECK_MAX_BLOCKS);
+}
+
 struct Layout {
   size_t fA, fB, stage, uprev, partials, stats, flags, total, nblk;
 };
@@ -74,9 +80,8 @@ struct Layout {
 Layout make_layout(int lat, int nx, int ny, int nz, int st) {
   const size_t N = size_t(nx) * ny * nz;
   const int q = lattice_q(lat), d = lattice_d(lat);
-  const size_t bx = block_x(nx);
   Layout L;
-  L.nblk = ((nx + bx - 1) / bx) * size_t(ny) * nz;
+  L.nblk = check_blocks(N);
   const size_t pop = align_up(q * N * storage_size(st));
   L.fA = 0;
   L.fB = L.fA + pop;
@@ -206,20 +211,39 @@ KParams<CT> to_kparams(const Consts& k) {
   p.nx = k.nx; p.ny = k.ny; p.nz = k.nz;
   p.kind = k.kind; p.forced = k.forced; p.N = k.N;
   p.rho0 = CT(k.rho0); p.cs2 = CT(k.cs2); p.dt = CT(k.dt); p.source = CT(k.source);
+  p.rho0d = k.rho0;
+  double c[3], c2[3];
+  for (int a = 0; a < 3; ++a) {
+    c[a] = a < k.d ? k.c[a] : 1.0;
+    c2[a] = c[a] * c[a];
+  }
   for (int a = 0; a < 3; ++a) {
     const bool used = a < k.d;
-    const double c = used ? k.c[a] : 1.0;
-    p.c[a] = CT(c); p.c2[a] = CT(c * c); p.ic[a] = CT(1.0 / c); p.ic2[a] = CT(1.0 / (c * c));
+    p.c[a] = CT(c[a]);
+    p.mu2[a] = used ? CT(k.cs2 / c2[a]) : CT(0);
     p.force[a] = used ? CT(k.force[a]) : CT(0);
+    p.fh[a] = used ? CT(k.force[a] / c[a]) : CT(0);
     p.adv[a] = used ? CT(k.adv[a]) : CT(0);
+    p.advh[a] = used ? CT(k.adv[a] / c[a]) : CT(0);
     p.s1[a] = CT(k.s1[a]);
     p.soff[a] = CT(k.soff[a]);
-    for (int b = 0; b < 3; ++b) p.s2[a][b] = CT(k.s2[a][b]);
-    p.q19k[a] = used ? CT(k.cs2 * k.cs2 / (c * c - k.cs2)) : CT(0);
+    // index units: dmh_a = (1 / c_a^2) sum_b S_ab c_b^2 Xh_b
+    for (int b = 0; b < 3; ++b) p.s2h[a][b] = CT(k.s2[a][b] * c2[b] / c2[a]);
+  }
+  if (k.lat == RMRTLB_D3Q19) {
+    for (int g = 0; g < 3; ++g) {
+      const int al = (g + 1) % 3, be = (g + 2) % 3;
+      p.q19h[g] = CT(k.cs2 * k.cs2 * c2[g] / ((c2[g] - k.cs2) * c2[al] * c2[be]));
+    }
   }
   for (int j = 0; j < 27; ++j) {
-    p.w[j] = j < k.q ? CT(k.w[j]) : CT(0);
-    p.iw[j] = j < k.q ? CT(1.0 / k.w[j]) : CT(0);
+    if (j < k.q) {
+      // power of two nearest 1/omega_j: scaling by it is exact
+      const int e = int(lround(-log2(k.w[j])));
+      p.sc[j] = CT(ldexp(1.0, e));
+      p.sinv[j] = CT(ldexp(1.0, -e));
+      p.wd[j] = k.w[j];
+    }
   }
   p.s0 = CT(k.s0); p.sfree = CT(k.sfree);
   return p;
@@ -237,6 +261,7 @@ struct rmrtlb_solver {
   int cur;            // 0: populations in fA, 1: in fB
   long long step;
   int check_every;
+  int pairs;          // step kernel handles two nodes per thread (nx even)
   bool has_prev;      // a periodic check wrote the residual snapshot
   long long slot_step[kSlots];
   bool slot_prev[kSlots];
@@ -293,6 +318,8 @@ cudaError_t run_check(rmrtlb_solver* s, int slot, double* rho_out, double* u_out
     if (e != cudaSuccess) return e;
   }
   LaunchArgs a = base_args(s, OP_CHECK);
+  a.grid = dim3(unsigned(s->L.nblk), 1, 1);
+  a.block = dim3(CHECK_THREADS, 1, 1);
   a.fin = pop_ptr(s, s->cur);
   a.rho_out = rho_out;
   a.u_out = u_out;
@@ -415,6 +442,7 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
   s->kp64 = to_kparams<double>(k);
   s->kp32 = to_kparams<float>(k);
   s->check_every = params->check_every;
+  s->pairs = (nx % 2 == 0);
   *solver = s;
   return RMRTLB_OK;
 }
@@ -521,6 +549,13 @@ int rmrtlb_step(rmrtlb_t s, int n) {
   if (!s || n < 0) return RMRTLB_EINVAL;
   for (int i = 0; i < n; ++i) {
     LaunchArgs a = base_args(s, OP_STEP);
+    if (s->pairs) {
+      const int half = s->k.nx / 2;
+      const int bx = block_x(half);
+      a.pairs = 1;
+      a.block = dim3(bx, 1, 1);
+      a.grid = dim3((half + bx - 1) / bx, s->k.ny, s->k.nz);
+    }
     a.fin = pop_ptr(s, s->cur);
     a.fout = pop_ptr(s, 1 - s->cur);
     if (launch(s, a) != cudaSuccess) return RMRTLB_ECUDA;

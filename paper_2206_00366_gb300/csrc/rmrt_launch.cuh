@@ -10,14 +10,26 @@ namespace rmrt {
 template <int LAT, typename ST, typename CT>
 static cudaError_t launch_typed(const LaunchArgs& a, const KParams<CT>& p) {
   switch (a.op) {
-    case OP_STEP:
-      if (a.central)
-        step_kernel<LAT, ST, CT, true><<<a.grid, a.block, 0, a.stream>>>(
-            static_cast<const ST*>(a.fin), static_cast<ST*>(a.fout), p);
-      else
-        step_kernel<LAT, ST, CT, false><<<a.grid, a.block, 0, a.stream>>>(
-            static_cast<const ST*>(a.fin), static_cast<ST*>(a.fout), p);
+    case OP_STEP: {
+      const ST* fin = static_cast<const ST*>(a.fin);
+      ST* fout = static_cast<ST*>(a.fout);
+      if (a.pairs) {
+        if (a.central) {
+          if (p.forced) step_kernel_x2<LAT, ST, CT, true, true><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+          else step_kernel_x2<LAT, ST, CT, true, false><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+        } else {
+          if (p.forced) step_kernel_x2<LAT, ST, CT, false, true><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+          else step_kernel_x2<LAT, ST, CT, false, false><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+        }
+      } else if (a.central) {
+        if (p.forced) step_kernel<LAT, ST, CT, true, true><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+        else step_kernel<LAT, ST, CT, true, false><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+      } else {
+        if (p.forced) step_kernel<LAT, ST, CT, false, true><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+        else step_kernel<LAT, ST, CT, false, false><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+      }
       break;
+    }
     case OP_INIT_EQ:
       init_eq_kernel<LAT, ST, CT><<<a.grid, a.block, 0, a.stream>>>(static_cast<ST*>(a.fout), a.rho, a.u, p);
       break;

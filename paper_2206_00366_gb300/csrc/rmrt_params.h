@@ -22,11 +22,15 @@ struct KParams {
   int pad_;
   size_t N;        // nodes = nx * ny * nz
   CT rho0, cs2, dt, source;
-  CT c[3], c2[3], ic[3], ic2[3];       // c_a, c_a^2, 1/c_a, 1/c_a^2
-  CT w[27], iw[27];                    // omega_j, 1/omega_j
-  CT s0, s1[3], s2[3][3], soff[3], sfree;
-  CT force[3], adv[3];
-  CT q19k[3];                          // c_s^4 / (c_g^2 - c_s^2), rD3Q19 only
+  CT c[3];                             // c_a
+  CT mu2[3];                           // c_s^2 / c_a^2 (index-unit second weight moment)
+  CT sc[27], sinv[27];                 // storage scale (power of two ~ 1/omega_j) and its inverse
+  CT s0, s1[3], s2h[3][3], soff[3], sfree;  // rates; s2h: S_2 diagonal block in index units
+  CT force[3], fh[3];                  // Fbar_a and Fbar_a / c_a
+  CT adv[3], advh[3];                  // NCDE advection u_a and u_a / c_a
+  CT q19h[3];                          // rD3Q19 fourth-moment term in index units
+  double wd[27];                       // omega_j in FP64 (population set/get)
+  double rho0d;
 };
 
 enum Op { OP_STEP = 0, OP_INIT_EQ = 1, OP_PLANE = 2, OP_CHECK = 3 };
@@ -35,6 +39,7 @@ struct LaunchArgs {
   Op op;
   int storage;     // ST_*
   int central;     // 1: central-moment relaxation
+  int pairs;       // OP_STEP: two nodes per thread (nx even)
   const void* fin;
   void* fout;
   const double* rho;       // OP_INIT_EQ
