@@ -48,12 +48,16 @@ CHECK_EVERY = 100
 FALLBACK_HBM_GBS = 6800.0
 
 
+STEP_KERNEL_SOURCES = ("rmrt_device.cuh", "rmrt_params.h", "rmrt_launch.cuh", "build.py")
+
+
 def kernel_source_hash() -> str:
-    csrc = os.path.join(ROOT, "paper_2206_00366_gb300", "csrc")
+    """Hash of the files that define the step kernels and how they are built."""
+    pkg = os.path.join(ROOT, "paper_2206_00366_gb300")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_KERNEL_SOURCES:
+        path = os.path.join(pkg, "csrc", f) if f != "build.py" else os.path.join(pkg, f)
+        h.update(open(path, "rb").read())
     return h.hexdigest()[:16]
 
 

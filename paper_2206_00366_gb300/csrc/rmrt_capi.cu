@@ -8,6 +8,7 @@
 #include <new>
 
 #include "../../include/rmrtlb.h"
+#include "rmrt_aux.cuh"
 #include "rmrt_device.cuh"
 #include "rmrt_params.h"
 

@@ -557,163 +557,4 @@ __global__ void __launch_bounds__(128) step_kernel_x2(const ST* __restrict__ fin
   });
 }
 
-// fbar = f^eq(rho, u) at node x, stored where the next pull gather reads it
-// (slot of x - e_j).
-template <int LAT, typename ST, typename CT>
-__global__ void init_eq_kernel(ST* __restrict__ f, const double* __restrict__ rho,
-                               const double* __restrict__ u, const KParams<CT> p) {
-  using L = Lat<LAT>;
-  constexpr int D = L::D, NZ = L::NZ;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  if (x >= p.nx) return;
-  const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
-  const size_t N = p.N;
-  const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
-  const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
-  const CT r = CT(rho[own]);
-  CT uh[3] = {CT(0), CT(0), CT(0)};
-  for (int al = 0; al < D; ++al) uh[al] = nse ? CT(u[al * N + own] / double(p.c[al])) : p.advh[al];
-  Macro<CT> mc;
-  mc.dA = CT(rho[own] - double(p.rho0));
-  mc.rho = r;
-  eq_args(mc, r, uh, p);
-  Cube<LAT, CT> q;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < NZ; ++c)
-        q.v[a][b][c] = absent<LAT>(a, b, c) ? CT(0) : meq_moment<LAT>(a, b, c, mc.dA, mc.B, mc.M, p);
-  q.inverse();
-  static_for<L::Q>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-    const int dx_ = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
-    const int dy_ = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
-    const int dz_ = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
-    const size_t idx = (size_t(dz_) * p.ny + dy_) * p.nx + dx_;
-    store_st<ST, CT>(f + j * N + idx, q.v[ex + 1][ey + 1][zi<LAT>(ez)] * p.sc[j]);
-  });
-}
-
-// Canonical populations <-> storage (one plane j at a time), in FP64.
-// to_storage: f[j][x - e_j] = encode(src[x]); from_storage: dst[x] = decode(f[j][x - e_j]).
-template <int LAT, typename ST, typename CT>
-__global__ void plane_kernel(ST* __restrict__ f, double* __restrict__ plane, int j, int to_storage,
-                             const KParams<CT> p) {
-  using L = Lat<LAT>;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  if (x >= p.nx) return;
-  const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
-  int ex = 0, ey = 0, ez = 0;
-  static_for<L::Q>([&](auto J) {
-    constexpr int jj = decltype(J)::value;
-    constexpr int cx = L::EX[jj], cy = L::EY[jj], cz = L::EZ[jj];
-    if (jj == j) { ex = cx; ey = cy; ez = cz; }
-  });
-  const int sx = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
-  const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
-  const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
-  const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
-  const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
-  ST* fj = f + size_t(j) * p.N;
-  const double rest = p.wd[j] * p.rho0d;
-  if (to_storage) {
-    store_st<ST, CT>(fj + idx, CT((plane[own] - rest) * double(p.sc[j])));
-  } else {
-    plane[own] = double(load_st<ST, CT>(fj + idx)) * double(p.sinv[j]) + rest;
-  }
-}
-
-// Macroscopic fields and FP64 check sums of the current populations.
-// Grid-stride over the nodes (1-D grid of CHECK_THREADS-thread blocks);
-// sums per block: [0] sum drho, [1..3] momentum, [4] kinetic energy,
-// [5] sum |u - u_prev|^2, [6] sum |u|^2, [7] unused.
-constexpr int CHECK_THREADS = 256;
-constexpr int CHECK_MAX_BLOCKS = 1024;
-
-template <int LAT, typename ST, typename CT>
-__global__ void __launch_bounds__(CHECK_THREADS) check_kernel(
-    const ST* __restrict__ fin, double* __restrict__ rho_out, double* __restrict__ u_out,
-    double* __restrict__ uprev, int use_prev, int write_prev, double* __restrict__ partials,
-    int* __restrict__ flags, const KParams<CT> p) {
-  using L = Lat<LAT>;
-  constexpr int D = L::D;
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  int flag = 0;
-  const size_t N = p.N;
-  const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
-  const double hdt = 0.5 * double(p.dt);
-  for (size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x; n < N; n += size_t(gridDim.x) * blockDim.x) {
-    const int x = int(n % p.nx);
-    const size_t r = n / p.nx;
-    const int y = int(r % p.ny), z = int(r / p.ny);
-    const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
-    double s0 = 0, s1[3] = {0, 0, 0};
-    static_for<L::Q>([&](auto J) {
-      constexpr int j = decltype(J)::value;
-      constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-      const int sx = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
-      const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
-      const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
-      const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
-      const double dj = double(load_st<ST, CT>(fin + j * N + idx)) * double(p.sinv[j]);
-      s0 += dj;
-      if (ex) s1[0] += ex * dj;
-      if (ey) s1[1] += ey * dj;
-      if (ez) s1[2] += ez * dj;
-    });
-    const double drho = s0 + hdt * double(p.source);
-    const double rho = double(p.rho0) + drho;
-    double u[3] = {0, 0, 0}, jm[3] = {0, 0, 0};
-    for (int al = 0; al < D; ++al) {
-      jm[al] = s1[al] * double(p.c[al]) + hdt * double(p.force[al]);
-      u[al] = nse ? jm[al] / (p.kind == KIND_NSE ? rho : double(p.rho0)) : double(p.adv[al]);
-    }
-    if (!nse)
-      for (int al = 0; al < D; ++al) jm[al] = rho * u[al];
-    if (rho_out) rho_out[n] = rho;
-    double u2 = 0, du2 = 0;
-    for (int al = 0; al < D; ++al) {
-      if (u_out) u_out[al * N + n] = u[al];
-      u2 += u[al] * u[al];
-      if (uprev) {
-        const double d = u[al] - (use_prev ? uprev[al * N + n] : 0.0);
-        du2 += d * d;
-        if (write_prev) uprev[al * N + n] = u[al];
-      }
-    }
-    acc[0] += drho;
-    acc[1] += jm[0]; acc[2] += jm[1]; acc[3] += jm[2];
-    acc[4] += 0.5 * rho * u2;
-    acc[5] += du2;
-    acc[6] += u2;
-    if (!(drho == drho) || !(u2 == u2) || isinf(drho) || isinf(u2)) flag |= 1;
-    if (nse && rho <= 0.0) flag |= 2;
-    if (nse && u2 >= double(p.cs2)) flag |= 4;
-  }
-  if (partials) {
-    // warp then block reduction in FP64, fixed order (deterministic)
-#pragma unroll
-    for (int k = 0; k < 7; ++k)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
-    __shared__ double sm[CHECK_THREADS / 32][7];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-#pragma unroll
-      for (int k = 0; k < 7; ++k) sm[warp][k] = acc[k];
-    __syncthreads();
-    if (threadIdx.x < 7) {
-      double s = 0;
-      for (int w = 0; w < CHECK_THREADS / 32; ++w) s += sm[w][threadIdx.x];
-      partials[size_t(blockIdx.x) * 8 + threadIdx.x] = s;
-    }
-  }
-  if (flag && flags) atomicOr(flags, flag);
-}
-
 }  // namespace rmrt

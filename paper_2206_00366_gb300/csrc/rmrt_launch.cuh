@@ -3,6 +3,7 @@
 // rmrt_<lattice>.cu with RMRT_LAT and RMRT_LAUNCH_NAME defined.
 #pragma once
 
+#include "rmrt_aux.cuh"
 #include "rmrt_device.cuh"
 
 namespace rmrt {
