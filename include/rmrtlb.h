@@ -56,6 +56,8 @@ extern "C" {
 #define RMRTLB_ECUDA     (-3)  /* a CUDA runtime call failed */
 #define RMRTLB_EUNSTABLE (-4)  /* NaN/Inf, density <= 0 or |u| >= c_s seen by
                                   the last check step */
+#define RMRTLB_ETOOBIG   (-5)  /* input larger than a fixed-size internal
+                                  buffer allows */
 
 /* --------------------------------------------------------------- choices */
 enum rmrtlb_lattice { RMRTLB_D2Q9 = 0, RMRTLB_D3Q19 = 1, RMRTLB_D3Q27 = 2 };
@@ -197,6 +199,32 @@ int rmrtlb_stats(rmrtlb_t solver, double out[8]);
 /* Result of the last check that rmrtlb_step ran (same layout as
  * rmrtlb_stats; out[6] = -1 if none ran yet).  Synchronises the stream. */
 int rmrtlb_last_check(rmrtlb_t solver, double out[8]);
+
+/* ------------------------------------------------ allocation-free totals */
+/* The paper has no counterpart to this entry point.  It is for callers that
+ * cannot allocate device memory: code whose device memory is owned by
+ * another allocator (a framework's caching allocator, a pool sized in
+ * advance) or that must not let cudaMalloc synchronise the device between
+ * its stream work.  It computes, in FP64 with a fixed reduction order,
+ *   out[0] = sum_x sum_j f_j            out[1..3] = sum_x sum_j c_j f_j
+ *   out[4] = sum_x |sum_j c_j f_j|^2 / (2 sum_j f_j)
+ * for populations f given as q FP64 planes in rmrtlb_lattice_info order
+ * (device memory, e.g. filled by rmrtlb_get_populations); for an unforced
+ * NSE state these are the mass, momentum and kinetic energy that
+ * rmrtlb_stats reports.  out may be host or device memory (host: the call
+ * synchronises the stream).  No solver and no workspace are needed: the
+ * reduction scratch is a fixed array of (4096 * 8 + 8) doubles inside the
+ * library, present on every GPU that loads it until the process exits.  At
+ * most RMRTLB_NOALLOC_MAX_NODES nodes (nx*ny*nz) are accepted; larger grids
+ * return RMRTLB_ETOOBIG.  The first call on a device looks the array up on
+ * that device; make that first call before any stream capture.  All calls
+ * share the array: calls whose kernels overlap on the GPU (unordered
+ * streams) race and may return wrong totals; calls on one stream are
+ * ordered.  Calls no cudaMalloc or cudaFree. */
+#define RMRTLB_NOALLOC_MAX_NODES 67108864LL
+int rmrtlb_population_totals_noalloc(int lattice, int nx, int ny, int nz,
+                                     double dx, double dy, double dz, double dt,
+                                     const double* f, double* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -373,6 +373,7 @@ const char* rmrtlb_strerror(int status) {
     case RMRTLB_ENOMEM: return "workspace too small";
     case RMRTLB_ECUDA: return "CUDA runtime error";
     case RMRTLB_EUNSTABLE: return "unstable state (NaN/Inf, density <= 0 or |u| >= c_s)";
+    case RMRTLB_ETOOBIG: return "input larger than the fixed internal buffer allows";
     default: return "unknown status";
   }
 }

@@ -24,7 +24,8 @@ D2Q9, D3Q19, D3Q27 = 0, 1, 2
 EQ_NSE, EQ_NSE_HELUO, EQ_NCDE_LINEAR, EQ_NCDE_QUAD = 0, 1, 2, 3
 BASIS_RAW, BASIS_CENTRAL = 0, 1
 ST_F64, ST_F32, ST_F16, ST_BF16 = 0, 1, 2, 3
-OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE = 0, -1, -2, -3, -4
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETOOBIG = 0, -1, -2, -3, -4, -5
+NOALLOC_MAX_NODES = 67108864
 
 LATTICE_NAMES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}
 STORAGE_NAMES = {"f64": ST_F64, "f32": ST_F32, "f16": ST_F16, "bf16": ST_BF16}
@@ -101,6 +102,7 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_moments": (i, [_vp, _vp, _vp]),
         "rmrtlb_stats": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_last_check": (i, [_vp, ctypes.POINTER(d)]),
+        "rmrtlb_population_totals_noalloc": (i, [i, i, i, i, d, d, d, d, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -114,7 +116,7 @@ def exported_symbols() -> list:
     return ["rmrtlb_strerror", "rmrtlb_lattice_info", "rmrtlb_workspace_bytes", "rmrtlb_create",
             "rmrtlb_destroy", "rmrtlb_get_constants", "rmrtlb_init_equilibrium",
             "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
-            "rmrtlb_stats", "rmrtlb_last_check"]
+            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_population_totals_noalloc"]
 
 
 def _check(status: int, where: str):
@@ -192,6 +194,12 @@ def rmrtlb_last_check(h, allow_unstable: bool = False) -> np.ndarray:
     if not (allow_unstable and st == EUNSTABLE):
         _check(st, "rmrtlb_last_check")
     return np.array(out[:])
+
+
+def rmrtlb_population_totals_noalloc(lattice, nx, ny, nz, dx, dy, dz, dt, f: int, out: int, stream: int):
+    """Allocation-free FP64 totals of device populations (see include/rmrtlb.h)."""
+    _check(lib().rmrtlb_population_totals_noalloc(lattice, nx, ny, nz, dx, dy, dz, dt, f, out, stream),
+           "rmrtlb_population_totals_noalloc")
 
 
 # ------------------------------------------------------------------ convenience
