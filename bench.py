@@ -48,7 +48,7 @@ CHECK_EVERY = 100
 FALLBACK_HBM_GBS = 6800.0
 
 
-STEP_KERNEL_SOURCES = ("rmrt_device.cuh", "rmrt_params.h", "rmrt_launch.cuh", "build.py")
+STEP_KERNEL_SOURCES = ("rmrt_device.cuh", "rmrt_params.h", "rmrt_tuning.h", "rmrt_launch.cuh", "build.py")
 
 
 def kernel_source_hash() -> str:

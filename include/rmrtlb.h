@@ -81,10 +81,11 @@ enum rmrtlb_eq_kind {
  * about the local velocity (Eq. 5-1-2 with N = N(u)). */
 enum rmrtlb_basis { RMRTLB_BASIS_RAW = 0, RMRTLB_BASIS_CENTRAL = 1 };
 
-/* Population storage.  All kinds store the deviation fbar_j - omega_j rho0
- * times the power of two nearest 1/omega_j (exact to apply and undo); F64
- * computes in FP64, the others in FP32.  F16 and BF16 round to nearest even
- * on every store. */
+/* Population storage.  Every kind stores the deviation fbar_j - omega_j rho0;
+ * F16 and BF16 store it times the power of two nearest 1/omega_j (exact to
+ * apply and undo, keeps small-weight populations in the normal range) and
+ * round to nearest even on every store.  F64 computes in FP64, the others
+ * in FP32. */
 enum rmrtlb_storage {
     RMRTLB_ST_F64 = 0,
     RMRTLB_ST_F32 = 1,

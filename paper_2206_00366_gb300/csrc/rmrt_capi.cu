@@ -237,10 +237,12 @@ KParams<CT> to_kparams(const Consts& k) {
       p.q19h[g] = CT(k.cs2 * k.cs2 * c2[g] / ((c2[g] - k.cs2) * c2[al] * c2[be]));
     }
   }
+  const bool scaled = k.storage == RMRTLB_ST_F16 || k.storage == RMRTLB_ST_BF16;
   for (int j = 0; j < 27; ++j) {
     if (j < k.q) {
-      // power of two nearest 1/omega_j: scaling by it is exact
-      const int e = int(lround(-log2(k.w[j])));
+      // 16-bit storage: power of two nearest 1/omega_j (exact to apply and
+      // undo); 32/64-bit storage is unscaled
+      const int e = scaled ? int(lround(-log2(k.w[j]))) : 0;
       p.sc[j] = CT(ldexp(1.0, e));
       p.sinv[j] = CT(ldexp(1.0, -e));
       p.wd[j] = k.w[j];
@@ -290,11 +292,12 @@ LaunchArgs base_args(rmrtlb_solver* s, Op op) {
 }
 
 cudaError_t launch(rmrtlb_solver* s, const LaunchArgs& a) {
-  switch (s->k.lat) {
-    case RMRTLB_D2Q9: return launch_d2q9(a);
-    case RMRTLB_D3Q19: return launch_d3q19(a);
-    default: return launch_d3q27(a);
-  }
+  using Fn = cudaError_t (*)(const LaunchArgs&);
+  static const Fn table[3][4] = {
+      {launch_d2q9_f64, launch_d2q9_f32, launch_d2q9_f16, launch_d2q9_bf16},
+      {launch_d3q19_f64, launch_d3q19_f32, launch_d3q19_f16, launch_d3q19_bf16},
+      {launch_d3q27_f64, launch_d3q27_f32, launch_d3q27_f16, launch_d3q27_bf16}};
+  return table[s->k.lat][s->k.storage](a);
 }
 
 bool is_device_ptr(const void* p) {

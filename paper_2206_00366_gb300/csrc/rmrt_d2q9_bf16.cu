@@ -1,0 +1,7 @@
+// Kernels of the d2q9 lattice with bf16 storage (raw and central bases,
+// forced and unforced, NSE and NCDE families).
+#include "rmrt_launch.cuh"
+
+namespace rmrt {
+cudaError_t launch_d2q9_bf16(const LaunchArgs& a) { return launch_storage<LAT_D2Q9, __nv_bfloat16>(a); }
+}  // namespace rmrt

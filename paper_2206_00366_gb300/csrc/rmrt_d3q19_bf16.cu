@@ -1,0 +1,7 @@
+// Kernels of the d3q19 lattice with bf16 storage (raw and central bases,
+// forced and unforced, NSE and NCDE families).
+#include "rmrt_launch.cuh"
+
+namespace rmrt {
+cudaError_t launch_d3q19_bf16(const LaunchArgs& a) { return launch_storage<LAT_D3Q19, __nv_bfloat16>(a); }
+}  // namespace rmrt

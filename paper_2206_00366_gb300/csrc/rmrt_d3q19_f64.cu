@@ -1,0 +1,7 @@
+// Kernels of the d3q19 lattice with f64 storage (raw and central bases,
+// forced and unforced, NSE and NCDE families).
+#include "rmrt_launch.cuh"
+
+namespace rmrt {
+cudaError_t launch_d3q19_f64(const LaunchArgs& a) { return launch_storage<LAT_D3Q19, double>(a); }
+}  // namespace rmrt

@@ -1,0 +1,7 @@
+// Kernels of the d3q27 lattice with f32 storage (raw and central bases,
+// forced and unforced, NSE and NCDE families).
+#include "rmrt_launch.cuh"
+
+namespace rmrt {
+cudaError_t launch_d3q27_f32(const LaunchArgs& a) { return launch_storage<LAT_D3Q27, float>(a); }
+}  // namespace rmrt

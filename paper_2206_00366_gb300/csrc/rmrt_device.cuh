@@ -23,6 +23,7 @@
 #include <utility>
 
 #include "rmrt_params.h"
+#include "rmrt_tuning.h"
 
 namespace rmrt {
 
@@ -97,38 +98,74 @@ struct Nbr {
   __device__ __forceinline__ static int dn(int e, int m, int c, int p) { return e > 0 ? p : (e < 0 ? m : c); }
 };
 
+// ------------------------------------------------------------------ value types
+// The collision is written once for a value type V with scalar parameter
+// type S = Scalar<V>: V = float or double (one node per value), or F2 (two
+// nodes per value, FP32).  F2 arithmetic maps onto the packed FP32
+// instructions of sm_100-class GPUs (__fadd2_rn, __fmul2_rn, __ffma2_rn),
+// so a thread that owns two nodes spends one instruction per operation.
+struct F2 {
+  float2 v;
+  F2() = default;
+  __device__ __forceinline__ F2(float2 x) : v(x) {}
+  __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+  __device__ __forceinline__ F2(double s) : v(make_float2(float(s), float(s))) {}
+  __device__ __forceinline__ F2(int s) : v(make_float2(float(s), float(s))) {}
+  __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { a = a + b; return a; }
+__device__ __forceinline__ F2& operator-=(F2& a, F2 b) { a = a - b; return a; }
+
+template <typename V> struct ScalarOf { using T = V; };
+template <> struct ScalarOf<F2> { using T = float; };
+template <typename V> using Scalar = typename ScalarOf<V>::T;
+
+__device__ __forceinline__ float fmav(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmav(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ F2 fmav(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
+// 1 / x: CUDA's fast single-precision reciprocal for FP32 (its error is far
+// below the FP32 storage rounding), exact division for FP64.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ F2 recip(F2 x) { return F2(__frcp_rn(x.v.x), __frcp_rn(x.v.y)); }
+
 // ------------------------------------------------------------------ 1-D transforms
 // The moments are index moments mh_abc = sum_j e_jx^a e_jy^b e_jz^c f_j; the
 // physical raw moments of Eq. (5-2) are m_abc = c_x^a c_y^b c_z^c mh_abc.
 // Every constant that meets a moment is scaled on the host accordingly, so
 // the transforms are additions only.
 // (f_{-1}, f_0, f_{+1}) -> (sum f, sum e f, sum e^2 f) in place.
-template <typename CT>
-__device__ __forceinline__ void fwd3(CT& a, CT& b, CT& c) {
-  const CT s = a + c, t = c - a;
+template <typename V>
+__device__ __forceinline__ void fwd3(V& a, V& b, V& c) {
+  const V s = a + c, t = c - a;
   a = b + s; b = t; c = s;
 }
 // inverse of fwd3
-template <typename CT>
-__device__ __forceinline__ void inv3(CT& a, CT& b, CT& c) {
-  const CT r = c, t = b, m0 = a;
-  a = CT(0.5) * (r - t); c = CT(0.5) * (r + t); b = m0 - r;
+template <typename V>
+__device__ __forceinline__ void inv3(V& a, V& b, V& c) {
+  const V r = c, t = b, m0 = a;
+  a = (r - t) * V(0.5f); c = (r + t) * V(0.5f); b = m0 - r;
 }
 // index moments about velocity u (in index units u / c): kappa_k = sum (e - u)^k f
-template <typename CT>
-__device__ __forceinline__ void shift3(CT& m0, CT& m1, CT& m2, CT u) {
-  m2 = m2 - CT(2) * u * m1 + u * u * m0;
-  m1 = m1 - u * m0;
+template <typename V>
+__device__ __forceinline__ void shift3(V& m0, V& m1, V& m2, V u) {
+  m2 = fmav(u * u, m0, fmav(V(-2.0f) * u, m1, m2));
+  m1 = fmav(-u, m0, m1);
 }
-template <typename CT>
-__device__ __forceinline__ void unshift3(CT& k0, CT& k1, CT& k2, CT u) {
-  k2 = k2 + CT(2) * u * k1 + u * u * k0;
-  k1 = k1 + u * k0;
+template <typename V>
+__device__ __forceinline__ void unshift3(V& k0, V& k1, V& k2, V u) {
+  k2 = fmav(u * u, k0, fmav(V(2.0f) * u, k1, k2));
+  k1 = fmav(u, k0, k1);
 }
 
-template <int LAT, typename CT> struct Cube {
+template <int LAT, typename V> struct Cube {
   static constexpr int NZ = Lat<LAT>::NZ;
-  CT v[3][3][NZ];
+  V v[3][3][NZ];
 
   __device__ __forceinline__ void forward() {
 #pragma unroll
@@ -163,7 +200,7 @@ template <int LAT, typename CT> struct Cube {
       for (int c = 0; c < NZ; ++c) inv3(v[0][b][c], v[1][b][c], v[2][b][c]);
   }
   template <bool BACK>
-  __device__ __forceinline__ void shift(const CT u[3]) {
+  __device__ __forceinline__ void shift(const V u[3]) {
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
@@ -201,60 +238,95 @@ __device__ __forceinline__ constexpr bool absent(int a, int b, int c) {
 // -c_s^4 M_gg / (c_g^2 - c_s^2) to the physical (2,2,0)-type moments (g
 // the axis with exponent 0), q19h[g] carrying the index scaling.
 // Mh is packed xx, yy, zz, xy, xz, yz.
-template <int LAT, typename CT>
-__device__ __forceinline__ CT meq_moment(int a, int b, int c, CT A, const CT B[3], const CT M[6],
-                                         const KParams<CT>& p) {
-  auto mx = [&](int k) -> CT { return k == 0 ? CT(1) : (k == 1 ? CT(0) : p.mu2[0]); };
-  auto my = [&](int k) -> CT { return k == 0 ? CT(1) : (k == 1 ? CT(0) : p.mu2[1]); };
-  auto mz = [&](int k) -> CT { return k == 0 ? CT(1) : (k == 1 ? CT(0) : p.mu2[2]); };
-  CT r = CT(0);
-  if (a != 1 && b != 1 && c != 1) r = A * mx(a) * my(b) * mz(c);
-  if (a == 1 && b != 1 && c != 1) r += B[0] * my(b) * mz(c);
-  if (b == 1 && a != 1 && c != 1) r += B[1] * mx(a) * mz(c);
-  if (c == 1 && a != 1 && b != 1) r += B[2] * mx(a) * my(b);
-  if (a == 2 && b != 1 && c != 1) r += M[0] * my(b) * mz(c);
-  if (b == 2 && a != 1 && c != 1) r += M[1] * mx(a) * mz(c);
-  if (c == 2 && a != 1 && b != 1) r += M[2] * mx(a) * my(b);
-  if (a == 1 && b == 1 && c != 1) r += M[3] * mz(c);
-  if (a == 1 && c == 1 && b != 1) r += M[4] * my(b);
-  if (b == 1 && c == 1 && a != 1) r += M[5] * mx(a);
+template <int LAT, typename V, typename S>
+__device__ __forceinline__ V meq_moment(int a, int b, int c, V A, const V B[3], const V M[6],
+                                        const KParams<S>& p) {
+  auto mx = [&](int k) -> S { return k == 0 ? S(1) : (k == 1 ? S(0) : p.mu2[0]); };
+  auto my = [&](int k) -> S { return k == 0 ? S(1) : (k == 1 ? S(0) : p.mu2[1]); };
+  auto mz = [&](int k) -> S { return k == 0 ? S(1) : (k == 1 ? S(0) : p.mu2[2]); };
+  // term * factor with the factor folded away when it is exactly 1
+  auto acc = [&](V r, V term, int f0, int f1, S fac) -> V {
+    return (f0 == 0 && f1 == 0) ? r + term : fmav(term, V(fac), r);
+  };
+  V r = V(0.0f);
+  if (a != 1 && b != 1 && c != 1) {
+    const int n2 = (a == 2) + (b == 2) + (c == 2);
+    r = n2 == 0 ? A : A * V(mx(a) * my(b) * mz(c));
+  }
+  if (a == 1 && b != 1 && c != 1) r = acc(r, B[0], b, c, my(b) * mz(c));
+  if (b == 1 && a != 1 && c != 1) r = acc(r, B[1], a, c, mx(a) * mz(c));
+  if (c == 1 && a != 1 && b != 1) r = acc(r, B[2], a, b, mx(a) * my(b));
+  if (a == 2 && b != 1 && c != 1) r = acc(r, M[0], b, c, my(b) * mz(c));
+  if (b == 2 && a != 1 && c != 1) r = acc(r, M[1], a, c, mx(a) * mz(c));
+  if (c == 2 && a != 1 && b != 1) r = acc(r, M[2], a, b, mx(a) * my(b));
+  if (a == 1 && b == 1 && c != 1) r = acc(r, M[3], c, 0, mz(c));
+  if (a == 1 && c == 1 && b != 1) r = acc(r, M[4], b, 0, my(b));
+  if (b == 1 && c == 1 && a != 1) r = acc(r, M[5], a, 0, mx(a));
   if (LAT == LAT_D3Q19) {
-    if (a == 2 && b == 2 && c == 0) r -= p.q19h[2] * M[2];
-    if (a == 2 && b == 0 && c == 2) r -= p.q19h[1] * M[1];
-    if (a == 0 && b == 2 && c == 2) r -= p.q19h[0] * M[0];
+    if (a == 2 && b == 2 && c == 0) r = fmav(M[2], V(-p.q19h[2]), r);
+    if (a == 2 && b == 0 && c == 2) r = fmav(M[1], V(-p.q19h[1]), r);
+    if (a == 0 && b == 2 && c == 2) r = fmav(M[0], V(-p.q19h[0]), r);
   }
   return r;
 }
 
-// S x for the entry (a, b, c) (Eq. 5-1 block structure in index units): the
-// order-2 diagonal entries use the dense block, scaled to index units on the
-// host (s2h = D^-1 S_2 D).
-template <int LAT, typename CT>
-__device__ __forceinline__ CT relax(int a, int b, int c, const CT (&X)[3][3][Lat<LAT>::NZ],
-                                    const KParams<CT>& p) {
+// Rate of a diagonal moment class (Eq. 5-1 block structure in index units);
+// the order-2 diagonal entries instead use the dense block s2h = D^-1 S_2 D.
+template <typename S>
+__device__ __forceinline__ S diag_rate(int a, int b, int c, const KParams<S>& p) {
   const int o = a + b + c;
-  if (absent<LAT>(a, b, c)) return CT(0);
-  if (o == 0) return p.s0 * X[0][0][0];
-  if (o == 1) return p.s1[a == 1 ? 0 : (b == 1 ? 1 : 2)] * X[a][b][c];
-  if (o == 2 && (a == 2 || b == 2 || c == 2)) {
-    const int r = a == 2 ? 0 : (b == 2 ? 1 : 2);
-    CT s = p.s2h[r][0] * X[2][0][0] + p.s2h[r][1] * X[0][2][0];
-    if constexpr (Lat<LAT>::NZ == 3) s += p.s2h[r][2] * X[0][0][2];
-    return s;
-  }
-  if (o == 2) return p.soff[(a == 1 && b == 1) ? 0 : ((a == 1) ? 1 : 2)] * X[a][b][c];
-  return p.sfree * X[a][b][c];
+  if (o == 0) return p.s0;
+  if (o == 1) return p.s1[a == 1 ? 0 : (b == 1 ? 1 : 2)];
+  if (o == 2) return p.soff[(a == 1 && b == 1) ? 0 : ((a == 1) ? 1 : 2)];
+  return p.sfree;
+}
+template <int a, int b, int c>
+__device__ __forceinline__ constexpr bool dense_block() {
+  return a + b + c == 2 && (a == 2 || b == 2 || c == 2);
+}
+
+// out = out - S X (ACC) or out = S X (!ACC).  For the NSE family orders 0
+// and 1 are conserved: X vanishes there (Eq. 4-18-1 with the dt F / 2 terms
+// of Eq. 2-4-2), so s_0 and S_1 act on zero and are skipped.
+template <int LAT, bool NSE, bool ACC, typename V, typename S>
+__device__ __forceinline__ void relax(V (&out)[3][3][Lat<LAT>::NZ], const V (&X)[3][3][Lat<LAT>::NZ],
+                                      const KParams<S>& p) {
+  constexpr int NZ = Lat<LAT>::NZ;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) {
+        const int o = a + b + c;
+        if (absent<LAT>(a, b, c) || (NSE && o < 2)) {
+          if (!ACC) out[a][b][c] = V(0.0f);
+          continue;
+        }
+        if (o == 2 && (a == 2 || b == 2 || c == 2)) {
+          const int r = a == 2 ? 0 : (b == 2 ? 1 : 2);
+          V t = ACC ? out[a][b][c] : V(0.0f);
+          const S sg = ACC ? S(-1) : S(1);
+          t = fmav(X[2][0][0], V(sg * p.s2h[r][0]), t);
+          t = fmav(X[0][2][0], V(sg * p.s2h[r][1]), t);
+          if constexpr (NZ == 3) t = fmav(X[0][0][2], V(sg * p.s2h[r][2]), t);
+          out[a][b][c] = t;
+        } else {
+          const S s = diag_rate(a, b, c, p);
+          out[a][b][c] = ACC ? fmav(X[a][b][c], V(-s), out[a][b][c]) : X[a][b][c] * V(s);
+        }
+      }
 }
 
 // Equilibrium arguments in index units and the velocity (u / c) about
 // which central moments are taken.
-template <typename CT>
+template <typename V>
 struct Macro {
-  CT dA;      // A - rho0 (density or phi deviation)
-  CT B[3];    // B_a / c_a
-  CT M[6];    // M_ab / (c_a c_b): xx yy zz xy xz yz
-  CT u[3];    // u_a / c_a: fluid (NSE) or advection (NCDE) velocity
-  CT rho;     // density or phi
+  V dA;      // A - rho0 (density or phi deviation)
+  V B[3];    // B_a / c_a
+  V M[6];    // M_ab / (c_a c_b): xx yy zz xy xz yz
+  V u[3];    // u_a / c_a: fluid (NSE) or advection (NCDE) velocity
+  V rho;     // density or phi
 };
 
 // A, B, M of the model for density (or phi) rho and index velocity uh.
@@ -271,96 +343,108 @@ __device__ __forceinline__ void eq_args(Macro<CT>& r, CT rho, const CT uh[3], co
   r.M[3] = fc * uh[0] * uh[1]; r.M[4] = fc * uh[0] * uh[2]; r.M[5] = fc * uh[1] * uh[2];
 }
 
-// Conserved fields from the index moments (Eqs. 2-4-1 / 2-4-2).
-template <int D, typename CT>
-__device__ __forceinline__ Macro<CT> macroscopic(CT m000, const CT jh[3], const KParams<CT>& p) {
-  Macro<CT> r;
-  const CT hdt = CT(0.5) * p.dt;
-  const CT drho = m000 + hdt * p.source;
+// Conserved fields from the index moments (Eqs. 2-4-1 / 2-4-2).  NSE: the
+// family of the NSE and He-Luo equilibria; otherwise the two NCDE kinds.
+template <int D, bool NSE, typename V, typename S>
+__device__ __forceinline__ Macro<V> macroscopic(V m000, const V jh[3], const KParams<S>& p) {
+  Macro<V> r;
+  const S hdt = S(0.5) * p.dt;
+  const V drho = m000 + V(hdt * p.source);
   r.dA = drho;
-  r.rho = p.rho0 + drho;
-  CT uh[3];
-  if (p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO) {
-    const CT inv = CT(1) / (p.kind == KIND_NSE ? r.rho : p.rho0);
+  r.rho = V(p.rho0) + drho;
+  V uh[3], fb, fc;
+  if constexpr (NSE) {
+    const bool heluo = p.kind == KIND_NSE_HELUO;
+    const V inv = heluo ? V(S(1) / p.rho0) : recip(r.rho);
 #pragma unroll
-    for (int al = 0; al < 3; ++al) uh[al] = (al < D) ? (jh[al] + hdt * p.fh[al]) * inv : CT(0);
+    for (int al = 0; al < 3; ++al) uh[al] = (al < D) ? fmav(V(hdt * p.fh[al]), inv, jh[al] * inv) : V(0.0f);
+    fb = heluo ? V(p.rho0) : r.rho;                    // g^eq(rho, rho u, rho u u) or (rho, rho0 u, rho0 u u)
+    fc = fb;
   } else {
 #pragma unroll
-    for (int al = 0; al < 3; ++al) uh[al] = p.advh[al];
+    for (int al = 0; al < 3; ++al) uh[al] = V(p.advh[al]);
+    const bool lin = p.kind == KIND_NCDE_LINEAR;       // B = u phi, C = u u phi
+    fb = lin ? r.rho : V(0.5f) * r.rho * r.rho;        // B = u phi^2/2
+    fc = lin ? r.rho : r.rho * r.rho * r.rho * V(S(1.0 / 3.0));   // C = u u phi^3/3
   }
-  eq_args(r, r.rho, uh, p);
+#pragma unroll
+  for (int al = 0; al < 3; ++al) { r.u[al] = uh[al]; r.B[al] = fb * uh[al]; }
+  const V fu0 = fc * uh[0], fu1 = fc * uh[1];
+  r.M[0] = fu0 * uh[0]; r.M[1] = fu1 * uh[1]; r.M[2] = fc * uh[2] * uh[2];
+  r.M[3] = fu0 * uh[1]; r.M[4] = fu0 * uh[2]; r.M[5] = fu1 * uh[2];
   return r;
 }
 
-// Collision of one node in moment space, Eq. (2-2-3):
+// Collision of one node (or a pair of nodes, V = F2) in moment space,
+// Eq. (2-2-3):
 //   m* - m0 = m(delta) + dt (m_G + m_F) - S (m^ne + dt m_F / 2),
 // central variant: S replaced by N(u)^-1 Sbar N(u) (Eq. 5-1-2).
-template <int LAT, typename CT, bool CENTRAL, bool FORCED>
-__device__ __forceinline__ void collide(Cube<LAT, CT>& q, const KParams<CT>& p) {
+template <int LAT, bool CENTRAL, bool FORCED, bool NSE, typename V, typename S>
+__device__ __forceinline__ void collide(Cube<LAT, V>& q, const KParams<S>& p) {
   constexpr int D = Lat<LAT>::D, NZ = Lat<LAT>::NZ;
   q.forward();
-  CT jh[3] = {q.v[1][0][0], q.v[0][1][0], CT(0)};
+  V jh[3] = {q.v[1][0][0], q.v[0][1][0], V(0.0f)};
   if constexpr (NZ == 3) jh[2] = q.v[0][0][NZ - 2];
-  const Macro<CT> mc = macroscopic<D>(q.v[0][0][0], jh, p);
+  const Macro<V> mc = macroscopic<D, NSE>(q.v[0][0][0], jh, p);
 
   // forcing moments (index units): F = g^eq(Sbar, Fbar, -c_s^2 Sbar I) (NSE)
   // or omega S (NCDE); G = g^eq(0, 0, M_2G), M_2G = (I - S_2/2)(u F + F u +
   // c_s^2 Sbar I) (NSE), or G = g^eq(0, (I - S_1/2) B' S, 0) (NCDE).
-  CT FA = CT(0), FB[3] = {CT(0), CT(0), CT(0)}, FM[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
-  CT GB[3] = {CT(0), CT(0), CT(0)}, GM[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
-  const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
+  V FA = V(0.0f), FB[3] = {V(0.0f), V(0.0f), V(0.0f)};
+  V FM[6] = {V(0.0f), V(0.0f), V(0.0f), V(0.0f), V(0.0f), V(0.0f)};
+  V GB[3] = {V(0.0f), V(0.0f), V(0.0f)}, GM[6] = {V(0.0f), V(0.0f), V(0.0f), V(0.0f), V(0.0f), V(0.0f)};
   if constexpr (FORCED) {
-    FA = p.source;
-    if (nse) {
+    FA = V(p.source);
+    if constexpr (NSE) {
 #pragma unroll
-      for (int al = 0; al < 3; ++al) { FB[al] = p.fh[al]; FM[al] = -p.source * p.mu2[al]; }
-      CT Y[6];
+      for (int al = 0; al < 3; ++al) { FB[al] = V(p.fh[al]); FM[al] = V(-p.source * p.mu2[al]); }
+      V Y[6];
 #pragma unroll
-      for (int al = 0; al < 3; ++al) Y[al] = CT(2) * mc.u[al] * p.fh[al] + p.source * p.mu2[al];
-      Y[3] = mc.u[0] * p.fh[1] + p.fh[0] * mc.u[1];
-      Y[4] = mc.u[0] * p.fh[2] + p.fh[0] * mc.u[2];
-      Y[5] = mc.u[1] * p.fh[2] + p.fh[1] * mc.u[2];
+      for (int al = 0; al < 3; ++al) Y[al] = fmav(mc.u[al], V(S(2) * p.fh[al]), V(p.source * p.mu2[al]));
+      Y[3] = fmav(mc.u[0], V(p.fh[1]), mc.u[1] * V(p.fh[0]));
+      Y[4] = fmav(mc.u[0], V(p.fh[2]), mc.u[2] * V(p.fh[0]));
+      Y[5] = fmav(mc.u[1], V(p.fh[2]), mc.u[2] * V(p.fh[1]));
 #pragma unroll
       for (int r = 0; r < D; ++r) {
-        CT s = CT(0);
+        V t = Y[r];
 #pragma unroll
-        for (int k = 0; k < D; ++k) s += p.s2h[r][k] * Y[k];
-        GM[r] = Y[r] - CT(0.5) * s;
+        for (int k = 0; k < D; ++k) t = fmav(Y[k], V(S(-0.5) * p.s2h[r][k]), t);
+        GM[r] = t;
       }
-      GM[3] = (CT(1) - CT(0.5) * p.soff[0]) * Y[3];
-      GM[4] = (CT(1) - CT(0.5) * p.soff[1]) * Y[4];
-      GM[5] = (CT(1) - CT(0.5) * p.soff[2]) * Y[5];
+      GM[3] = Y[3] * V(S(1) - S(0.5) * p.soff[0]);
+      GM[4] = Y[4] * V(S(1) - S(0.5) * p.soff[1]);
+      GM[5] = Y[5] * V(S(1) - S(0.5) * p.soff[2]);
     } else {
-      const CT bp = p.kind == KIND_NCDE_LINEAR ? CT(1) : mc.rho;   // B' = u bp
+      const V bp = p.kind == KIND_NCDE_LINEAR ? V(1.0f) : mc.rho;   // B' = u bp
 #pragma unroll
-      for (int al = 0; al < 3; ++al) GB[al] = (CT(1) - CT(0.5) * p.s1[al]) * p.advh[al] * bp * p.source;
+      for (int al = 0; al < 3; ++al) GB[al] = bp * V((S(1) - S(0.5) * p.s1[al]) * p.advh[al] * p.source);
     }
   }
-  const CT zero3[3] = {CT(0), CT(0), CT(0)};
-  const CT zero6[6] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
-  const CT hdt = CT(0.5) * p.dt;
+  const V zero3[3] = {V(0.0f), V(0.0f), V(0.0f)};
+  const V zero6[6] = {V(0.0f), V(0.0f), V(0.0f), V(0.0f), V(0.0f), V(0.0f)};
+  const S hdt = S(0.5) * p.dt;
 
   // X = m^ne + dt m_F / 2 ; q becomes m(delta) + dt (m_G + m_F)
-  CT X[3][3][NZ];
+  V X[3][3][NZ];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int c = 0; c < NZ; ++c) {
-        if (absent<LAT>(a, b, c)) { X[a][b][c] = CT(0); continue; }
-        const CT meq = meq_moment<LAT>(a, b, c, mc.dA, mc.B, mc.M, p);
+        if (absent<LAT>(a, b, c)) { X[a][b][c] = V(0.0f); continue; }
+        const V meq = meq_moment<LAT>(a, b, c, mc.dA, mc.B, mc.M, p);
         X[a][b][c] = q.v[a][b][c] - meq;
         if constexpr (FORCED) {
-          const CT mF = meq_moment<LAT>(a, b, c, FA, FB, FM, p);
-          const CT mG = nse ? meq_moment<LAT>(a, b, c, CT(0), zero3, GM, p)
-                            : meq_moment<LAT>(a, b, c, CT(0), GB, zero6, p);
-          X[a][b][c] += hdt * mF;
-          q.v[a][b][c] += p.dt * (mG + mF);
+          const V mF = meq_moment<LAT>(a, b, c, FA, FB, FM, p);
+          const V mG = NSE ? meq_moment<LAT>(a, b, c, V(0.0f), zero3, GM, p)
+                           : meq_moment<LAT>(a, b, c, V(0.0f), GB, zero6, p);
+          X[a][b][c] = fmav(mF, V(hdt), X[a][b][c]);
+          q.v[a][b][c] = fmav(mG + mF, V(p.dt), q.v[a][b][c]);
         }
       }
   if constexpr (CENTRAL) {
-    Cube<LAT, CT> k;
+    Cube<LAT, V> k;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -368,40 +452,17 @@ __device__ __forceinline__ void collide(Cube<LAT, CT>& q, const KParams<CT>& p) 
 #pragma unroll
         for (int c = 0; c < NZ; ++c) k.v[a][b][c] = X[a][b][c];
     k.template shift<false>(mc.u);
-    CT SX[3][3][NZ];
+    Cube<LAT, V> sk;
+    relax<LAT, NSE, false>(sk.v, k.v, p);
+    sk.template shift<true>(mc.u);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int c = 0; c < NZ; ++c) SX[a][b][c] = relax<LAT>(a, b, c, k.v, p);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < NZ; ++c) k.v[a][b][c] = SX[a][b][c];
-    k.template shift<true>(mc.u);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < NZ; ++c) q.v[a][b][c] -= k.v[a][b][c];
+        for (int c = 0; c < NZ; ++c) q.v[a][b][c] -= sk.v[a][b][c];
   } else {
-    CT SX[3][3][NZ];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < NZ; ++c) SX[a][b][c] = relax<LAT>(a, b, c, X, p);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < NZ; ++c) q.v[a][b][c] -= SX[a][b][c];
+    relax<LAT, NSE, true>(q.v, X, p);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -409,17 +470,22 @@ __device__ __forceinline__ void collide(Cube<LAT, CT>& q, const KParams<CT>& p) 
     for (int b = 0; b < 3; ++b)
 #pragma unroll
       for (int c = 0; c < NZ; ++c)
-        if (absent<LAT>(a, b, c)) q.v[a][b][c] = CT(0);
+        if (absent<LAT>(a, b, c)) q.v[a][b][c] = V(0.0f);
   q.inverse();
 }
 
 template <int LAT>
 __device__ __forceinline__ constexpr int zi(int ez) { return Lat<LAT>::NZ == 3 ? ez + 1 : 0; }
 
+// Storage scaling: 16-bit populations are stored times a power of two near
+// 1/omega_j (for range); 32/64-bit ones unscaled.
+template <typename ST>
+__device__ __forceinline__ constexpr bool scaled_storage() { return sizeof(ST) == 2; }
+
 // ------------------------------------------------------------------ kernels
 // One time step: pull gather from fin (post-collision of the previous step,
 // x - e_j), collide, store the post-collision state of node x in fout.
-template <int LAT, typename ST, typename CT, bool CENTRAL, bool FORCED>
+template <int LAT, typename ST, typename CT, bool CENTRAL, bool FORCED, bool NSE>
 __global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, ST* __restrict__ fout,
                                                    const KParams<CT> p) {
   using L = Lat<LAT>;
@@ -442,14 +508,18 @@ __global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, S
     const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
     const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
     const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
-    q.v[ex + 1][ey + 1][zi<LAT>(ez)] = load_st<ST, CT>(fin + j * N + idx) * p.sinv[j];
+    CT v = load_st<ST, CT>(fin + j * N + idx);
+    if constexpr (scaled_storage<ST>()) v *= p.sinv[j];
+    q.v[ex + 1][ey + 1][zi<LAT>(ez)] = v;
   });
-  collide<LAT, CT, CENTRAL, FORCED>(q, p);
+  collide<LAT, CENTRAL, FORCED, NSE>(q, p);
   const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-    store_st<ST, CT>(fout + j * N + own, q.v[ex + 1][ey + 1][zi<LAT>(ez)] * p.sc[j]);
+    CT v = q.v[ex + 1][ey + 1][zi<LAT>(ez)];
+    if constexpr (scaled_storage<ST>()) v *= p.sc[j];
+    store_st<ST, CT>(fout + j * N + own, v);
   });
 }
 
@@ -498,11 +568,14 @@ __device__ __forceinline__ void store_pair<__nv_bfloat16, float>(__nv_bfloat16* 
 // For e_x = -1 it needs (x0 + 1, x0 + 2) symmetrically from the lane above,
 // the last lane of a warp or of a row loading x0 + 2 itself (periodic wrap).
 // Every lane takes part in the shuffles; lanes past the row end clamp their
-// loads to the last pair and store nothing.
-template <int LAT, typename ST, typename CT, bool CENTRAL, bool FORCED>
-__global__ void __launch_bounds__(128) step_kernel_x2(const ST* __restrict__ fin, ST* __restrict__ fout,
-                                                      const KParams<CT> p) {
+// loads to the last pair and store nothing.  With FP32 compute the pair is
+// collided as one F2 value (packed FP32 arithmetic); FP64 collides the two
+// nodes one after the other.
+template <int LAT, typename ST, typename CT, bool CENTRAL, bool FORCED, bool NSE>
+__global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), CENTRAL>::X2_MIN_BLOCKS)
+    step_kernel_x2(const ST* __restrict__ fin, ST* __restrict__ fout, const KParams<CT> p) {
   using L = Lat<LAT>;
+  constexpr bool PACKED = std::is_same<CT, float>::value;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int x0 = 2 * t;
   const bool active = x0 < p.nx;
@@ -513,47 +586,69 @@ __global__ void __launch_bounds__(128) step_kernel_x2(const ST* __restrict__ fin
   const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
   const bool fix_lo = lane == 0;                       // needs x0 - 1 from memory
   const bool fix_hi = lane == 31 || xc + 2 >= p.nx;    // needs x0 + 2 from memory
-  const int x_lo = xc == 0 ? p.nx - 1 : xc - 1;
-  const int x_hi = xc + 2 >= p.nx ? 0 : xc + 2;
+  const int d_lo = (xc == 0 ? p.nx - 1 : xc - 1) - xc; // offsets of x0 - 1, x0 + 2 from x0
+  const int d_hi = (xc + 2 >= p.nx ? 0 : xc + 2) - xc;
   const size_t N = p.N;
-  Cube<LAT, CT> qa, qb;
+  // 32-bit offsets of the source rows (y - e_y, z - e_z) plus x0 (N < 2^31)
+  int roff[3][Lat<LAT>::NZ];
+#pragma unroll
+  for (int ey = -1; ey <= 1; ++ey)
+#pragma unroll
+    for (int ez = -1; ez <= 1; ++ez) {
+      if (Lat<LAT>::NZ == 1 && ez != 0) continue;
+      const int sy = Nbr::up(ey, ym, y, yp), sz = Nbr::up(ez, zm, z, zp);
+      roff[ey + 1][zi<LAT>(ez)] = (sz * p.ny + sy) * p.nx + xc;
+    }
+  using V = typename std::conditional<PACKED, F2, CT>::type;
+  Cube<LAT, V> qa, qb;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int c = 0; c < L::NZ; ++c) { qa.v[a][b][c] = CT(0); qb.v[a][b][c] = CT(0); }
+      for (int c = 0; c < L::NZ; ++c) { qa.v[a][b][c] = V(0.0f); qb.v[a][b][c] = V(0.0f); }
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-    const int sy = Nbr::up(ey, ym, y, yp);
-    const int sz = Nbr::up(ez, zm, z, zp);
-    const ST* row = fin + j * N + (size_t(sz) * p.ny + sy) * p.nx;
+    const ST* src = fin + j * N + roff[ey + 1][zi<LAT>(ez)];
     CT lo, hi, va, vb;
-    load_pair<ST, CT>(row + xc, lo, hi);
+    load_pair<ST, CT>(src, lo, hi);
     if constexpr (ex == 0) {
       va = lo; vb = hi;
     } else if constexpr (ex == 1) {
       CT prev = __shfl_up_sync(0xffffffffu, hi, 1);
-      if (fix_lo) prev = load_st<ST, CT>(row + x_lo);
+      if (fix_lo) prev = load_st<ST, CT>(src + d_lo);
       va = prev; vb = lo;
     } else {
       CT next = __shfl_down_sync(0xffffffffu, lo, 1);
-      if (fix_hi) next = load_st<ST, CT>(row + x_hi);
+      if (fix_hi) next = load_st<ST, CT>(src + d_hi);
       va = hi; vb = next;
     }
-    qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = va * p.sinv[j];
-    qb.v[ex + 1][ey + 1][zi<LAT>(ez)] = vb * p.sinv[j];
+    if constexpr (scaled_storage<ST>()) { va *= p.sinv[j]; vb *= p.sinv[j]; }
+    if constexpr (PACKED) {
+      qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = V(va, vb);
+    } else {
+      qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = va;
+      qb.v[ex + 1][ey + 1][zi<LAT>(ez)] = vb;
+    }
   });
-  collide<LAT, CT, CENTRAL, FORCED>(qa, p);
-  collide<LAT, CT, CENTRAL, FORCED>(qb, p);
+  collide<LAT, CENTRAL, FORCED, NSE>(qa, p);
+  if constexpr (!PACKED) collide<LAT, CENTRAL, FORCED, NSE>(qb, p);
   if (!active) return;
-  const size_t own = (size_t(z) * p.ny + y) * p.nx + x0;
+  const int own = (z * p.ny + y) * p.nx + x0;
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-    store_pair<ST, CT>(fout + j * N + own, qa.v[ex + 1][ey + 1][zi<LAT>(ez)] * p.sc[j],
-                       qb.v[ex + 1][ey + 1][zi<LAT>(ez)] * p.sc[j]);
+    CT va, vb;
+    if constexpr (PACKED) {
+      const F2 r = qa.v[ex + 1][ey + 1][zi<LAT>(ez)];
+      va = r.v.x; vb = r.v.y;
+    } else {
+      va = qa.v[ex + 1][ey + 1][zi<LAT>(ez)];
+      vb = qb.v[ex + 1][ey + 1][zi<LAT>(ez)];
+    }
+    if constexpr (scaled_storage<ST>()) { va *= p.sc[j]; vb *= p.sc[j]; }
+    store_pair<ST, CT>(fout + j * N + own, va, vb);
   });
 }
 

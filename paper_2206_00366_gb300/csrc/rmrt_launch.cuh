@@ -8,27 +8,34 @@
 
 namespace rmrt {
 
+template <int LAT, typename ST, typename CT, bool NSE>
+static void launch_step(const LaunchArgs& a, const KParams<CT>& p, const ST* fin, ST* fout) {
+  if (a.pairs) {
+    if (a.central) {
+      if (p.forced) step_kernel_x2<LAT, ST, CT, true, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+      else step_kernel_x2<LAT, ST, CT, true, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+    } else {
+      if (p.forced) step_kernel_x2<LAT, ST, CT, false, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+      else step_kernel_x2<LAT, ST, CT, false, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+    }
+  } else if (a.central) {
+    if (p.forced) step_kernel<LAT, ST, CT, true, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+    else step_kernel<LAT, ST, CT, true, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+  } else {
+    if (p.forced) step_kernel<LAT, ST, CT, false, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+    else step_kernel<LAT, ST, CT, false, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+  }
+}
+
 template <int LAT, typename ST, typename CT>
 static cudaError_t launch_typed(const LaunchArgs& a, const KParams<CT>& p) {
   switch (a.op) {
     case OP_STEP: {
       const ST* fin = static_cast<const ST*>(a.fin);
       ST* fout = static_cast<ST*>(a.fout);
-      if (a.pairs) {
-        if (a.central) {
-          if (p.forced) step_kernel_x2<LAT, ST, CT, true, true><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-          else step_kernel_x2<LAT, ST, CT, true, false><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-        } else {
-          if (p.forced) step_kernel_x2<LAT, ST, CT, false, true><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-          else step_kernel_x2<LAT, ST, CT, false, false><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-        }
-      } else if (a.central) {
-        if (p.forced) step_kernel<LAT, ST, CT, true, true><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-        else step_kernel<LAT, ST, CT, true, false><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-      } else {
-        if (p.forced) step_kernel<LAT, ST, CT, false, true><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-        else step_kernel<LAT, ST, CT, false, false><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-      }
+      const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
+      if (nse) launch_step<LAT, ST, CT, true>(a, p, fin, fout);
+      else launch_step<LAT, ST, CT, false>(a, p, fin, fout);
       break;
     }
     case OP_INIT_EQ:
@@ -49,15 +56,12 @@ static cudaError_t launch_typed(const LaunchArgs& a, const KParams<CT>& p) {
   return cudaGetLastError();
 }
 
-template <int LAT>
-static cudaError_t launch_lattice(const LaunchArgs& a) {
-  switch (a.storage) {
-    case ST_F64: return launch_typed<LAT, double, double>(a, *a.kp64);
-    case ST_F32: return launch_typed<LAT, float, float>(a, *a.kp32);
-    case ST_F16: return launch_typed<LAT, __half, float>(a, *a.kp32);
-    case ST_BF16: return launch_typed<LAT, __nv_bfloat16, float>(a, *a.kp32);
-    default: return cudaErrorInvalidValue;
-  }
+// Storage dispatch of one lattice; the typed launchers live in one
+// translation unit per (lattice, storage) so that they compile in parallel.
+template <int LAT, typename ST>
+cudaError_t launch_storage(const LaunchArgs& a) {
+  if constexpr (std::is_same<ST, double>::value) return launch_typed<LAT, double, double>(a, *a.kp64);
+  else return launch_typed<LAT, ST, float>(a, *a.kp32);
 }
 
 }  // namespace rmrt

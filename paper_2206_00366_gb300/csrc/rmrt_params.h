@@ -58,9 +58,15 @@ struct LaunchArgs {
   cudaStream_t stream;
 };
 
-cudaError_t launch_d2q9(const LaunchArgs& a);
-cudaError_t launch_d3q19(const LaunchArgs& a);
-cudaError_t launch_d3q27(const LaunchArgs& a);
+#define RMRT_DECLARE_LAUNCH(lat) \
+  cudaError_t launch_##lat##_f64(const LaunchArgs& a); \
+  cudaError_t launch_##lat##_f32(const LaunchArgs& a); \
+  cudaError_t launch_##lat##_f16(const LaunchArgs& a); \
+  cudaError_t launch_##lat##_bf16(const LaunchArgs& a);
+RMRT_DECLARE_LAUNCH(d2q9)
+RMRT_DECLARE_LAUNCH(d3q19)
+RMRT_DECLARE_LAUNCH(d3q27)
+#undef RMRT_DECLARE_LAUNCH
 cudaError_t launch_finalize(const double* partials, size_t nblk, double* out, cudaStream_t s);
 
 }  // namespace rmrt

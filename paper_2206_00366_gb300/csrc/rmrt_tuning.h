@@ -1,0 +1,54 @@
+// Launch-shape constants of the step kernels, chosen by measurement on
+// GB300 (kernels).  Each may be overridden with -D at build
+// time to compare alternatives.
+#pragma once
+
+// Minimum resident 128-thread blocks per SM requested from the compiler for
+// the two-nodes-per-thread step kernel; this caps registers at
+// 65536 / (128 * n), and 1 leaves the count to the compiler.  Measured on
+// the full-size workloads with packed FP32 collision (GB/s of the step
+// kernel, best setting first):
+//   rD2Q9  FP32 12: 6665      16-bit  1: 5066 (12: 4944)
+//   rD3Q19 FP32  6: 6842 raw, 6396 central (1: 4941 central)
+//          16-bit raw 8: 5448, central 6: 4303 (8: 4088)
+//   rD3Q27 FP32  5: 6899 raw, 6312 central (1: 6230 / 4431)
+//          16-bit raw 6: 5447, central 5: 4276 (6: 3619)
+// FP64 (the correctness path) is left to the compiler.
+#ifndef RMRT_X2_MINB_D2Q9_W4
+#define RMRT_X2_MINB_D2Q9_W4 12
+#endif
+#ifndef RMRT_X2_MINB_D2Q9_W2
+#define RMRT_X2_MINB_D2Q9_W2 1
+#endif
+#ifndef RMRT_X2_MINB_D3Q19_W4
+#define RMRT_X2_MINB_D3Q19_W4 6
+#endif
+#ifndef RMRT_X2_MINB_D3Q19_W2
+#define RMRT_X2_MINB_D3Q19_W2 8
+#endif
+#ifndef RMRT_X2_MINB_D3Q19_W2_CENTRAL
+#define RMRT_X2_MINB_D3Q19_W2_CENTRAL 6
+#endif
+#ifndef RMRT_X2_MINB_D3Q27_W4
+#define RMRT_X2_MINB_D3Q27_W4 5
+#endif
+#ifndef RMRT_X2_MINB_D3Q27_W2
+#define RMRT_X2_MINB_D3Q27_W2 6
+#endif
+#ifndef RMRT_X2_MINB_D3Q27_W2_CENTRAL
+#define RMRT_X2_MINB_D3Q27_W2_CENTRAL 5
+#endif
+
+namespace rmrt {
+// LAT: lattice; BYTES: size of one stored population; CENTRAL: basis.
+template <int LAT, int BYTES, bool CENTRAL>
+struct Tuning {
+  static constexpr int X2_MIN_BLOCKS =
+      BYTES == 8 ? 1
+      : LAT == 0 ? (BYTES == 4 ? RMRT_X2_MINB_D2Q9_W4 : RMRT_X2_MINB_D2Q9_W2)
+      : LAT == 1 ? (BYTES == 4 ? RMRT_X2_MINB_D3Q19_W4
+                               : (CENTRAL ? RMRT_X2_MINB_D3Q19_W2_CENTRAL : RMRT_X2_MINB_D3Q19_W2))
+                 : (BYTES == 4 ? RMRT_X2_MINB_D3Q27_W4
+                               : (CENTRAL ? RMRT_X2_MINB_D3Q27_W2_CENTRAL : RMRT_X2_MINB_D3Q27_W2));
+};
+}  // namespace rmrt
