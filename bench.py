@@ -38,9 +38,11 @@ VARIANTS = [
     ("rD3Q19-raw-f32", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "raw", "nse"),
     ("rD3Q19-central-f32", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "central", "nse"),
     ("rD3Q19-raw-f16", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "raw", "nse"),
+    ("rD3Q19-central-f16", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "central", "nse"),
     ("rD3Q27-raw-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "raw", "nse"),
     ("rD3Q27-central-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "central", "nse"),
     ("rD3Q27-raw-f16", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "raw", "nse"),
+    ("rD3Q27-central-f16", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "central", "nse"),
 ]
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 ESIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
