@@ -24,7 +24,7 @@ __global__ void init_eq_kernel(ST* __restrict__ f, const double* __restrict__ rh
   const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
   const CT r = CT(rho[own]);
   CT uh[3] = {CT(0), CT(0), CT(0)};
-  for (int al = 0; al < D; ++al) uh[al] = nse ? CT(u[al * N + own] / double(p.c[al])) : p.advh[al];
+  for (int al = 0; al < D; ++al) uh[al] = nse ? CT(u[al * N + own]) / p.c[al] : p.advh[al];
   Macro<CT> mc;
   mc.dA = CT(rho[own] - double(p.rho0));
   mc.rho = r;
@@ -84,7 +84,7 @@ __global__ void plane_kernel(ST* __restrict__ f, double* __restrict__ plane, int
 // sums per block: [0] sum drho, [1..3] momentum, [4] kinetic energy,
 // [5] sum |u - u_prev|^2, [6] sum |u|^2, [7] unused.
 constexpr int CHECK_THREADS = 256;
-constexpr int CHECK_MAX_BLOCKS = 1024;
+constexpr int CHECK_MAX_BLOCKS = 4096;
 
 template <int LAT, typename ST, typename CT>
 __global__ void __launch_bounds__(CHECK_THREADS) check_kernel(
@@ -97,10 +97,13 @@ __global__ void __launch_bounds__(CHECK_THREADS) check_kernel(
   int flag = 0;
   const size_t N = p.N;
   const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
-  for (size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x; n < N; n += size_t(gridDim.x) * blockDim.x) {
-    const int x = int(n % p.nx);
-    const size_t r = n / p.nx;
-    const int y = int(r % p.ny), z = int(r / p.ny);
+  // grid-stride over nodes with the coordinates advanced by carries (no
+  // per-node integer division)
+  const size_t G = size_t(gridDim.x) * blockDim.x;
+  const size_t n0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int gx = int(G % p.nx), gy = int((G / p.nx) % p.ny), gz = int(G / (size_t(p.nx) * p.ny));
+  int x = int(n0 % p.nx), y = int((n0 / p.nx) % p.ny), z = int(n0 / (size_t(p.nx) * p.ny));
+  for (size_t n = n0; n < N; n += G) {
     const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
     // per-node arithmetic in the compute type; only the sums are FP64
     CT s0 = CT(0), s1[3] = {CT(0), CT(0), CT(0)};
@@ -148,6 +151,11 @@ __global__ void __launch_bounds__(CHECK_THREADS) check_kernel(
     if (!(drho == drho) || !(u2 == u2) || isinf(double(drho)) || isinf(double(u2))) flag |= 1;
     if (nse && rho <= CT(0)) flag |= 2;
     if (nse && u2 >= p.cs2) flag |= 4;
+    x += gx;
+    if (x >= p.nx) { x -= p.nx; ++y; }
+    y += gy;
+    if (y >= p.ny) { y -= p.ny; ++z; }
+    z += gz;
   }
   if (partials) {
     // warp then block reduction in FP64, fixed order (deterministic)

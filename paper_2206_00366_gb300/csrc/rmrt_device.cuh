@@ -624,10 +624,11 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), CENTRAL>::X2
       if (fix_hi) next = load_st<ST, CT>(src + d_hi);
       va = hi; vb = next;
     }
-    if constexpr (scaled_storage<ST>()) { va *= p.sinv[j]; vb *= p.sinv[j]; }
     if constexpr (PACKED) {
-      qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = V(va, vb);
+      if constexpr (scaled_storage<ST>()) qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = V(va, vb) * V(p.sinv[j]);
+      else qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = V(va, vb);
     } else {
+      if constexpr (scaled_storage<ST>()) { va *= p.sinv[j]; vb *= p.sinv[j]; }
       qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = va;
       qb.v[ex + 1][ey + 1][zi<LAT>(ez)] = vb;
     }
@@ -641,13 +642,14 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), CENTRAL>::X2
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
     CT va, vb;
     if constexpr (PACKED) {
-      const F2 r = qa.v[ex + 1][ey + 1][zi<LAT>(ez)];
+      F2 r = qa.v[ex + 1][ey + 1][zi<LAT>(ez)];
+      if constexpr (scaled_storage<ST>()) r = r * V(p.sc[j]);
       va = r.v.x; vb = r.v.y;
     } else {
       va = qa.v[ex + 1][ey + 1][zi<LAT>(ez)];
       vb = qb.v[ex + 1][ey + 1][zi<LAT>(ez)];
+      if constexpr (scaled_storage<ST>()) { va *= p.sc[j]; vb *= p.sc[j]; }
     }
-    if constexpr (scaled_storage<ST>()) { va *= p.sc[j]; vb *= p.sc[j]; }
     store_pair<ST, CT>(fout + j * N + own, va, vb);
   });
 }
