@@ -201,6 +201,76 @@ int rmrtlb_stats(rmrtlb_t solver, double out[8]);
  * rmrtlb_stats; out[6] = -1 if none ran yet).  Synchronises the stream. */
 int rmrtlb_last_check(rmrtlb_t solver, double out[8]);
 
+/* ------------------------------------------------------ batched cavities */
+/* Many independent rD2Q9 NSE domains advanced together (SURVEY config 4):
+ * each a closed rectangle of nx x ny nodes with half-way bounce-back walls
+ * half a spacing outside the first and last nodes, the top wall (beyond
+ * y = ny - 1) moving along x with lid_u.  A population whose source lies
+ * outside the domain is the node's own post-collision population in the
+ * opposite direction; crossing the lid it gains 2 omega_j rho0 (c_j . U) /
+ * c_s^2, the linear term of the REDF (Eq. 3-3).  Every node collides as in
+ * rmrtlb_step (Eq. 2-2-3, raw moments, unforced NSE), with its domain's
+ * own spacing, c_s^2 (<= 0: min(dx, dy)^2 / 3), weights (Eq. 3-3-5) and
+ * rates (Eq. 4-31, Eq. 5-8-1).  The paper has no boundaries; the wall rule
+ * is the standard half-way bounce-back. */
+typedef struct {
+    int nx, ny;
+    double dx, dy;       /* spacings; lattice units, dt = 1 */
+    double nu, nu_bulk;  /* kinematic and bulk viscosity */
+    double s_free;       /* rate of every moment of order >= 3 */
+    double lid_u;        /* lid velocity (along +x) on the top wall */
+    double cs2;          /* <= 0 selects min(dx, dy)^2 / 3 */
+} rmrtlb_domain;
+
+typedef struct rmrtlb_batch* rmrtlb_batch_t;
+
+/* Workspace bytes for these domains (storage RMRTLB_ST_F32 or _F64).
+ * Host only. */
+int rmrtlb_batch_workspace_bytes(int ndomains, const rmrtlb_domain* domains,
+                                 int storage, size_t* bytes);
+
+/* Bind a batch to the caller's workspace (device, 256-byte aligned, owned
+ * by the caller).  Every domain starts at rest (rho0, u = 0).  Every
+ * check_every steps (rounded up to even) the FP64 residual
+ * ||u(t) - u(t - check_every)||_2 / ||u(t)||_2 of each domain is formed; a
+ * domain whose residual falls below tol retires: it is no longer stepped
+ * and keeps its state.  With a non-NULL stream, each chunk of check_every
+ * steps plus its check is captured once as a CUDA graph and replayed; the
+ * legacy NULL stream launches directly (capture needs a created stream).
+ * The tile list starts with 128-node row tiles (see rmrtlb_batch_tune). */
+int rmrtlb_batch_create(rmrtlb_batch_t* batch, int ndomains,
+                        const rmrtlb_domain* domains, int storage, double rho0,
+                        int check_every, double tol, void* workspace,
+                        size_t workspace_bytes, void* stream);
+int rmrtlb_batch_destroy(rmrtlb_batch_t batch);
+
+/* Every domain back at rest, active, step 0. */
+int rmrtlb_batch_reset(rmrtlb_batch_t batch);
+
+/* Time `steps` steps with each tile width (32, 64, 128, 256 nodes per
+ * row tile and threads per block), keep the fastest, then reset.  Writes
+ * the chosen width. */
+int rmrtlb_batch_tune(rmrtlb_batch_t batch, int steps, int* tile_width);
+
+/* Advance every active domain n steps (asynchronous). */
+int rmrtlb_batch_step(rmrtlb_batch_t batch, int n);
+
+/* Per-domain arrays (any may be NULL): residual of the last check (-1
+ * before the second check), step at which the domain retired (-1 while
+ * active), active flag; *steps_done = steps issued.  Synchronises. */
+int rmrtlb_batch_status(rmrtlb_batch_t batch, double* residual,
+                        long long* steps_to_converge, int* active,
+                        long long* steps_done);
+
+/* Populations fbar_j(x, t) of one domain, 9 FP64 planes of ny*nx in
+ * rmrtlb_lattice_info order, host or device memory.  Synchronise. */
+int rmrtlb_batch_set_populations(rmrtlb_batch_t batch, int domain, const double* f);
+int rmrtlb_batch_get_populations(rmrtlb_batch_t batch, int domain, double* f);
+
+/* rho (one plane) and u (2 planes) of one domain; host or device; either
+ * may be NULL.  Synchronises. */
+int rmrtlb_batch_fields(rmrtlb_batch_t batch, int domain, double* rho, double* u);
+
 /* ------------------------------------------------ allocation-free totals */
 /* The paper has no counterpart to this entry point.  It is for callers that
  * cannot allocate device memory: code whose device memory is owned by

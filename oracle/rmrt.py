@@ -515,15 +515,19 @@ def opposite(lat: Lattice) -> np.ndarray:
     return np.array([int(np.where((e == -e[j]).all(axis=1))[0][0]) for j in range(lat.q)])
 
 
-def stream(lat: Lattice, fstar: np.ndarray, walls: tuple = ()) -> np.ndarray:
+def stream(lat: Lattice, fstar: np.ndarray, walls: tuple = (), lid=None) -> np.ndarray:
     """Propagation f_j(x + c_j dt) = f*_j(x), Eq. (2-2b).
 
     Periodic on every axis, except that an axis listed in `walls` (0 = x,
-    1 = y, 2 = z) is closed by resting walls half a spacing outside its first
-    and last node (half-way bounce-back: a population that would leave
-    through the wall returns to its node in the opposite direction).  The
-    paper treats no boundaries; walls are only used to pin the oracle
-    against the Poiseuille profile.
+    1 = y, 2 = z) is closed by walls half a spacing outside its first and
+    last node (half-way bounce-back: a population that would leave through
+    the wall returns to its node in the opposite direction).  The paper
+    treats no boundaries; walls serve the Poiseuille, Couette and cavity
+    checks.  `lid` = (axis, u_wall, rho_w) makes the wall beyond the last
+    node of that axis move with velocity u_wall: a population j reflected
+    there gains 2 omega_j rho_w (c_j . u_wall) / c_s^2, the linear term of
+    the REDF (Eq. 3-3).  Walls are applied axis by axis in increasing order,
+    so a corner population that crosses the lid gets the lid term.
     """
     out = np.empty_like(fstar)
     for j in range(lat.q):
@@ -533,7 +537,7 @@ def stream(lat: Lattice, fstar: np.ndarray, walls: tuple = ()) -> np.ndarray:
         out[j] = np.roll(fstar[j], shift=sh, axis=(0, 1, 2))
     if walls:
         opp = opposite(lat)
-        for al in walls:
+        for al in sorted(walls):
             ax = 2 - al
             n = fstar.shape[1 + ax]
             for j in range(lat.q):
@@ -543,18 +547,22 @@ def stream(lat: Lattice, fstar: np.ndarray, walls: tuple = ()) -> np.ndarray:
                 first = [slice(None)] * 3
                 first[ax] = 0 if ej > 0 else n - 1
                 # populations arriving at the first (last) node from outside
-                out[j][tuple(first)] = fstar[opp[j]][tuple(first)]
+                val = fstar[opp[j]][tuple(first)]
+                if lid is not None and lid[0] == al and ej < 0:
+                    uw = np.asarray(lid[1], dtype=np.float64)[: lat.d]
+                    val = val + 2.0 * lat.w[j] * lid[2] * float(lat.cv[j] @ uw) / lat.cs2
+                out[j][tuple(first)] = val
     return out
 
 
 def step(lat: Lattice, m: Model, S: np.ndarray, fbar: np.ndarray, nsteps: int = 1,
-         walls: tuple = ()) -> np.ndarray:
+         walls: tuple = (), lid=None) -> np.ndarray:
     """nsteps of collide-and-stream on a field (q, nz, ny, nx)."""
     shape = fbar.shape
     f = fbar
     for _ in range(nsteps):
         fs = collide(lat, m, S, f.reshape(lat.q, -1)).reshape(shape)
-        f = stream(lat, fs, walls)
+        f = stream(lat, fs, walls, lid)
     return f
 
 

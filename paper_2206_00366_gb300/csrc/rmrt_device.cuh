@@ -238,9 +238,14 @@ __device__ __forceinline__ constexpr bool absent(int a, int b, int c) {
 // -c_s^4 M_gg / (c_g^2 - c_s^2) to the physical (2,2,0)-type moments (g
 // the axis with exponent 0), q19h[g] carrying the index scaling.
 // Mh is packed xx, yy, zz, xy, xz, yz.
-template <int LAT, typename V, typename S>
-__device__ __forceinline__ V meq_moment(int a, int b, int c, V A, const V B[3], const V M[6],
-                                        const KParams<S>& p) {
+// Scalar type of a parameter block (KParams<S> or any struct with the same
+// field names).
+template <typename P>
+using PScalar = typename std::remove_cv<typename std::remove_reference<decltype(P::rho0)>::type>::type;
+
+template <int LAT, typename V, typename P>
+__device__ __forceinline__ V meq_moment(int a, int b, int c, V A, const V B[3], const V M[6], const P& p) {
+  using S = PScalar<P>;
   auto mx = [&](int k) -> S { return k == 0 ? S(1) : (k == 1 ? S(0) : p.mu2[0]); };
   auto my = [&](int k) -> S { return k == 0 ? S(1) : (k == 1 ? S(0) : p.mu2[1]); };
   auto mz = [&](int k) -> S { return k == 0 ? S(1) : (k == 1 ? S(0) : p.mu2[2]); };
@@ -272,8 +277,8 @@ __device__ __forceinline__ V meq_moment(int a, int b, int c, V A, const V B[3], 
 
 // Rate of a diagonal moment class (Eq. 5-1 block structure in index units);
 // the order-2 diagonal entries instead use the dense block s2h = D^-1 S_2 D.
-template <typename S>
-__device__ __forceinline__ S diag_rate(int a, int b, int c, const KParams<S>& p) {
+template <typename P>
+__device__ __forceinline__ PScalar<P> diag_rate(int a, int b, int c, const P& p) {
   const int o = a + b + c;
   if (o == 0) return p.s0;
   if (o == 1) return p.s1[a == 1 ? 0 : (b == 1 ? 1 : 2)];
@@ -288,9 +293,10 @@ __device__ __forceinline__ constexpr bool dense_block() {
 // out = out - S X (ACC) or out = S X (!ACC).  For the NSE family orders 0
 // and 1 are conserved: X vanishes there (Eq. 4-18-1 with the dt F / 2 terms
 // of Eq. 2-4-2), so s_0 and S_1 act on zero and are skipped.
-template <int LAT, bool NSE, bool ACC, typename V, typename S>
+template <int LAT, bool NSE, bool ACC, typename V, typename P>
 __device__ __forceinline__ void relax(V (&out)[3][3][Lat<LAT>::NZ], const V (&X)[3][3][Lat<LAT>::NZ],
-                                      const KParams<S>& p) {
+                                      const P& p) {
+  using S = PScalar<P>;
   constexpr int NZ = Lat<LAT>::NZ;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -312,7 +318,7 @@ __device__ __forceinline__ void relax(V (&out)[3][3][Lat<LAT>::NZ], const V (&X)
           if constexpr (NZ == 3) t = fmav(X[0][0][2], V(sg * p.s2h[r][2]), t);
           out[a][b][c] = t;
         } else {
-          const S s = diag_rate(a, b, c, p);
+          const S s = diag_rate<P>(a, b, c, p);
           out[a][b][c] = ACC ? fmav(X[a][b][c], V(-s), out[a][b][c]) : X[a][b][c] * V(s);
         }
       }
@@ -345,8 +351,9 @@ __device__ __forceinline__ void eq_args(Macro<CT>& r, CT rho, const CT uh[3], co
 
 // Conserved fields from the index moments (Eqs. 2-4-1 / 2-4-2).  NSE: the
 // family of the NSE and He-Luo equilibria; otherwise the two NCDE kinds.
-template <int D, bool NSE, typename V, typename S>
-__device__ __forceinline__ Macro<V> macroscopic(V m000, const V jh[3], const KParams<S>& p) {
+template <int D, bool NSE, typename V, typename P>
+__device__ __forceinline__ Macro<V> macroscopic(V m000, const V jh[3], const P& p) {
+  using S = PScalar<P>;
   Macro<V> r;
   const S hdt = S(0.5) * p.dt;
   const V drho = m000 + V(hdt * p.source);
@@ -379,8 +386,9 @@ __device__ __forceinline__ Macro<V> macroscopic(V m000, const V jh[3], const KPa
 // Eq. (2-2-3):
 //   m* - m0 = m(delta) + dt (m_G + m_F) - S (m^ne + dt m_F / 2),
 // central variant: S replaced by N(u)^-1 Sbar N(u) (Eq. 5-1-2).
-template <int LAT, bool CENTRAL, bool FORCED, bool NSE, typename V, typename S>
-__device__ __forceinline__ void collide(Cube<LAT, V>& q, const KParams<S>& p) {
+template <int LAT, bool CENTRAL, bool FORCED, bool NSE, typename V, typename P>
+__device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p) {
+  using S = PScalar<P>;
   constexpr int D = Lat<LAT>::D, NZ = Lat<LAT>::NZ;
   q.forward();
   V jh[3] = {q.v[1][0][0], q.v[0][1][0], V(0.0f)};

@@ -60,6 +60,15 @@ class rmrtlb_params(ctypes.Structure):
     ]
 
 
+class rmrtlb_domain(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+        ("nu", ctypes.c_double), ("nu_bulk", ctypes.c_double),
+        ("s_free", ctypes.c_double), ("lid_u", ctypes.c_double), ("cs2", ctypes.c_double),
+    ]
+
+
 def make_params(**kw) -> rmrtlb_params:
     """rmrtlb_params from keyword arguments (missing fields are zero)."""
     p = rmrtlb_params()
@@ -103,6 +112,18 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_stats": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_last_check": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_population_totals_noalloc": (i, [i, i, i, i, d, d, d, d, _vp, _vp, _vp]),
+        "rmrtlb_batch_workspace_bytes": (i, [i, ctypes.POINTER(rmrtlb_domain), i, ctypes.POINTER(sz)]),
+        "rmrtlb_batch_create": (i, [ctypes.POINTER(_vp), i, ctypes.POINTER(rmrtlb_domain), i, d, i, d, _vp, sz,
+                                    _vp]),
+        "rmrtlb_batch_destroy": (i, [_vp]),
+        "rmrtlb_batch_reset": (i, [_vp]),
+        "rmrtlb_batch_tune": (i, [_vp, i, ctypes.POINTER(i)]),
+        "rmrtlb_batch_step": (i, [_vp, i]),
+        "rmrtlb_batch_status": (i, [_vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]),
+        "rmrtlb_batch_set_populations": (i, [_vp, i, _vp]),
+        "rmrtlb_batch_get_populations": (i, [_vp, i, _vp]),
+        "rmrtlb_batch_fields": (i, [_vp, i, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -116,7 +137,10 @@ def exported_symbols() -> list:
     return ["rmrtlb_strerror", "rmrtlb_lattice_info", "rmrtlb_workspace_bytes", "rmrtlb_create",
             "rmrtlb_destroy", "rmrtlb_get_constants", "rmrtlb_init_equilibrium",
             "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
-            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_population_totals_noalloc"]
+            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_population_totals_noalloc",
+            "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
+            "rmrtlb_batch_tune", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
+            "rmrtlb_batch_get_populations", "rmrtlb_batch_fields"]
 
 
 def _check(status: int, where: str):
@@ -202,6 +226,70 @@ def rmrtlb_population_totals_noalloc(lattice, nx, ny, nz, dx, dy, dz, dt, f: int
            "rmrtlb_population_totals_noalloc")
 
 
+def _domains(domains):
+    arr = (rmrtlb_domain * len(domains))()
+    for k, dd in enumerate(domains):
+        for f, _ in rmrtlb_domain._fields_:
+            setattr(arr[k], f, dd.get(f, 0))
+    return arr
+
+
+def rmrtlb_batch_workspace_bytes(domains, storage: int) -> int:
+    arr = _domains(domains)
+    b = ctypes.c_size_t()
+    _check(lib().rmrtlb_batch_workspace_bytes(len(domains), arr, storage, ctypes.byref(b)),
+           "rmrtlb_batch_workspace_bytes")
+    return b.value
+
+
+def rmrtlb_batch_create(domains, storage, rho0, check_every, tol, workspace: int, workspace_bytes: int,
+                        stream: int):
+    arr = _domains(domains)
+    h = _vp()
+    _check(lib().rmrtlb_batch_create(ctypes.byref(h), len(domains), arr, storage, rho0, check_every, tol,
+                                     workspace, workspace_bytes, stream), "rmrtlb_batch_create")
+    return h
+
+
+def rmrtlb_batch_destroy(h):
+    _check(lib().rmrtlb_batch_destroy(h), "rmrtlb_batch_destroy")
+
+
+def rmrtlb_batch_reset(h):
+    _check(lib().rmrtlb_batch_reset(h), "rmrtlb_batch_reset")
+
+
+def rmrtlb_batch_tune(h, steps: int) -> int:
+    w = ctypes.c_int()
+    _check(lib().rmrtlb_batch_tune(h, steps, ctypes.byref(w)), "rmrtlb_batch_tune")
+    return w.value
+
+
+def rmrtlb_batch_step(h, n: int):
+    _check(lib().rmrtlb_batch_step(h, n), "rmrtlb_batch_step")
+
+
+def rmrtlb_batch_status(h, ndomains: int):
+    res = (ctypes.c_double * ndomains)()
+    conv = (ctypes.c_longlong * ndomains)()
+    act = (ctypes.c_int * ndomains)()
+    done = ctypes.c_longlong()
+    _check(lib().rmrtlb_batch_status(h, res, conv, act, ctypes.byref(done)), "rmrtlb_batch_status")
+    return np.array(res[:]), np.array(conv[:]), np.array(act[:]), done.value
+
+
+def rmrtlb_batch_set_populations(h, domain: int, f: int):
+    _check(lib().rmrtlb_batch_set_populations(h, domain, f), "rmrtlb_batch_set_populations")
+
+
+def rmrtlb_batch_get_populations(h, domain: int, f: int):
+    _check(lib().rmrtlb_batch_get_populations(h, domain, f), "rmrtlb_batch_get_populations")
+
+
+def rmrtlb_batch_fields(h, domain: int, rho: int, u: int):
+    _check(lib().rmrtlb_batch_fields(h, domain, rho, u), "rmrtlb_batch_fields")
+
+
 # ------------------------------------------------------------------ convenience
 def _ptr(x) -> int:
     """Address of a torch tensor or numpy array (must be contiguous float64)."""
@@ -280,3 +368,59 @@ class Solver:
 
     def last_check(self, allow_unstable=False):
         return rmrtlb_last_check(self.h, allow_unstable)
+
+
+class Batch:
+    """Batched lid-driven cavities (rmrtlb_batch_*) on a torch workspace.
+
+    domains: list of dicts with the rmrtlb_domain fields.  A dedicated torch
+    stream is used so that chunks can be captured as CUDA graphs (pass
+    use_graphs=False to launch on the legacy default stream instead).
+    """
+
+    def __init__(self, domains, storage="f32", rho0=1.0, check_every=100, tol=1e-6, device="cuda",
+                 use_graphs=True):
+        import torch
+        self.domains = [dict(d) for d in domains]
+        self.storage = STORAGE_NAMES.get(storage, storage)
+        nbytes = rmrtlb_batch_workspace_bytes(self.domains, self.storage)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = torch.cuda.Stream(device=self.workspace.device) if use_graphs else None
+        sp = self.stream.cuda_stream if use_graphs else 0
+        torch.cuda.synchronize()
+        self.h = rmrtlb_batch_create(self.domains, self.storage, rho0, check_every, tol,
+                                     self.workspace.data_ptr(), nbytes, sp)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.rmrtlb_batch_destroy(h)
+            self.h = None
+
+    def reset(self):
+        rmrtlb_batch_reset(self.h)
+
+    def tune(self, steps=20):
+        return rmrtlb_batch_tune(self.h, steps)
+
+    def step(self, n=1):
+        rmrtlb_batch_step(self.h, n)
+
+    def status(self):
+        return rmrtlb_batch_status(self.h, len(self.domains))
+
+    def set_populations(self, domain, f):
+        rmrtlb_batch_set_populations(self.h, domain, _ptr(f))
+
+    def get_populations(self, domain):
+        d = self.domains[domain]
+        out = np.empty((9, 1, d["ny"], d["nx"]))
+        rmrtlb_batch_get_populations(self.h, domain, _ptr(out))
+        return out
+
+    def fields(self, domain):
+        d = self.domains[domain]
+        rho = np.empty((1, d["ny"], d["nx"]))
+        u = np.empty((2, 1, d["ny"], d["nx"]))
+        rmrtlb_batch_fields(self.h, domain, _ptr(rho), _ptr(u))
+        return rho, u

@@ -1,0 +1,123 @@
+"""Batched lid-driven cavities (rmrtlb_batch_*) against the oracle.
+
+The oracle steps each domain on its own with half-way bounce-back walls on
+both axes and the moving lid (oracle.rmrt.stream with walls and lid); the
+batch must agree domain by domain at the parity tolerances (FP64 1e-12,
+FP32 1e-5)."""
+import numpy as np
+import pytest
+
+import oracle.rmrt as R
+import workloads as W
+from cases import normwise
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2206_00366_gb300 import build
+    build.build()
+
+
+def oracle_domain(d, steps, f0, rho0=1.0):
+    lat = R.make_lattice("D2Q9", (d["dx"], d["dy"]), 1.0, d["cs2"] if d["cs2"] > 0 else None)
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, d["nu"], d["nu_bulk"], d["s_free"]))
+    m = R.Model(R.NSE, rho0=rho0)
+    f = R.step(lat, m, S, f0, steps, walls=(0, 1), lid=(1, (d["lid_u"], 0.0), rho0))
+    return f, R.fields(lat, m, f)
+
+
+DOMAINS = [
+    dict(nx=17, ny=12, dx=1.0, dy=1.0, nu=0.02, nu_bulk=0.02, s_free=1.1, lid_u=0.05, cs2=0.0),
+    dict(nx=24, ny=9, dx=1.0, dy=2.0, nu=0.05, nu_bulk=0.04, s_free=1.2, lid_u=0.04, cs2=0.0),
+    dict(nx=10, ny=21, dx=2.0, dy=1.0, nu=0.03, nu_bulk=0.03, s_free=1.0, lid_u=0.05, cs2=0.0),
+    dict(nx=33, ny=7, dx=1.0, dy=4.0, nu=0.2, nu_bulk=0.2, s_free=1.1, lid_u=0.03, cs2=0.0),
+    dict(nx=8, ny=30, dx=4.0, dy=1.0, nu=0.1, nu_bulk=0.1, s_free=1.1, lid_u=0.05, cs2=0.0),
+    dict(nx=1, ny=5, dx=1.0, dy=0.5, nu=0.02, nu_bulk=0.02, s_free=1.1, lid_u=0.02, cs2=0.0),
+]
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("graphs", [False, True])
+def test_batch_matches_oracle(storage, tol, graphs):
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    b = Batch(DOMAINS, storage=storage, check_every=1000, tol=1e-9, use_graphs=graphs)
+    f0 = [W.random_populations(9, (1, d["ny"], d["nx"]), seed=20 + k) for k, d in enumerate(DOMAINS)]
+    for k in range(len(DOMAINS)):
+        b.set_populations(k, f0[k])
+        assert normwise(b.get_populations(k), f0[k]) <= (1e-6 if storage == "f32" else 1e-15)
+    steps = 25
+    b.step(steps)
+    for k, d in enumerate(DOMAINS):
+        fo, (ro, uo) = oracle_domain(d, steps, f0[k])
+        fg = b.get_populations(k)
+        rg, ug = b.fields(k)
+        assert normwise(fg, fo) <= tol
+        assert normwise(rg, ro) <= tol
+        assert normwise(ug, uo) <= 10 * tol
+
+
+def test_batch_graph_equals_direct():
+    """CUDA-graph chunks and direct launches give bitwise the same state."""
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    doms = W.cavity_domains(12, seed=3, size=(16, 48), re=(50, 200))
+    a = Batch(doms, storage="f32", check_every=20, tol=1e-12, use_graphs=True)
+    b = Batch(doms, storage="f32", check_every=20, tol=1e-12, use_graphs=False)
+    a.step(130)
+    b.step(130)
+    for k in range(len(doms)):
+        np.testing.assert_array_equal(a.get_populations(k), b.get_populations(k))
+    ra, _, _, sa = a.status()
+    rb, _, _, sb = b.status()
+    assert sa == sb == 130
+    np.testing.assert_array_equal(ra, rb)
+
+
+def test_batch_converges_and_retires():
+    """Small low-Re cavities run to residual 1e-6: each retires at a check,
+    keeps its state afterwards, and its state equals the oracle's after the
+    same number of steps."""
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    doms = [dict(nx=12, ny=10, dx=1.0, dy=0.5, nu=0.1, nu_bulk=0.1, s_free=1.1, lid_u=0.05, cs2=0.0),
+            dict(nx=16, ny=8, dx=1.0, dy=1.0, nu=0.08, nu_bulk=0.08, s_free=1.1, lid_u=0.05, cs2=0.0),
+            dict(nx=10, ny=14, dx=2.0, dy=1.0, nu=0.15, nu_bulk=0.15, s_free=1.1, lid_u=0.05, cs2=0.0)]
+    b = Batch(doms, storage="f64", check_every=100, tol=1e-6)
+    for _ in range(60):
+        b.step(100)
+        res, conv, act, done = b.status()
+        if not act.any():
+            break
+    assert not act.any(), (res, conv)
+    assert (conv > 0).all() and (conv % 100 == 0).all()
+    for k, d in enumerate(doms):
+        f_before = b.get_populations(k)
+        b.step(100)                      # retired domains are not stepped
+        np.testing.assert_array_equal(b.get_populations(k), f_before)
+        f0 = np.zeros((9, 1, d["ny"], d["nx"]))
+        lat = R.make_lattice("D2Q9", (d["dx"], d["dy"]))
+        f0 += lat.w.reshape(9, 1, 1, 1)          # rest state at rho0 = 1
+        errs = {}
+        for dk in (-100, 0, 100):
+            fo, (ro, uo) = oracle_domain(d, int(conv[k]) + dk, f0)
+            errs[dk] = normwise(f_before, fo)
+        assert errs[0] <= 1e-11, (k, int(conv[k]), errs)
+    # the lid drives the flow: mean x velocity near the lid is positive
+    rho, u = b.fields(0)
+    assert u[0, 0, -1, :].mean() > 0
+
+
+def test_batch_tune_picks_a_width_and_resets():
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    doms = W.cavity_domains(20, seed=4, size=(20, 80))
+    b = Batch(doms, storage="f32", check_every=100, tol=1e-6)
+    b.step(10)
+    w = b.tune(5)
+    assert w in (32, 64, 128, 256)
+    res, conv, act, done = b.status()
+    assert done == 0 and act.all()
+    z = b.get_populations(0)
+    lat = R.make_lattice("D2Q9", (doms[0]["dx"], doms[0]["dy"]))
+    np.testing.assert_allclose(z, lat.w.reshape(9, 1, 1, 1) * np.ones_like(z), rtol=1e-6)

@@ -137,3 +137,21 @@ def random_fields(shape, d, seed, rho0=1.0, drho=0.01, umax=0.03):
     rho = rho0 + drho * rng.uniform(-1, 1, size=shape)
     u = umax * rng.uniform(-1, 1, size=(d,) + tuple(shape))
     return rho, u
+
+
+def cavity_domains(n, seed, size=(32, 512), ratios=(0.25, 0.5, 1.0, 2.0, 4.0), re=(100.0, 1000.0),
+                   lid=0.05, s_free=1.1):
+    """Seeded lid-driven cavities: nx, ny uniform in `size`, dy/dx drawn from
+    `ratios` with the smaller spacing 1, Reynolds number uniform in `re`
+    (Re = lid * nx * dx / nu), bulk viscosity equal to nu.  Returns a list of
+    dicts with the fields of rmrtlb_domain."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx, ny = (int(v) for v in rng.integers(size[0], size[1] + 1, size=2))
+        r = float(rng.choice(ratios))
+        dx, dy = (1.0, r) if r >= 1 else (1.0 / r, 1.0)
+        Re = float(rng.uniform(*re))
+        nu = lid * nx * dx / Re
+        out.append(dict(nx=nx, ny=ny, dx=dx, dy=dy, nu=nu, nu_bulk=nu, s_free=s_free, lid_u=lid, cs2=0.0))
+    return out
