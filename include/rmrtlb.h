@@ -257,7 +257,9 @@ int rmrtlb_batch_step(rmrtlb_batch_t batch, int n);
 
 /* Per-domain arrays (any may be NULL): residual of the last check (-1
  * before the second check), step at which the domain retired (-1 while
- * active), active flag; *steps_done = steps issued.  Synchronises. */
+ * stepping), state: 1 stepping, 0 converged (residual < tol), -1 unstable
+ * (a non-finite velocity or |u| >= c_s at a check: retired so that it
+ * cannot spoil the batch); *steps_done = steps issued.  Synchronises. */
 int rmrtlb_batch_status(rmrtlb_batch_t batch, double* residual,
                         long long* steps_to_converge, int* active,
                         long long* steps_done);

@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(256) batch_check_kernel(const ST* __restrict__
                                                           double* __restrict__ partials, int only_domain,
                                                           double* __restrict__ fields) {
   const int4 t = tiles[blockIdx.x];
-  __shared__ double red[3][8];
-  double acc[3] = {0, 0, 0};
+  __shared__ double red[4][8];
+  double acc[4] = {0, 0, 0, 0};
   const bool run = only_domain < 0 ? (active[t.x] != 0) : (t.x == only_domain);
   if (run) {
     __shared__ BParams<CT> sp;
@@ -151,49 +151,60 @@ __global__ void __launch_bounds__(256) batch_check_kernel(const ST* __restrict__
         acc[0] = dx * dx + dy * dy;
         acc[1] = ux * ux + uy * uy;
         acc[2] = double(s0);
+        acc[3] = isfinite(acc[1]) && isfinite(acc[2]) ? acc[1] : INFINITY;
       }
     }
   }
   if (fields) return;
-  // block reduction in a fixed order (blockDim is a multiple of 32, <= 256)
+  // block reduction in a fixed order (blockDim is a multiple of 32, <= 256);
+  // sums for [0..2], maximum for [3]
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 4; ++k)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v = __shfl_down_sync(0xffffffffu, acc[k], o);
+      acc[k] = k < 3 ? acc[k] + v : fmax(acc[k], v);
+    }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) red[k][warp] = acc[k];
+    for (int k = 0; k < 4; ++k) red[k][warp] = acc[k];
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < 4) {
     double s = 0;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+    for (int w = 0; w < int(blockDim.x >> 5); ++w)
+      s = threadIdx.x < 3 ? s + red[threadIdx.x][w] : fmax(s, red[threadIdx.x][w]);
     partials[size_t(blockIdx.x) * 4 + threadIdx.x] = s;
   }
 }
 
 // One block per domain: fixed-order sum of its tiles' partials, residual,
-// retirement.  status: [0] residual, [1] mass deviation; conv[d] = check
-// index at which the domain retired (-1 while active).
+// retirement.  status: [0] residual, [1] mass deviation.  active[d]: 1
+// stepping, 0 converged (residual < tol), -1 unstable (a non-finite velocity
+// or |u| >= c_s at the check).  conv[d] = index of the check that retired it.
 __global__ void __launch_bounds__(256) batch_reduce_kernel(const double* __restrict__ partials,
                                                            const int* __restrict__ tile_begin,
                                                            int* __restrict__ active, double* __restrict__ status,
                                                            int* __restrict__ conv, const int* __restrict__ counters,
-                                                           double tol) {
+                                                           const double* __restrict__ cs2, double tol) {
   const int d = blockIdx.x;
-  if (!active[d]) return;
-  __shared__ double sm[3][256];
-  double acc[3] = {0, 0, 0};
-  for (int i = tile_begin[d] + threadIdx.x; i < tile_begin[d + 1]; i += blockDim.x)
+  if (active[d] != 1) return;
+  __shared__ double sm[4][256];
+  double acc[4] = {0, 0, 0, 0};
+  for (int i = tile_begin[d] + threadIdx.x; i < tile_begin[d + 1]; i += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) acc[k] += partials[size_t(i) * 4 + k];
+    acc[3] = fmax(acc[3], partials[size_t(i) * 4 + 3]);
+  }
 #pragma unroll
-  for (int k = 0; k < 3; ++k) sm[k][threadIdx.x] = acc[k];
+  for (int k = 0; k < 4; ++k) sm[k][threadIdx.x] = acc[k];
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (int(threadIdx.x) < s)
+    if (int(threadIdx.x) < s) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+      sm[3][threadIdx.x] = fmax(sm[3][threadIdx.x], sm[3][threadIdx.x + s]);
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -201,7 +212,10 @@ __global__ void __launch_bounds__(256) batch_reduce_kernel(const double* __restr
     const double res = checks > 0 && sm[1][0] > 0 ? sqrt(sm[0][0] / sm[1][0]) : -1.0;
     status[2 * d] = res;
     status[2 * d + 1] = sm[2][0];
-    if (checks > 0 && res >= 0 && res < tol) {
+    if (!(sm[3][0] < cs2[d])) {
+      active[d] = -1;
+      conv[d] = checks;
+    } else if (checks > 0 && res >= 0 && res < tol) {
       active[d] = 0;
       conv[d] = checks;
     }
@@ -288,7 +302,7 @@ size_t align_b(size_t v) { return (v + kAlignB - 1) / kAlignB * kAlignB; }
 const int kWidths[4] = {32, 64, 128, 256};
 
 struct BatchLayout {
-  size_t fA, fB, uprev, dom, tiles, partials, tile_begin, active, status, conv, counters, stage, total;
+  size_t fA, fB, uprev, dom, tiles, partials, tile_begin, active, status, conv, counters, cs2, stage, total;
   size_t pop_elems;          // elements of one population lattice (all domains)
   size_t max_tiles;
   size_t max_n;              // largest domain
@@ -326,7 +340,8 @@ BatchLayout batch_layout(const std::vector<rmrtlb_domain>& d, int storage) {
   L.status = L.active + align_b(nd * sizeof(int));
   L.conv = L.status + align_b(2 * nd * sizeof(double));
   L.counters = L.conv + align_b(nd * sizeof(int));
-  L.stage = L.counters + align_b(16 * sizeof(int));
+  L.cs2 = L.counters + align_b(16 * sizeof(int));
+  L.stage = L.cs2 + align_b(nd * sizeof(double));
   L.total = L.stage + align_b(2 * 9 * maxn * sizeof(double));
   return L;
 }
@@ -460,7 +475,7 @@ cudaError_t launch_check(rmrtlb_batch* b, double* fields, int only_domain) {
   if (e != cudaSuccess || fields) return e;
   batch_reduce_kernel<<<unsigned(b->dom.size()), 256, 0, b->stream>>>(
       at<double>(b, b->L.partials), at<int>(b, b->L.tile_begin), at<int>(b, b->L.active),
-      at<double>(b, b->L.status), at<int>(b, b->L.conv), at<int>(b, b->L.counters), b->tol);
+      at<double>(b, b->L.status), at<int>(b, b->L.conv), at<int>(b, b->L.counters), at<double>(b, b->L.cs2), b->tol);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   batch_bump_kernel<<<1, 32, 0, b->stream>>>(at<int>(b, b->L.counters));
@@ -595,7 +610,15 @@ int rmrtlb_batch_create(rmrtlb_batch_t* out, int ndomains, const rmrtlb_domain* 
     off += align_b(9 * n * es) / es;
     uoff += 2 * n;
   }
+  std::vector<double> cs2(ndomains);
+  for (int d = 0; d < ndomains; ++d) {
+    const double m = fmin(b->dom[d].dx, b->dom[d].dy);
+    cs2[d] = b->dom[d].cs2 > 0 ? b->dom[d].cs2 : m * m / 3.0;
+  }
   cudaError_t e = cudaMemcpyAsync(b->ws + b->L.dom, params.data(), params.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->ws + b->L.cs2, cs2.data(), cs2.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess) e = build_tiles(b, 128);
   if (e == cudaSuccess) e = reset_state(b);
   if (e != cudaSuccess) { delete b; return RMRTLB_ECUDA; }
@@ -724,7 +747,7 @@ static int domain_buffer(rmrtlb_batch* b, int domain, int* which) {
                       b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return RMRTLB_ECUDA;
-  *which = act ? b->cur : 0;
+  *which = act == 1 ? b->cur : 0;
   return RMRTLB_OK;
 }
 

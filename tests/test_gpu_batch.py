@@ -121,3 +121,21 @@ def test_batch_tune_picks_a_width_and_resets():
     z = b.get_populations(0)
     lat = R.make_lattice("D2Q9", (doms[0]["dx"], doms[0]["dy"]))
     np.testing.assert_allclose(z, lat.w.reshape(9, 1, 1, 1) * np.ones_like(z), rtol=1e-6)
+
+
+def test_batch_retires_unstable_domain():
+    """An under-resolved cavity on a strongly anisotropic lattice (the oracle
+    blows up on it too) is retired as unstable at a check; the other domains
+    of the batch are untouched and match the oracle."""
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    bad = dict(nx=48, ny=48, dx=1.0, dy=4.0, nu=0.0024, nu_bulk=0.0024, s_free=1.1, lid_u=0.05, cs2=0.0)
+    good = dict(nx=20, ny=12, dx=1.0, dy=0.5, nu=0.05, nu_bulk=0.05, s_free=1.1, lid_u=0.05, cs2=0.0)
+    b = Batch([good, bad], storage="f64", check_every=100, tol=1e-12)
+    b.step(1500)
+    res, conv, act, done = b.status()
+    assert act[1] == -1 and conv[1] > 0
+    assert act[0] == 1
+    lat = R.make_lattice("D2Q9", (good["dx"], good["dy"]))
+    f0 = np.zeros((9, 1, good["ny"], good["nx"])) + lat.w.reshape(9, 1, 1, 1)
+    fo, _ = oracle_domain(good, 1500, f0)
+    assert normwise(b.get_populations(0), fo) <= 1e-11
