@@ -202,43 +202,50 @@ int rmrtlb_stats(rmrtlb_t solver, double out[8]);
 int rmrtlb_last_check(rmrtlb_t solver, double out[8]);
 
 /* ------------------------------------------------------ batched cavities */
-/* Many independent rD2Q9 NSE domains advanced together (SURVEY config 4):
- * each a closed rectangle of nx x ny nodes with half-way bounce-back walls
- * half a spacing outside the first and last nodes, the top wall (beyond
- * y = ny - 1) moving along x with lid_u.  A population whose source lies
- * outside the domain is the node's own post-collision population in the
- * opposite direction; crossing the lid it gains 2 omega_j rho0 (c_j . U) /
- * c_s^2, the linear term of the REDF (Eq. 3-3).  Every node collides as in
- * rmrtlb_step (Eq. 2-2-3, raw moments, unforced NSE), with its domain's
- * own spacing, c_s^2 (<= 0: min(dx, dy)^2 / 3), weights (Eq. 3-3-5) and
- * rates (Eq. 4-31, Eq. 5-8-1).  The paper has no boundaries; the wall rule
- * is the standard half-way bounce-back. */
+/* Many independent lid-driven cavities advanced together on one lattice
+ * (rD2Q9, rD3Q19 or rD3Q27; raw or central moments): each a closed box of
+ * nx x ny (x nz) nodes with half-way bounce-back walls half a spacing
+ * outside the first and last node of every axis; the lid is the wall beyond
+ * the last node of the last axis (y = ny - 1 on rD2Q9, z = nz - 1 on the
+ * 3-D lattices) and moves along +x with lid_u.  A population whose source
+ * x - e_j lies outside the box is the node's own post-collision population
+ * in the opposite direction; one whose source lies beyond the lid gains
+ * 2 omega_j rho0 (c_j . U) / c_s^2, the linear term of the REDF (Eq. 3-3).
+ * Every node collides as in rmrtlb_step (Eq. 2-2-3, unforced NSE, the
+ * central variant of Eq. 5-1-2 with basis RMRTLB_BASIS_CENTRAL), with its
+ * domain's own spacing, c_s^2 (<= 0: the smallest spacing squared / 3),
+ * weights (Sec. III) and rates (Eq. 4-31, Eq. 5-8-1).  The paper has no
+ * boundaries; the wall rule is the standard half-way bounce-back. */
 typedef struct {
-    int nx, ny;
-    double dx, dy;       /* spacings; lattice units, dt = 1 */
+    int nx, ny, nz;      /* nz = 1 on rD2Q9 */
+    double dx, dy, dz;   /* spacings; lattice units, dt = 1 (dz unused on rD2Q9) */
     double nu, nu_bulk;  /* kinematic and bulk viscosity */
     double s_free;       /* rate of every moment of order >= 3 */
-    double lid_u;        /* lid velocity (along +x) on the top wall */
-    double cs2;          /* <= 0 selects min(dx, dy)^2 / 3 */
+    double lid_u;        /* lid velocity (along +x) */
+    double cs2;          /* <= 0 selects the smallest spacing squared / 3 */
 } rmrtlb_domain;
 
 typedef struct rmrtlb_batch* rmrtlb_batch_t;
 
-/* Workspace bytes for these domains (storage RMRTLB_ST_F32 or _F64).
- * Host only. */
-int rmrtlb_batch_workspace_bytes(int ndomains, const rmrtlb_domain* domains,
+/* Workspace bytes for these domains on `lattice` (RMRTLB_D2Q9, _D3Q19,
+ * _D3Q27), storage RMRTLB_ST_F32 or _F64.  RMRTLB_EINVAL for a bad lattice,
+ * storage or size (nz != 1 on rD2Q9, more than 65535 domains or 2^31 row
+ * tiles).  Host only. */
+int rmrtlb_batch_workspace_bytes(int lattice, int ndomains, const rmrtlb_domain* domains,
                                  int storage, size_t* bytes);
 
 /* Bind a batch to the caller's workspace (device, 256-byte aligned, owned
- * by the caller).  Every domain starts at rest (rho0, u = 0).  Every
- * check_every steps (rounded up to even) the FP64 residual
- * ||u(t) - u(t - check_every)||_2 / ||u(t)||_2 of each domain is formed; a
- * domain whose residual falls below tol retires: it is no longer stepped
- * and keeps its state.  With a non-NULL stream, each chunk of check_every
- * steps plus its check is captured once as a CUDA graph and replayed; the
- * legacy NULL stream launches directly (capture needs a created stream).
- * The tile list starts with 128-node row tiles (see rmrtlb_batch_tune). */
-int rmrtlb_batch_create(rmrtlb_batch_t* batch, int ndomains,
+ * by the caller).  basis: RMRTLB_BASIS_RAW or _CENTRAL.  Every domain starts
+ * at rest (rho0, u = 0).  Every check_every steps (rounded up to even) the
+ * FP64 residual ||u(t) - u(t - check_every)||_2 / ||u(t)||_2 of each domain
+ * is formed; a domain whose residual falls below tol retires: it is no
+ * longer stepped and keeps its state.  With a non-NULL stream, each chunk
+ * of check_every steps plus its check is captured once as a CUDA graph and
+ * replayed; the legacy NULL stream launches directly (capture needs a
+ * created stream).  The tile list starts with 128-node row tiles (see
+ * rmrtlb_batch_tune).  RMRTLB_EINVAL for invalid rates or weights of a
+ * domain (as rmrtlb_create), RMRTLB_ENOMEM for a short workspace. */
+int rmrtlb_batch_create(rmrtlb_batch_t* batch, int lattice, int basis, int ndomains,
                         const rmrtlb_domain* domains, int storage, double rho0,
                         int check_every, double tol, void* workspace,
                         size_t workspace_bytes, void* stream);
@@ -255,6 +262,13 @@ int rmrtlb_batch_tune(rmrtlb_batch_t batch, int steps, int* tile_width);
 /* Advance every active domain n steps (asynchronous). */
 int rmrtlb_batch_step(rmrtlb_batch_t batch, int n);
 
+/* Advance until no domain is stepping (all converged or unstable) or
+ * max_steps steps were issued; the state flags are read every 8 checks, so
+ * up to 8 * check_every steps are issued after the last domain retired
+ * (retired domains are skipped by the kernels).  *steps_done = steps
+ * issued by this call.  Synchronises. */
+int rmrtlb_batch_run(rmrtlb_batch_t batch, long long max_steps, long long* steps_done);
+
 /* Per-domain arrays (any may be NULL): residual of the last check (-1
  * before the second check), step at which the domain retired (-1 while
  * stepping), state: 1 stepping, 0 converged (residual < tol), -1 unstable
@@ -264,12 +278,24 @@ int rmrtlb_batch_status(rmrtlb_batch_t batch, double* residual,
                         long long* steps_to_converge, int* active,
                         long long* steps_done);
 
-/* Populations fbar_j(x, t) of one domain, 9 FP64 planes of ny*nx in
- * rmrtlb_lattice_info order, host or device memory.  Synchronise. */
+/* Populations fbar_j(x, t) of one domain, q FP64 planes of nz*ny*nx (x
+ * fastest) in rmrtlb_lattice_info order, host or device memory.
+ * Synchronise. */
 int rmrtlb_batch_set_populations(rmrtlb_batch_t batch, int domain, const double* f);
 int rmrtlb_batch_get_populations(rmrtlb_batch_t batch, int domain, double* f);
 
-/* rho (one plane) and u (2 planes) of one domain; host or device; either
+/* Start one domain from macroscopic fields: rho one plane, u d planes
+ * (FP64, host or device).  fbar = f^eq(rho, u) (Eq. NSEfeq); with
+ * with_noneq != 0 the non-equilibrium part of Eq. (fne) is added, with
+ * m_2^ne from Eq. (4-35): m_2^ne_aa = -rho (c_a^2 - c_s^2) dt (du_a/dx_a)
+ * / s_sa and m_2^ne_ab = -rho c_s^2 dt (du_a/dx_b + du_b/dx_a) / s_ab,
+ * the velocity gradients by central differences (one-sided at the first and
+ * last node of an axis).  The domain's state flag is unchanged.
+ * Synchronises. */
+int rmrtlb_batch_init_fields(rmrtlb_batch_t batch, int domain, const double* rho,
+                             const double* u, int with_noneq);
+
+/* rho (one plane) and u (d planes) of one domain; host or device; either
  * may be NULL.  Synchronises. */
 int rmrtlb_batch_fields(rmrtlb_batch_t batch, int domain, double* rho, double* u);
 

@@ -22,6 +22,7 @@ paper's order and notation:
 * collision operator ................ Eqs. (5-1), (5-1-2)
 * forced moment-space step .......... Eqs. (2-3), (2-2-3), (2-4-1), (2-4-2)
 * propagation ....................... Eq. (2-2b)
+* non-equilibrium initialisation .... Eqs. (4-29), (4-35), (fne)
 
 Matrices are built numerically (M from the monomial list over the velocity
 set, M^-1 and the S_2 block by numerical inversion, m^eq = M f^eq from the
@@ -584,6 +585,72 @@ def init_equilibrium(lat: Lattice, m: Model, S: np.ndarray, rho: np.ndarray, u: 
     uu = u.reshape(lat.d, -1).T.astype(np.float64)
     feq, _, _ = equilibrium_and_sources(lat, m, S, r, uu)
     return feq.reshape((lat.q,) + shp)
+
+
+def velocity_gradient(lat: Lattice, u: np.ndarray) -> np.ndarray:
+    """g[a, b] = d u_b / d x_a on a field u (d, nz, ny, nx); shape (d, d, nz, ny, nx).
+
+    The paper gives no difference stencil (it derives the local stress of
+    Eqs. 4-32/4-33 precisely to avoid one).  Reading taken for the
+    initialisation of Eq. (fne): second-order central differences inside the
+    domain, first-order one-sided differences at the first and last node of
+    an axis, zero along an axis with a single node; spacing dx_a = c_a dt.
+    """
+    d = lat.d
+    g = np.zeros((d, d) + u.shape[1:])
+    for a in range(d):
+        ax = 2 - a                # array axis of x_a in (nz, ny, nx)
+        n = u.shape[1 + ax]
+        if n < 2:
+            continue
+        h = lat.dx[a]
+        for b in range(d):
+            ub = u[b]
+            gb = np.empty_like(ub)
+            sl = lambda i: tuple(slice(None) if k != ax else i for k in range(3))
+            gb[sl(slice(1, n - 1))] = (ub[sl(slice(2, n))] - ub[sl(slice(0, n - 2))]) / (2.0 * h)
+            gb[sl(0)] = (ub[sl(1)] - ub[sl(0)]) / h
+            gb[sl(n - 1)] = (ub[sl(n - 1)] - ub[sl(n - 2)]) / h
+            g[a, b] = gb
+    return g
+
+
+def noneq_second_moment(lat: Lattice, r: Rates, rho: np.ndarray, grad: np.ndarray) -> np.ndarray:
+    """m_2^ne = sum_k c_k c_k f_k^ne of Eq. (4-35) without forcing or source.
+
+    m_2^ne = -(I - S_2/2)^-1 K_mu (grad u + grad u^T), the products taken
+    entry by entry, with S_2 the matrix of entries s_sa (diagonal) and s_ab
+    (off-diagonal) named below Eq. (4-32), and the viscosity tensor of
+    Eq. (4-29a): K_mu,aa = (1/2)(1/s_sa - 1/2) rho (c_a^2 - c_s^2) dt,
+    K_mu,ab = (1/s_ab - 1/2) rho c_s^2 dt.  rho (n,), grad (d, d, n);
+    returns (n, d, d).
+    """
+    d, cs2, dt, c = lat.d, lat.cs2, lat.dt, lat.c
+    rho = np.asarray(rho, dtype=np.float64).reshape(-1)
+    out = np.zeros((rho.size, d, d))
+    for a in range(d):
+        for b in range(d):
+            if a == b:
+                s = r.s_shear[a]
+                K = 0.5 * (1.0 / s - 0.5) * rho * (c[a] * c[a] - cs2) * dt
+            else:
+                s = r.s_off[a, b]
+                K = (1.0 / s - 0.5) * rho * cs2 * dt
+            strain = grad[a, b].reshape(-1) + grad[b, a].reshape(-1)
+            out[:, a, b] = -K * strain / (1.0 - 0.5 * s)
+    return out
+
+
+def init_noneq(lat: Lattice, m: Model, S: np.ndarray, r: Rates, rho: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """f-bar = f^eq(rho, u) + f^ne, f^ne = g^eq(0, 0, m_2^ne) (Eq. fne), with
+    m_2^ne from Eq. (4-35) and the velocity gradient of velocity_gradient.
+    NSE only; rho (nz,ny,nx), u (d,nz,ny,nx)."""
+    shp = rho.shape
+    feq = init_equilibrium(lat, m, S, rho, u)
+    m2 = noneq_second_moment(lat, r, rho, velocity_gradient(lat, u))
+    n = rho.size
+    fne = geq(lat, np.zeros(n), np.zeros((n, lat.d)), m2)
+    return feq + fne.reshape((lat.q,) + shp)
 
 
 def collide_stream_at(lat: Lattice, m: Model, S: np.ndarray, fbar: np.ndarray, nodes: np.ndarray) -> np.ndarray:

@@ -1,16 +1,17 @@
-// Batched rD2Q9 lid-driven cavities: many independent rectangular domains
-// (own size, spacing and viscosity) advanced together, one launch per step
-// over a list of row tiles, with half-way bounce-back walls, a moving lid,
-// a per-domain FP64 residual check and retirement of converged domains.
-// Chunks of check_every steps plus their check are replayed as a CUDA graph.
+// Batched lid-driven cavities on rD2Q9, rD3Q19 and rD3Q27 (raw or central
+// moments): many independent rectangular domains (own size, spacing and
+// viscosity) advanced together, one launch per step over a list of row
+// tiles, with half-way bounce-back walls, a moving lid, a per-domain FP64
+// residual check and retirement of converged or unstable domains.  Chunks of
+// check_every steps plus their check are replayed as a CUDA graph.
 //
 // The paper has no boundaries and no batching; the collision of every node
 // is the same Eq. (2-2-3) step as the single-domain kernels (shared code in
 // rmrt_device.cuh).  Walls: a population whose source node x - e_j lies
 // outside the domain is the node's own post-collision population in the
-// opposite direction (half-way bounce-back); crossing the top wall (the lid,
-// moving along x with U) adds 2 omega_j rho0 (c_j . U) / c_s^2, the linear
-// term of the REDF (Eq. 3-3).
+// opposite direction (half-way bounce-back); crossing the lid (the face
+// beyond the last node of the last axis, moving along x with U) adds
+// 2 omega_j rho0 (c_j . U) / c_s^2, the linear term of the REDF (Eq. 3-3).
 #include <math.h>
 #include <string.h>
 
@@ -19,33 +20,30 @@
 
 #include "../../include/rmrtlb.h"
 #include "rmrt_device.cuh"
+#include "rmrt_host.h"
 
 namespace rmrt {
 
-// Per-domain parameter block; the field names follow KParams so that the
-// shared collision reads it.  Only what an unforced rD2Q9 NSE step needs.
+// Per-domain parameter block: the collision constants of the shared
+// derivation (weights of Sec. III, rates of Eq. 4-31, S_2 of Eq. 5-8-1) plus
+// what the walls, the lid and the non-equilibrium initialisation need.
 template <typename CT>
 struct BParams {
-  int nx, ny;
-  int kind;                 // KIND_NSE
-  int pad_;
+  KParams<CT> k;
   unsigned long long off;   // element offset of the domain's population block
-  unsigned long long uoff;  // element offset of its residual snapshot (2 planes)
-  CT rho0, dt, source, cs2;
-  CT mu2[3], s0, s1[3], s2h[3][3], soff[3], sfree;
-  CT fh[3], advh[3], q19h[3];
-  CT lid;                   // 2 omega_5 rho0 c_x U / c_s^2 (diagonal directions into the fluid)
-  CT c[2];
-  double wd[9];             // weights and rho0 in FP64 for population set/get
-  double rho0d;
+  unsigned long long uoff;  // element offset of its residual snapshot (d planes)
+  CT lid[27];               // 2 omega_j rho0 c_x e_jx U / c_s^2: lid term of a population arriving from the lid
+  double ned[3];            // (c_a^2 - c_s^2) dt / s_sa: diagonal of Eq. (4-35) per unit rho and du_a/dx_a
+  double neo[3];            // c_s^2 dt / s_ab (xy, xz, yz): off-diagonal of Eq. (4-35)
 };
 
-using L9 = Lat<LAT_D2Q9>;
-
-__device__ __forceinline__ constexpr int opposite9(int j) {
+template <int LAT>
+__host__ __device__ constexpr int opposite_dir(int j) {
   int r = 0;
-  for (int k = 0; k < 9; ++k)
-    if (L9::EX[k] == -L9::EX[j] && L9::EY[k] == -L9::EY[j]) r = k;
+  for (int k = 0; k < Lat<LAT>::Q; ++k)
+    if (Lat<LAT>::EX[k] == -Lat<LAT>::EX[j] && Lat<LAT>::EY[k] == -Lat<LAT>::EY[j] &&
+        Lat<LAT>::EZ[k] == -Lat<LAT>::EZ[j])
+      r = k;
   return r;
 }
 
@@ -59,103 +57,142 @@ __device__ __forceinline__ void load_params(BParams<CT>& sp, const BParams<CT>* 
   __syncthreads();
 }
 
-// Population j arriving at (x, y): pulled from (x - e_j) inside the domain,
-// else bounced back from the node itself, with the lid term across the top.
-template <typename CT, typename ST, int j>
-__device__ __forceinline__ CT gather9(const ST* __restrict__ base, int x, int y, const BParams<CT>& sp) {
-  constexpr int ex = L9::EX[j], ey = L9::EY[j], jo = opposite9(j);
-  const int nx = sp.nx, ny = sp.ny;
-  const int sx = x - ex, sy = y - ey;
-  const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny;
-  const size_t N = size_t(nx) * ny;
-  const size_t idx = inside ? size_t(j) * N + size_t(sy) * nx + sx : size_t(jo) * N + size_t(y) * nx + x;
+// Node coordinates of a tile thread: rows are numbered z * ny + y.
+struct NodeXYZ {
+  int x, y, z;
+  size_t own;
+};
+template <typename CT>
+__device__ __forceinline__ NodeXYZ node_of(int x, int row, const BParams<CT>& sp) {
+  NodeXYZ r;
+  r.x = x;
+  r.y = row % sp.k.ny;
+  r.z = row / sp.k.ny;
+  r.own = size_t(row) * sp.k.nx + x;
+  return r;
+}
+
+// True when x - e crosses the lid: the face beyond the last node of the
+// last axis (y on rD2Q9, z on the 3-D lattices).
+template <int LAT>
+__device__ __forceinline__ bool from_lid(int sy, int sz, int ny, int nz) {
+  return Lat<LAT>::D == 2 ? sy >= ny : sz >= nz;
+}
+
+// Population j arriving at a node: pulled from x - e_j inside the domain,
+// else bounced back from the node itself (half-way bounce-back), with the
+// lid term when x - e_j lies beyond the lid.
+template <int LAT, typename CT, typename ST, int j>
+__device__ __forceinline__ CT gather(const ST* __restrict__ base, const NodeXYZ& n, const BParams<CT>& sp) {
+  constexpr int ex = Lat<LAT>::EX[j], ey = Lat<LAT>::EY[j], ez = Lat<LAT>::EZ[j];
+  constexpr int jo = opposite_dir<LAT>(j);
+  const int nx = sp.k.nx, ny = sp.k.ny, nz = sp.k.nz;
+  const int sx = n.x - ex, sy = n.y - ey, sz = n.z - ez;
+  const bool inside = unsigned(sx) < unsigned(nx) && unsigned(sy) < unsigned(ny) && unsigned(sz) < unsigned(nz);
+  const size_t N = sp.k.N;
+  const size_t idx = inside ? size_t(j) * N + (size_t(sz) * ny + sy) * nx + sx : size_t(jo) * N + n.own;
   CT v = CT(__ldg(base + idx));
-  if (ex != 0 && sy >= ny) v += CT(ex) * sp.lid;
+  if (ex != 0 && from_lid<LAT>(sy, sz, ny, nz)) v += sp.lid[j];
   return v;
 }
 
-template <typename ST, typename CT>
+template <int LAT, bool CENTRAL, typename ST, typename CT>
 __global__ void __launch_bounds__(256) batch_step_kernel(const ST* __restrict__ fin, ST* __restrict__ fout,
                                                          const BParams<CT>* __restrict__ dom,
                                                          const int4* __restrict__ tiles,
                                                          const int* __restrict__ active) {
-  const int4 t = tiles[blockIdx.x];  // (domain, y, x0, width)
-  if (!active[t.x]) return;          // retired: its last state stays in buffer A
+  using L = Lat<LAT>;
+  const int4 t = tiles[blockIdx.x];  // (domain, row, x0, width)
+  if (active[t.x] != 1) return;      // retired: its last state stays in buffer A
   __shared__ BParams<CT> sp;
   load_params(sp, dom, t.x);
-  const int x = t.z + int(threadIdx.x);
   if (int(threadIdx.x) >= t.w) return;
-  const int y = t.y;
+  const NodeXYZ n = node_of(t.z + int(threadIdx.x), t.y, sp);
   const ST* base = fin + sp.off;
-  Cube<LAT_D2Q9, CT> q;
-  static_for<9>([&](auto J) {
+  Cube<LAT, CT> q;
+  if constexpr (LAT == LAT_D3Q19) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q.v[a][b][c] = CT(0);
+  }
+  static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
-    constexpr int ex = L9::EX[j], ey = L9::EY[j];
-    q.v[ex + 1][ey + 1][0] = gather9<CT, ST, j>(base, x, y, sp);
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    q.v[ex + 1][ey + 1][zi<LAT>(ez)] = gather<LAT, CT, ST, j>(base, n, sp);
   });
-  collide<LAT_D2Q9, false, false, true>(q, sp);
-  const size_t N = size_t(sp.nx) * sp.ny;
-  ST* out = fout + sp.off + size_t(y) * sp.nx + x;
-  static_for<9>([&](auto J) {
+  collide<LAT, CENTRAL, false, true>(q, sp.k);
+  const size_t N = sp.k.N;
+  ST* out = fout + sp.off + n.own;
+  static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
-    constexpr int ex = L9::EX[j], ey = L9::EY[j];
-    out[size_t(j) * N] = ST(q.v[ex + 1][ey + 1][0]);
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    out[size_t(j) * N] = ST(q.v[ex + 1][ey + 1][zi<LAT>(ez)]);
   });
 }
 
+// Density and velocity of a node from its gathered populations.
+template <int LAT, typename ST, typename CT>
+__device__ __forceinline__ void node_fields(const ST* __restrict__ base, const NodeXYZ& n, const BParams<CT>& sp,
+                                            CT& s0, double u[3]) {
+  using L = Lat<LAT>;
+  CT m1[3] = {CT(0), CT(0), CT(0)};
+  s0 = CT(0);
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    const CT v = gather<LAT, CT, ST, j>(base, n, sp);
+    s0 += v;
+    if (ex) m1[0] += CT(ex) * v;
+    if (ey) m1[1] += CT(ey) * v;
+    if (ez) m1[2] += CT(ez) * v;
+  });
+  const CT inv = CT(1) / (sp.k.rho0 + s0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = a < L::D ? double(m1[a] * sp.k.c[a] * inv) : 0.0;
+}
+
 // Per-tile FP64 sums for the residual ||u - u_prev|| / ||u||: [0] sum
-// |u - u_prev|^2, [1] sum |u|^2, [2] sum (rho - rho0).  Optionally writes
-// the fields (rho_out, u_out: one domain, device, 3 planes).
-template <typename ST, typename CT>
+// |u - u_prev|^2, [1] sum |u|^2, [2] sum (rho - rho0), [3] max |u|^2
+// (infinite when a value is not finite).
+template <int LAT, typename ST, typename CT>
 __global__ void __launch_bounds__(256) batch_check_kernel(const ST* __restrict__ fin,
                                                           const BParams<CT>* __restrict__ dom,
                                                           const int4* __restrict__ tiles,
                                                           const int* __restrict__ active,
                                                           double* __restrict__ uprev, int use_prev,
-                                                          double* __restrict__ partials, int only_domain,
-                                                          double* __restrict__ fields) {
+                                                          double* __restrict__ partials) {
+  using L = Lat<LAT>;
+  constexpr int D = L::D;
   const int4 t = tiles[blockIdx.x];
   __shared__ double red[4][8];
   double acc[4] = {0, 0, 0, 0};
-  const bool run = only_domain < 0 ? (active[t.x] != 0) : (t.x == only_domain);
-  if (run) {
+  if (active[t.x] == 1) {
     __shared__ BParams<CT> sp;
     load_params(sp, dom, t.x);
-    const int x = t.z + int(threadIdx.x);
     if (int(threadIdx.x) < t.w) {
-      const int y = t.y;
-      const ST* base = fin + sp.off;
-      CT s0 = CT(0), sx = CT(0), sy = CT(0);
-      static_for<9>([&](auto J) {
-        constexpr int j = decltype(J)::value;
-        constexpr int ex = L9::EX[j], ey = L9::EY[j];
-        const CT v = gather9<CT, ST, j>(base, x, y, sp);
-        s0 += v;
-        if (ex) sx += CT(ex) * v;
-        if (ey) sy += CT(ey) * v;
-      });
-      const CT rho = sp.rho0 + s0;
-      const CT inv = CT(1) / rho;
-      const double ux = double(sx * sp.c[0] * inv), uy = double(sy * sp.c[1] * inv);
-      const size_t n = size_t(y) * sp.nx + x;
-      const size_t N = size_t(sp.nx) * sp.ny;
-      if (fields) {
-        fields[n] = double(rho);
-        fields[N + n] = ux;
-        fields[2 * N + n] = uy;
-      } else {
-        double* up = uprev + sp.uoff;
-        const double dx = ux - (use_prev ? up[n] : 0.0), dy = uy - (use_prev ? up[N + n] : 0.0);
-        up[n] = ux;
-        up[N + n] = uy;
-        acc[0] = dx * dx + dy * dy;
-        acc[1] = ux * ux + uy * uy;
-        acc[2] = double(s0);
-        acc[3] = isfinite(acc[1]) && isfinite(acc[2]) ? acc[1] : INFINITY;
+      const NodeXYZ n = node_of(t.z + int(threadIdx.x), t.y, sp);
+      CT s0;
+      double u[3];
+      node_fields<LAT, ST, CT>(fin + sp.off, n, sp, s0, u);
+      const size_t N = sp.k.N;
+      double* up = uprev + sp.uoff;
+      double du2 = 0.0, u2 = 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const double dlt = u[a] - (use_prev ? up[a * N + n.own] : 0.0);
+        up[a * N + n.own] = u[a];
+        du2 += dlt * dlt;
+        u2 += u[a] * u[a];
       }
+      acc[0] = du2;
+      acc[1] = u2;
+      acc[2] = double(s0);
+      acc[3] = isfinite(acc[1]) && isfinite(acc[2]) ? acc[1] : INFINITY;
     }
   }
-  if (fields) return;
   // block reduction in a fixed order (blockDim is a multiple of 32, <= 256);
   // sums for [0..2], maximum for [3]
 #pragma unroll
@@ -175,6 +212,25 @@ __global__ void __launch_bounds__(256) batch_check_kernel(const ST* __restrict__
     for (int w = 0; w < int(blockDim.x >> 5); ++w)
       s = threadIdx.x < 3 ? s + red[threadIdx.x][w] : fmax(s, red[threadIdx.x][w]);
     partials[size_t(blockIdx.x) * 4 + threadIdx.x] = s;
+  }
+}
+
+// rho and u (1 + d planes) of one domain, grid-stride over its nodes.
+template <int LAT, typename ST, typename CT>
+__global__ void batch_fields_kernel(const ST* __restrict__ fin, const BParams<CT>* __restrict__ dom, int d,
+                                    double* __restrict__ fields) {
+  __shared__ BParams<CT> sp;
+  load_params(sp, dom, d);
+  const size_t N = sp.k.N;
+  for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
+    const int row = int(i / sp.k.nx);
+    const NodeXYZ n = node_of(int(i % sp.k.nx), row, sp);
+    CT s0;
+    double u[3];
+    node_fields<LAT, ST, CT>(fin + sp.off, n, sp, s0, u);
+    fields[i] = double(sp.k.rho0 + s0);
+#pragma unroll
+    for (int a = 0; a < Lat<LAT>::D; ++a) fields[(1 + a) * N + i] = u[a];
   }
 }
 
@@ -223,21 +279,24 @@ __global__ void __launch_bounds__(256) batch_reduce_kernel(const double* __restr
 }
 
 // Rest state fbar = omega rho0 in pull storage: every stored deviation is 0
-// except the slots of the top row that stream into the lid: they bounce back
-// as the direction jo with e_y = -1 and gain e_jo,x * lid, so they hold
-// -e_jo,x * lid = e_j,x * lid.  grid (ceil(max nx / blockDim), ndomains).
-template <typename ST, typename CT>
+// except the slots of the layer under the lid that stream into it: they
+// bounce back as the opposite direction jo and gain lid[jo] = -lid[j], so
+// they hold lid[j].  grid (blocks, ndomains), grid-stride over the layer.
+template <int LAT, typename ST, typename CT>
 __global__ void batch_rest_kernel(ST* __restrict__ f, const BParams<CT>* __restrict__ dom) {
+  using L = Lat<LAT>;
   const BParams<CT>& p = dom[blockIdx.y];
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= p.nx) return;
-  const size_t N = size_t(p.nx) * p.ny;
-  const size_t n = size_t(p.ny - 1) * p.nx + x;
-  static_for<9>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    constexpr int ex = L9::EX[j], ey = L9::EY[j];
-    if (ey == 1 && ex != 0) f[p.off + size_t(j) * N + n] = ST(CT(ex) * p.lid);
-  });
+  const int nx = p.k.nx, ny = p.k.ny, nz = p.k.nz;
+  const size_t layer = L::D == 2 ? size_t(nx) : size_t(nx) * ny;
+  const size_t first = L::D == 2 ? size_t(ny - 1) * nx : size_t(nz - 1) * nx * ny;
+  for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < layer; t += size_t(gridDim.x) * blockDim.x) {
+    const size_t n = first + t;
+    static_for<L::Q>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int ex = L::EX[j], up = L::D == 2 ? L::EY[j] : L::EZ[j];
+      if (up == 1 && ex != 0) f[p.off + size_t(j) * p.k.N + n] = ST(p.lid[j]);
+    });
+  }
 }
 
 // counters[0]: number of completed checks (a check with counters[0] > 0 has a
@@ -246,60 +305,159 @@ __global__ void batch_bump_kernel(int* counters) {
   if (threadIdx.x == 0 && blockIdx.x == 0) counters[0] += 1;
 }
 
-// Canonical populations of one domain <-> storage (plane j).
-// to_storage: A_j(y) = fbar_j(y + e_j) inside, else fbar_opp(y) - lid term;
-// from_storage: fbar_j(x) = gather.
-template <typename ST, typename CT>
+// Direction j's components and opposite, at run time.
+template <int LAT>
+__device__ __forceinline__ void dir_of(int j, int& ex, int& ey, int& ez, int& jo) {
+  static_for<Lat<LAT>::Q>([&](auto J) {
+    constexpr int k = decltype(J)::value;
+    constexpr int cx = Lat<LAT>::EX[k], cy = Lat<LAT>::EY[k], cz = Lat<LAT>::EZ[k], ko = opposite_dir<LAT>(k);
+    if (k == j) {
+      ex = cx;
+      ey = cy;
+      ez = cz;
+      jo = ko;
+    }
+  });
+}
+
+// Canonical populations of one domain <-> storage, plane j.
+// to_storage: plane = fbar_j (first N values) and fbar_jo (next N); slot
+// A_j(x) = fbar_j(x + e_j) inside, else fbar_jo(x) - lid[jo] (the value that
+// bounces back into jo).  from_storage: plane = fbar_j = gather.
+template <int LAT, typename ST, typename CT>
 __global__ void batch_plane_kernel(ST* __restrict__ f, double* __restrict__ plane, int j, int to_storage,
                                    const BParams<CT>* __restrict__ dom, int d) {
   __shared__ BParams<CT> sp;
   load_params(sp, dom, d);
-  const int nx = sp.nx, ny = sp.ny;
-  const size_t N = size_t(nx) * ny;
-  const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const int x = int(n % nx), y = int(n / nx);
+  const int nx = sp.k.nx, ny = sp.k.ny, nz = sp.k.nz;
+  const size_t N = sp.k.N;
   ST* base = f + sp.off;   // storage holds fbar - omega rho0 (omega_j = omega_opp(j))
-  int ex = 0, ey = 0, jo = 0;
-  static_for<9>([&](auto J) {
-    constexpr int k = decltype(J)::value;
-    constexpr int cx = L9::EX[k], cy = L9::EY[k], ko = opposite9(k);
-    if (k == j) { ex = cx; ey = cy; jo = ko; }
-  });
-  if (to_storage) {
-    // slot (x, y) of direction j holds the post-collision value that moves to (x + e_j)
-    const int tx = x + ex, ty = y + ey;
-    double v;
-    if (tx >= 0 && tx < nx && ty >= 0 && ty < ny) {
-      v = plane[N * 0 + size_t(ty) * nx + tx];
+  int ex = 0, ey = 0, ez = 0, jo = 0;
+  dir_of<LAT>(j, ex, ey, ez, jo);
+  const double rest = sp.k.wd[j] * sp.k.rho0d;
+  for (size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x; n < N; n += size_t(gridDim.x) * blockDim.x) {
+    const int x = int(n % nx), y = int((n / nx) % ny), z = int(n / (size_t(nx) * ny));
+    if (to_storage) {
+      const int tx = x + ex, ty = y + ey, tz = z + ez;
+      double v;
+      if (unsigned(tx) < unsigned(nx) && unsigned(ty) < unsigned(ny) && unsigned(tz) < unsigned(nz)) {
+        v = plane[(size_t(tz) * ny + ty) * nx + tx];
+      } else {
+        v = plane[N + n];
+        if (ex != 0 && from_lid<LAT>(ty, tz, ny, nz)) v -= double(sp.lid[jo]);
+      }
+      base[size_t(j) * N + n] = ST(v - rest);
     } else {
-      // it bounces back as direction jo at (x, y)
-      v = plane[N * 1 + n];
-      if (ty >= ny && ex != 0) v += double(ex) * double(sp.lid);   // undo the lid term of jo
+      const int sx = x - ex, sy = y - ey, sz = z - ez;
+      double v;
+      if (unsigned(sx) < unsigned(nx) && unsigned(sy) < unsigned(ny) && unsigned(sz) < unsigned(nz)) {
+        v = double(base[size_t(j) * N + (size_t(sz) * ny + sy) * nx + sx]);
+      } else {
+        v = double(base[size_t(jo) * N + n]);
+        if (ex != 0 && from_lid<LAT>(sy, sz, ny, nz)) v += double(sp.lid[j]);
+      }
+      plane[n] = v + rest;
     }
-    base[size_t(j) * N + n] = ST(v - sp.wd[j] * sp.rho0d);
-  } else {
-    const int sx = x - ex, sy = y - ey;
-    double v;
-    if (sx >= 0 && sx < nx && sy >= 0 && sy < ny) {
-      v = double(base[size_t(j) * N + size_t(sy) * nx + sx]);
-    } else {
-      v = double(base[size_t(jo) * N + n]);
-      if (sy >= ny && ex != 0) v += double(ex) * double(sp.lid);
+  }
+}
+
+// d u_b / d x_a at a node from a field (b-th plane of u): central difference
+// inside, one-sided at the first and last node, 0 on a one-node axis.
+__device__ __forceinline__ double grad_at(const double* __restrict__ ub, size_t n, int i, int len, size_t stride,
+                                          double h) {
+  if (len < 2) return 0.0;
+  if (i == 0) return (ub[n + stride] - ub[n]) / h;
+  if (i == len - 1) return (ub[n] - ub[n - stride]) / h;
+  return (ub[n + stride] - ub[n - stride]) / (2.0 * h);
+}
+
+// fbar = f^eq(rho, u) (Eq. NSEfeq), plus with_ne the non-equilibrium part
+// f^ne = g^eq(0, 0, m_2^ne) of Eq. (fne) with m_2^ne from Eq. (4-35):
+// m_2^ne_aa = -rho (c_a^2 - c_s^2) dt du_a/dx_a / s_sa and
+// m_2^ne_ab = -rho c_s^2 dt (du_a/dx_b + du_b/dx_a) / s_ab (a != b); both
+// are the equilibrium moments of g^eq(rho, rho u, rho u u + m_2^ne).  Each
+// value goes to the slot the next pull gather reads it from.
+template <int LAT, typename ST, typename CT>
+__global__ void batch_init_kernel(ST* __restrict__ f, const double* __restrict__ rho, const double* __restrict__ u,
+                                  const BParams<CT>* __restrict__ dom, int d, int with_ne) {
+  using L = Lat<LAT>;
+  constexpr int D = L::D, NZ = L::NZ;
+  __shared__ BParams<CT> sp;
+  load_params(sp, dom, d);
+  const KParams<CT>& p = sp.k;
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const size_t N = p.N;
+  ST* base = f + sp.off;
+  for (size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x; n < N; n += size_t(gridDim.x) * blockDim.x) {
+    const int x = int(n % nx), y = int((n / nx) % ny), z = int(n / (size_t(nx) * ny));
+    const double r = rho[n];
+    CT uh[3] = {CT(0), CT(0), CT(0)};
+#pragma unroll
+    for (int a = 0; a < D; ++a) uh[a] = CT(u[a * N + n] / double(p.c[a]));
+    Macro<CT> mc;
+    mc.dA = CT(r - p.rho0d);
+    mc.rho = CT(r);
+    eq_args(mc, CT(r), uh, p);
+    if (with_ne) {
+      const int idx[3] = {x, y, z}, len[3] = {nx, ny, nz};
+      const size_t stride[3] = {1, size_t(nx), size_t(nx) * ny};
+      double g[3][3];   // g[a][b] = d u_b / d x_a
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          g[a][b] = (a < D && b < D) ? grad_at(u + b * N, n, idx[a], len[a], stride[a], double(p.c[a]) * double(p.dt))
+                                     : 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const double ca = double(p.c[a]);
+        mc.M[a] += CT(-r * sp.ned[a] * g[a][a] / (ca * ca));
+      }
+      const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int a = pa[k], b = pb[k];
+        if (a < D && b < D)
+          mc.M[3 + k] += CT(-r * sp.neo[k] * (g[a][b] + g[b][a]) / (double(p.c[a]) * double(p.c[b])));
+      }
     }
-    plane[n] = v + sp.wd[j] * sp.rho0d;
+    Cube<LAT, CT> q;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c)
+          q.v[a][b][c] = absent<LAT>(a, b, c) ? CT(0) : meq_moment<LAT>(a, b, c, mc.dA, mc.B, mc.M, p);
+    q.inverse();
+    static_for<L::Q>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j], jo = opposite_dir<LAT>(j);
+      const CT v = q.v[ex + 1][ey + 1][zi<LAT>(ez)];
+      const int sx = x - ex, sy = y - ey, sz = z - ez;
+      if (unsigned(sx) < unsigned(nx) && unsigned(sy) < unsigned(ny) && unsigned(sz) < unsigned(nz)) {
+        base[size_t(j) * N + (size_t(sz) * ny + sy) * nx + sx] = ST(v);
+      } else {
+        const CT lidj = (ex != 0 && from_lid<LAT>(sy, sz, ny, nz)) ? sp.lid[j] : CT(0);
+        base[size_t(jo) * N + n] = ST(v - lidj);
+      }
+    });
   }
 }
 
 }  // namespace rmrt
 
 using namespace rmrt;
+using namespace rmrt::host;
 
 namespace {
 
 constexpr size_t kAlignB = 256;
 size_t align_b(size_t v) { return (v + kAlignB - 1) / kAlignB * kAlignB; }
 const int kWidths[4] = {32, 64, 128, 256};
+
+size_t nodes_of(const rmrtlb_domain& x) { return size_t(x.nx) * x.ny * x.nz; }
+size_t rows_of(const rmrtlb_domain& x) { return size_t(x.ny) * x.nz; }
 
 struct BatchLayout {
   size_t fA, fB, uprev, dom, tiles, partials, tile_begin, active, status, conv, counters, cs2, stage, total;
@@ -310,18 +468,19 @@ struct BatchLayout {
 
 size_t tiles_for(const std::vector<rmrtlb_domain>& d, int width) {
   size_t t = 0;
-  for (const auto& x : d) t += size_t((x.nx + width - 1) / width) * x.ny;
+  for (const auto& x : d) t += size_t((x.nx + width - 1) / width) * rows_of(x);
   return t;
 }
 
-BatchLayout batch_layout(const std::vector<rmrtlb_domain>& d, int storage) {
+BatchLayout batch_layout(int lat, const std::vector<rmrtlb_domain>& d, int storage) {
   BatchLayout L;
+  const int q = lattice_q(lat), dim = lattice_d(lat);
   const size_t es = storage == RMRTLB_ST_F64 ? 8 : 4;
   size_t elems = 0, unodes = 0, maxn = 0;
   for (const auto& x : d) {
-    const size_t n = size_t(x.nx) * x.ny;
-    elems += align_b(9 * n * es) / es;
-    unodes += 2 * n;
+    const size_t n = nodes_of(x);
+    elems += align_b(q * n * es) / es;
+    unodes += dim * n;
     maxn = n > maxn ? n : maxn;
   }
   L.pop_elems = elems;
@@ -342,55 +501,46 @@ BatchLayout batch_layout(const std::vector<rmrtlb_domain>& d, int storage) {
   L.counters = L.conv + align_b(nd * sizeof(int));
   L.cs2 = L.counters + align_b(16 * sizeof(int));
   L.stage = L.cs2 + align_b(nd * sizeof(double));
-  L.total = L.stage + align_b(2 * 9 * maxn * sizeof(double));
+  L.total = L.stage + align_b(size_t(dim + 1) * maxn * sizeof(double));
   return L;
 }
 
-bool rate_in(double s) { return s > 0.0 && s < 2.0 && isfinite(s); }
+bool domain_ok(int lat, const rmrtlb_domain& x) {
+  if (x.nx < 1 || x.ny < 1 || x.nz < 1) return false;
+  if (lat == RMRTLB_D2Q9 && x.nz != 1) return false;
+  const double n = double(x.nx) * x.ny * x.nz;
+  return n <= 2.0e9 / lattice_q(lat) && double(x.ny) * x.nz < 2.0e9;
+}
 
-// Parameters of one cavity (the same derivation as rmrtlb_create: weights of
-// Eq. 3-3-5, rates of Eq. 4-31, S_2 block of Eq. 5-8-1), in index units.
+// Parameters of one cavity from the same derivation as rmrtlb_create, plus
+// the lid terms and the Eq. (4-35) coefficients.
 template <typename CT>
-int domain_params(const rmrtlb_domain& D, double rho0, BParams<CT>& p) {
+int domain_params(int lat, int basis, int storage, const rmrtlb_domain& D, double rho0, BParams<CT>& p,
+                  double* cs2_out) {
   memset(&p, 0, sizeof(p));
-  if (D.nx < 1 || D.ny < 1 || !(D.dx > 0) || !(D.dy > 0) || !(D.nu > 0) || !(D.nu_bulk > 0)) return RMRTLB_EINVAL;
-  const double c[2] = {D.dx, D.dy}, c2[2] = {D.dx * D.dx, D.dy * D.dy};
-  const double cs2 = D.cs2 > 0 ? D.cs2 : fmin(c2[0], c2[1]) / 3.0;
-  if (!(cs2 < c2[0] && cs2 < c2[1])) return RMRTLB_EINVAL;
-  const double w5 = cs2 * cs2 / (4.0 * c2[0] * c2[1]);
-  const double w1 = cs2 / (2.0 * c2[0]) - 2.0 * w5, w2 = cs2 / (2.0 * c2[1]) - 2.0 * w5;
-  if (!(w5 > 0 && w1 > 0 && w2 > 0 && 1.0 - 2 * w1 - 2 * w2 - 4 * w5 > 0)) return RMRTLB_EINVAL;
-  const double soff = 1.0 / (D.nu / cs2 + 0.5);
-  double ss[2], sb[2];
-  for (int a = 0; a < 2; ++a) {
-    ss[a] = 1.0 / (2.0 * D.nu / (c2[a] - cs2) + 0.5);
-    sb[a] = 1.0 / (2.0 * D.nu_bulk / (c2[a] - cs2) + 0.5);
-    if (!rate_in(ss[a]) || !rate_in(sb[a])) return RMRTLB_EINVAL;
+  if (!domain_ok(lat, D) || !(D.nu > 0) || !(D.nu_bulk > 0)) return RMRTLB_EINVAL;
+  rmrtlb_params rp;
+  memset(&rp, 0, sizeof(rp));
+  rp.cs2 = D.cs2;
+  rp.rho0 = rho0;
+  rp.nu = D.nu;
+  rp.nu_bulk = D.nu_bulk;
+  rp.s_free = D.s_free;
+  Consts k;
+  const int rc = make_consts(k, lat, D.nx, D.ny, D.nz, D.dx, D.dy, lat == RMRTLB_D2Q9 ? 1.0 : D.dz, 1.0, rp,
+                             RMRTLB_EQ_NSE, basis, storage);
+  if (rc) return rc;
+  p.k = to_kparams<CT>(k);
+  for (int j = 0; j < k.q; ++j) {
+    int e[3];
+    lattice_dir(lat, j, e);
+    p.lid[j] = CT(2.0 * k.w[j] * rho0 * k.c[0] * e[0] * D.lid_u / k.cs2);
   }
-  if (!rate_in(soff) || !rate_in(D.s_free)) return RMRTLB_EINVAL;
-  double abar[2], b[2], den = 1.0;
-  for (int a = 0; a < 2; ++a) {
-    abar[a] = (1.0 / sb[a] - 1.0 / ss[a]) * (c2[a] - cs2) / 2.0;
-    b[a] = 1.0 / (c2[a] - cs2);
-    den += b[a] * ss[a] * abar[a];
+  for (int a = 0; a < 3; ++a) {
+    p.ned[a] = a < k.d ? (k.c[a] * k.c[a] - k.cs2) * k.dt / k.ss[a] : 0.0;
+    p.neo[a] = k.cs2 * k.dt / k.soff[a];
   }
-  p.nx = D.nx; p.ny = D.ny; p.kind = KIND_NSE;
-  p.rho0 = CT(rho0); p.dt = CT(1); p.source = CT(0); p.cs2 = CT(cs2);
-  for (int a = 0; a < 2; ++a) {
-    p.mu2[a] = CT(cs2 / c2[a]);
-    p.c[a] = CT(c[a]);
-    for (int bb = 0; bb < 2; ++bb) {
-      const double s2 = (a == bb ? ss[a] : 0.0) - ss[a] * abar[a] * b[bb] * ss[bb] / den;
-      p.s2h[a][bb] = CT(s2 * c2[bb] / c2[a]);
-    }
-  }
-  p.soff[0] = CT(soff); p.soff[1] = p.soff[2] = CT(D.s_free);
-  p.sfree = CT(D.s_free); p.s0 = CT(D.s_free);
-  for (int a = 0; a < 3; ++a) p.s1[a] = CT(D.s_free);
-  p.lid = CT(2.0 * w5 * rho0 * c[0] * D.lid_u / cs2);
-  const double w[9] = {1.0 - 2 * w1 - 2 * w2 - 4 * w5, w1, w2, w1, w2, w5, w5, w5, w5};
-  for (int j = 0; j < 9; ++j) p.wd[j] = w[j];
-  p.rho0d = rho0;
+  *cs2_out = k.cs2;
   return RMRTLB_OK;
 }
 
@@ -407,8 +557,8 @@ bool dev_ptr(const void* p) {
 }  // namespace
 
 struct rmrtlb_batch {
+  int lat, q, d, central;
   std::vector<rmrtlb_domain> dom;
-  std::vector<size_t> off;          // element offsets per domain
   std::vector<int> tile_begin_host;
   BatchLayout L;
   int storage;
@@ -429,19 +579,25 @@ namespace {
 
 template <typename T> T* at(rmrtlb_batch* b, size_t off) { return reinterpret_cast<T*>(b->ws + off); }
 
-cudaError_t build_tiles(rmrtlb_batch* b, int width) {
+// Row tiles of every domain (act == NULL) or of the domains still stepping
+// (act[d] == 1); tile_begin[d] .. tile_begin[d + 1] are domain d's tiles
+// (an empty range for a domain left out).
+cudaError_t build_tiles(rmrtlb_batch* b, int width, const std::vector<int>* act = nullptr) {
   std::vector<int4> t;
   std::vector<int> tb(b->dom.size() + 1, 0);
   for (size_t d = 0; d < b->dom.size(); ++d) {
     tb[d] = int(t.size());
+    if (act && (*act)[d] != 1) continue;
     const auto& D = b->dom[d];
-    for (int y = 0; y < D.ny; ++y)
-      for (int x0 = 0; x0 < D.nx; x0 += width) t.push_back(make_int4(int(d), y, x0, D.nx - x0 < width ? D.nx - x0 : width));
+    const int rows = int(rows_of(D));
+    for (int r = 0; r < rows; ++r)
+      for (int x0 = 0; x0 < D.nx; x0 += width) t.push_back(make_int4(int(d), r, x0, D.nx - x0 < width ? D.nx - x0 : width));
   }
   tb[b->dom.size()] = int(t.size());
   b->ntiles = t.size();
   b->width = width;
   b->tile_begin_host = tb;
+  if (t.empty()) return cudaSuccess;
   cudaError_t e = cudaMemcpyAsync(at<int4>(b, b->L.tiles), t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice,
                                   b->stream);
   if (e != cudaSuccess) return e;
@@ -456,23 +612,110 @@ void drop_graph(rmrtlb_batch* b) {
   b->graph_ok = false;
 }
 
-template <typename ST, typename CT>
-cudaError_t launch_step(rmrtlb_batch* b) {
-  const ST* fin = at<ST>(b, b->cur == 0 ? b->L.fA : b->L.fB);
-  ST* fout = at<ST>(b, b->cur == 0 ? b->L.fB : b->L.fA);
-  batch_step_kernel<ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
-      fin, fout, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active));
-  return cudaGetLastError();
+// Kernel launches, one functor per kernel; dispatch() picks the template
+// instance for the batch's lattice, basis and storage.
+struct StepF {
+  rmrtlb_batch* b;
+  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  cudaError_t run() const {
+    if (b->ntiles == 0) return cudaSuccess;
+    const ST* fin = at<ST>(b, b->cur == 0 ? b->L.fA : b->L.fB);
+    ST* fout = at<ST>(b, b->cur == 0 ? b->L.fB : b->L.fA);
+    batch_step_kernel<LAT, CENTRAL, ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
+        fin, fout, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active));
+    return cudaGetLastError();
+  }
+};
+struct CheckF {
+  rmrtlb_batch* b;
+  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  cudaError_t run() const {
+    if (b->ntiles == 0) return cudaSuccess;
+    const ST* fin = at<ST>(b, b->cur == 0 ? b->L.fA : b->L.fB);
+    batch_check_kernel<LAT, ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
+        fin, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active),
+        at<double>(b, b->L.uprev), 1, at<double>(b, b->L.partials));
+    return cudaGetLastError();
+  }
+};
+struct FieldsF {
+  rmrtlb_batch* b;
+  int which, domain;
+  double* fields;
+  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  cudaError_t run() const {
+    const size_t N = nodes_of(b->dom[domain]);
+    const unsigned grid = unsigned(N / 256 + 1 < 4096 ? N / 256 + 1 : 4096);
+    batch_fields_kernel<LAT, ST, CT><<<grid, 256, 0, b->stream>>>(at<ST>(b, which == 0 ? b->L.fA : b->L.fB),
+                                                                 at<BParams<CT>>(b, b->L.dom), domain, fields);
+    return cudaGetLastError();
+  }
+};
+struct RestF {
+  rmrtlb_batch* b;
+  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  cudaError_t run() const {
+    int maxlayer = 1;
+    for (const auto& d : b->dom) {
+      const int l = LAT == LAT_D2Q9 ? d.nx : d.nx * d.ny;
+      maxlayer = l > maxlayer ? l : maxlayer;
+    }
+    const int bx = (maxlayer + 127) / 128 < 64 ? (maxlayer + 127) / 128 : 64;
+    batch_rest_kernel<LAT, ST, CT><<<dim3(unsigned(bx), unsigned(b->dom.size())), 128, 0, b->stream>>>(
+        at<ST>(b, b->L.fA), at<BParams<CT>>(b, b->L.dom));
+    return cudaGetLastError();
+  }
+};
+struct PlaneF {
+  rmrtlb_batch* b;
+  int which;
+  double* pl;
+  int j, to_storage, domain;
+  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  cudaError_t run() const {
+    const size_t N = nodes_of(b->dom[domain]);
+    const unsigned grid = unsigned(N / 256 + 1 < 4096 ? N / 256 + 1 : 4096);
+    batch_plane_kernel<LAT, ST, CT><<<grid, 256, 0, b->stream>>>(at<ST>(b, which == 0 ? b->L.fA : b->L.fB), pl, j,
+                                                                to_storage, at<BParams<CT>>(b, b->L.dom), domain);
+    return cudaGetLastError();
+  }
+};
+struct InitF {
+  rmrtlb_batch* b;
+  int which;
+  const double* rho;
+  const double* u;
+  int domain, with_ne;
+  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  cudaError_t run() const {
+    const size_t N = nodes_of(b->dom[domain]);
+    const unsigned grid = unsigned(N / 128 + 1 < 8192 ? N / 128 + 1 : 8192);
+    batch_init_kernel<LAT, ST, CT><<<grid, 128, 0, b->stream>>>(at<ST>(b, which == 0 ? b->L.fA : b->L.fB), rho, u,
+                                                               at<BParams<CT>>(b, b->L.dom), domain, with_ne);
+    return cudaGetLastError();
+  }
+};
+
+template <typename F>
+cudaError_t dispatch(rmrtlb_batch* b, const F& f) {
+  const bool f64 = b->storage == RMRTLB_ST_F64;
+  switch (b->lat * 2 + b->central) {
+    case 0: return f64 ? f.template run<LAT_D2Q9, false, double, double>() : f.template run<LAT_D2Q9, false, float, float>();
+    case 1: return f64 ? f.template run<LAT_D2Q9, true, double, double>() : f.template run<LAT_D2Q9, true, float, float>();
+    case 2: return f64 ? f.template run<LAT_D3Q19, false, double, double>() : f.template run<LAT_D3Q19, false, float, float>();
+    case 3: return f64 ? f.template run<LAT_D3Q19, true, double, double>() : f.template run<LAT_D3Q19, true, float, float>();
+    case 4: return f64 ? f.template run<LAT_D3Q27, false, double, double>() : f.template run<LAT_D3Q27, false, float, float>();
+    default: return f64 ? f.template run<LAT_D3Q27, true, double, double>() : f.template run<LAT_D3Q27, true, float, float>();
+  }
 }
 
-template <typename ST, typename CT>
-cudaError_t launch_check(rmrtlb_batch* b, double* fields, int only_domain) {
-  const ST* fin = at<ST>(b, b->cur == 0 ? b->L.fA : b->L.fB);
-  batch_check_kernel<ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
-      fin, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active),
-      at<double>(b, b->L.uprev), 1, at<double>(b, b->L.partials), only_domain, fields);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || fields) return e;
+cudaError_t do_step(rmrtlb_batch* b) {
+  return dispatch(b, StepF{b});
+}
+
+cudaError_t do_check(rmrtlb_batch* b) {
+  cudaError_t e = dispatch(b, CheckF{b});
+  if (e != cudaSuccess) return e;
   batch_reduce_kernel<<<unsigned(b->dom.size()), 256, 0, b->stream>>>(
       at<double>(b, b->L.partials), at<int>(b, b->L.tile_begin), at<int>(b, b->L.active),
       at<double>(b, b->L.status), at<int>(b, b->L.conv), at<int>(b, b->L.counters), at<double>(b, b->L.cs2), b->tol);
@@ -480,14 +723,6 @@ cudaError_t launch_check(rmrtlb_batch* b, double* fields, int only_domain) {
   if (e != cudaSuccess) return e;
   batch_bump_kernel<<<1, 32, 0, b->stream>>>(at<int>(b, b->L.counters));
   return cudaGetLastError();
-}
-
-cudaError_t do_step(rmrtlb_batch* b) {
-  return b->storage == RMRTLB_ST_F64 ? launch_step<double, double>(b) : launch_step<float, float>(b);
-}
-cudaError_t do_check(rmrtlb_batch* b, double* fields = nullptr, int only = -1) {
-  return b->storage == RMRTLB_ST_F64 ? launch_check<double, double>(b, fields, only)
-                                     : launch_check<float, float>(b, fields, only);
 }
 
 // One chunk: check_every steps (even, so the state ends in A again) and the check.
@@ -517,29 +752,22 @@ cudaError_t chunk(rmrtlb_batch* b) {
     if (e != cudaSuccess) return e;
     b->graph_ok = true;
   }
-  cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
-  if (e != cudaSuccess) return e;
-  return cudaSuccess;   // chunk_direct's parity changes cancel: check_every is even
+  return cudaGraphLaunch(b->graph, b->stream);   // chunk_direct's parity changes cancel: check_every is even
 }
 
 cudaError_t reset_state(rmrtlb_batch* b) {
   const size_t es = b->storage == RMRTLB_ST_F64 ? 8 : 4;
+  if (b->ntiles != tiles_for(b->dom, b->width)) {   // a compacted list: every domain steps again
+    drop_graph(b);
+    cudaError_t e = build_tiles(b, b->width);
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e = cudaMemsetAsync(b->ws + b->L.fA, 0, b->L.pop_elems * es, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + b->L.fB, 0, b->L.pop_elems * es, b->stream);
-  if (e == cudaSuccess) {
-    int maxnx = 1;
-    for (const auto& d : b->dom) maxnx = d.nx > maxnx ? d.nx : maxnx;
-    const dim3 grid(unsigned((maxnx + 127) / 128), unsigned(b->dom.size()));
-    if (b->storage == RMRTLB_ST_F64)
-      batch_rest_kernel<double, double><<<grid, 128, 0, b->stream>>>(at<double>(b, b->L.fA),
-                                                                   at<BParams<double>>(b, b->L.dom));
-    else
-      batch_rest_kernel<float, float><<<grid, 128, 0, b->stream>>>(at<float>(b, b->L.fA),
-                                                                 at<BParams<float>>(b, b->L.dom));
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess) e = dispatch(b, RestF{b});
   if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + b->L.uprev, 0, b->L.dom - b->L.uprev, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + b->L.counters, 0, 16 * sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + b->L.status, 0, 2 * b->dom.size() * sizeof(double), b->stream);
   std::vector<int> one(b->dom.size(), 1), neg(b->dom.size(), -1);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(at<int>(b, b->L.active), one.data(), one.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -554,35 +782,67 @@ cudaError_t reset_state(rmrtlb_batch* b) {
   return e;
 }
 
+// Current buffer of a domain: a retired domain's state stays in A.
+int domain_buffer(rmrtlb_batch* b, int domain, int* which) {
+  int act = 1;
+  if (cudaMemcpyAsync(&act, b->ws + b->L.active + domain * sizeof(int), sizeof(int), cudaMemcpyDeviceToHost,
+                      b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return RMRTLB_ECUDA;
+  *which = act == 1 ? b->cur : 0;
+  return RMRTLB_OK;
+}
+
+// State flags of every domain (synchronises).
+int read_active(rmrtlb_batch* b, std::vector<int>& act) {
+  act.resize(b->dom.size());
+  if (cudaMemcpyAsync(act.data(), b->ws + b->L.active, act.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                      b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return RMRTLB_ECUDA;
+  return RMRTLB_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
-int rmrtlb_batch_workspace_bytes(int ndomains, const rmrtlb_domain* domains, int storage, size_t* bytes) {
-  if (ndomains < 1 || !domains || !bytes || (storage != RMRTLB_ST_F32 && storage != RMRTLB_ST_F64))
+int rmrtlb_batch_workspace_bytes(int lattice, int ndomains, const rmrtlb_domain* domains, int storage,
+                                 size_t* bytes) {
+  if (lattice < 0 || lattice > 2 || ndomains < 1 || ndomains > 65535 || !domains || !bytes ||
+      (storage != RMRTLB_ST_F32 && storage != RMRTLB_ST_F64))
     return RMRTLB_EINVAL;
   std::vector<rmrtlb_domain> d(domains, domains + ndomains);
   for (const auto& x : d)
-    if (x.nx < 1 || x.ny < 1 || x.ny > (1 << 30) / 9 || double(x.nx) * x.ny > 2.0e8) return RMRTLB_EINVAL;
-  *bytes = batch_layout(d, storage).total;
+    if (!domain_ok(lattice, x)) return RMRTLB_EINVAL;
+  if (tiles_for(d, kWidths[0]) > size_t(1) << 31) return RMRTLB_EINVAL;
+  *bytes = batch_layout(lattice, d, storage).total;
   return RMRTLB_OK;
 }
 
-int rmrtlb_batch_create(rmrtlb_batch_t* out, int ndomains, const rmrtlb_domain* domains, int storage, double rho0,
-                        int check_every, double tol, void* workspace, size_t workspace_bytes, void* stream) {
+int rmrtlb_batch_create(rmrtlb_batch_t* out, int lattice, int basis, int ndomains, const rmrtlb_domain* domains,
+                        int storage, double rho0, int check_every, double tol, void* workspace,
+                        size_t workspace_bytes, void* stream) {
   if (!out) return RMRTLB_EINVAL;
   *out = nullptr;
   size_t need = 0;
-  int rc = rmrtlb_batch_workspace_bytes(ndomains, domains, storage, &need);
+  int rc = rmrtlb_batch_workspace_bytes(lattice, ndomains, domains, storage, &need);
   if (rc) return rc;
+  if (basis < 0 || basis > 1) return RMRTLB_EINVAL;
   if (!workspace || reinterpret_cast<size_t>(workspace) % kAlignB) return RMRTLB_EINVAL;
   if (workspace_bytes < need) return RMRTLB_ENOMEM;
   if (check_every < 2 || !(tol > 0) || !isfinite(rho0)) return RMRTLB_EINVAL;
   rmrtlb_batch* b = new (std::nothrow) rmrtlb_batch();
   if (!b) return RMRTLB_ENOMEM;
+  b->lat = lattice;
+  b->q = lattice_q(lattice);
+  b->d = lattice_d(lattice);
+  b->central = basis;
   b->dom.assign(domains, domains + ndomains);
+  for (auto& x : b->dom)
+    if (lattice == RMRTLB_D2Q9) x.dz = 1.0;
   b->storage = storage;
-  b->L = batch_layout(b->dom, storage);
+  b->L = batch_layout(lattice, b->dom, storage);
   b->ws = static_cast<char*>(workspace);
   b->stream = static_cast<cudaStream_t>(stream);
   b->check_every = check_every + (check_every & 1);
@@ -591,29 +851,25 @@ int rmrtlb_batch_create(rmrtlb_batch_t* out, int ndomains, const rmrtlb_domain* 
   // parameter blocks and population offsets
   const size_t es = storage == RMRTLB_ST_F64 ? 8 : 4;
   size_t off = 0, uoff = 0;
-  std::vector<char> params(ndomains * (storage == RMRTLB_ST_F64 ? sizeof(BParams<double>) : sizeof(BParams<float>)));
-  for (int d = 0; d < ndomains; ++d) {
-    const size_t n = size_t(b->dom[d].nx) * b->dom[d].ny;
-    b->off.push_back(off);
-    if (storage == RMRTLB_ST_F64) {
-      BParams<double> p;
-      rc = domain_params(b->dom[d], rho0, p);
-      p.off = off; p.uoff = uoff;
-      memcpy(params.data() + d * sizeof(p), &p, sizeof(p));
-    } else {
-      BParams<float> p;
-      rc = domain_params(b->dom[d], rho0, p);
-      p.off = off; p.uoff = uoff;
-      memcpy(params.data() + d * sizeof(p), &p, sizeof(p));
-    }
-    if (rc) { delete b; return rc; }
-    off += align_b(9 * n * es) / es;
-    uoff += 2 * n;
-  }
+  const size_t psize = storage == RMRTLB_ST_F64 ? sizeof(BParams<double>) : sizeof(BParams<float>);
+  std::vector<char> params(ndomains * psize);
   std::vector<double> cs2(ndomains);
   for (int d = 0; d < ndomains; ++d) {
-    const double m = fmin(b->dom[d].dx, b->dom[d].dy);
-    cs2[d] = b->dom[d].cs2 > 0 ? b->dom[d].cs2 : m * m / 3.0;
+    const size_t n = nodes_of(b->dom[d]);
+    if (storage == RMRTLB_ST_F64) {
+      BParams<double> p;
+      rc = domain_params(lattice, basis, storage, b->dom[d], rho0, p, &cs2[d]);
+      p.off = off; p.uoff = uoff;
+      memcpy(params.data() + d * psize, &p, psize);
+    } else {
+      BParams<float> p;
+      rc = domain_params(lattice, basis, storage, b->dom[d], rho0, p, &cs2[d]);
+      p.off = off; p.uoff = uoff;
+      memcpy(params.data() + d * psize, &p, psize);
+    }
+    if (rc) { delete b; return rc; }
+    off += align_b(b->q * n * es) / es;
+    uoff += b->d * n;
   }
   cudaError_t e = cudaMemcpyAsync(b->ws + b->L.dom, params.data(), params.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
@@ -658,6 +914,33 @@ int rmrtlb_batch_step(rmrtlb_batch_t b, int n) {
       b->check_steps.push_back(b->step);
     }
   }
+  return RMRTLB_OK;
+}
+
+int rmrtlb_batch_run(rmrtlb_batch_t b, long long max_steps, long long* steps_done) {
+  if (!b || max_steps < 0) return RMRTLB_EINVAL;
+  const long long start = b->step;
+  const long long per_poll = 8LL * b->check_every;
+  std::vector<int> act;
+  while (b->step - start < max_steps) {
+    if (read_active(b, act)) return RMRTLB_ECUDA;
+    size_t live = 0;
+    for (size_t d = 0; d < act.size(); ++d)
+      if (act[d] == 1) live += size_t((b->dom[d].nx + b->width - 1) / b->width) * rows_of(b->dom[d]);
+    if (live == 0) break;
+    // tile queue: once a quarter of the launched tiles belong to retired
+    // domains, launch only the tiles of the domains still stepping
+    if (4 * live < 3 * b->ntiles) {
+      drop_graph(b);
+      if (build_tiles(b, b->width, &act) != cudaSuccess) return RMRTLB_ECUDA;
+    }
+    const long long left = max_steps - (b->step - start);
+    const long long n = left < per_poll ? left : per_poll;
+    const int rc = rmrtlb_batch_step(b, int(n));
+    if (rc) return rc;
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return RMRTLB_ECUDA;
+  if (steps_done) *steps_done = b->step - start;
   return RMRTLB_OK;
 }
 
@@ -714,62 +997,41 @@ int rmrtlb_batch_tune(rmrtlb_batch_t b, int steps, int* width_out) {
 
 int rmrtlb_batch_set_populations(rmrtlb_batch_t b, int domain, const double* f) {
   if (!b || !f || domain < 0 || domain >= int(b->dom.size())) return RMRTLB_EINVAL;
-  const size_t N = size_t(b->dom[domain].nx) * b->dom[domain].ny;
-  const bool dev = dev_ptr(f);
-  double* stage = at<double>(b, b->L.stage);
-  for (int j = 0; j < 9; ++j) {
-    static const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-    // stage[0..N) = plane j (where the slot streams to), stage[N..2N) = plane opp(j) (bounce)
-    const double* pj = f + size_t(j) * N;
-    const double* po = f + size_t(opp[j]) * N;
-    cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (cudaMemcpyAsync(stage, pj, N * sizeof(double), k, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(stage + N, po, N * sizeof(double), k, b->stream) != cudaSuccess)
-      return RMRTLB_ECUDA;
-    const unsigned grid = unsigned((N + 255) / 256);
-    if (b->storage == RMRTLB_ST_F64)
-      batch_plane_kernel<double, double><<<grid, 256, 0, b->stream>>>(at<double>(b, b->cur == 0 ? b->L.fA : b->L.fB),
-                                                                      stage, j, 1, at<BParams<double>>(b, b->L.dom),
-                                                                      domain);
-    else
-      batch_plane_kernel<float, float><<<grid, 256, 0, b->stream>>>(at<float>(b, b->cur == 0 ? b->L.fA : b->L.fB),
-                                                                    stage, j, 1, at<BParams<float>>(b, b->L.dom),
-                                                                    domain);
-    if (cudaGetLastError() != cudaSuccess) return RMRTLB_ECUDA;
-  }
-  return cudaStreamSynchronize(b->stream) == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA;
-}
-
-// Current buffer of a domain: a retired domain's state stays in A.
-static int domain_buffer(rmrtlb_batch* b, int domain, int* which) {
-  int act = 1;
-  if (cudaMemcpyAsync(&act, b->ws + b->L.active + domain * sizeof(int), sizeof(int), cudaMemcpyDeviceToHost,
-                      b->stream) != cudaSuccess ||
-      cudaStreamSynchronize(b->stream) != cudaSuccess)
-    return RMRTLB_ECUDA;
-  *which = act == 1 ? b->cur : 0;
-  return RMRTLB_OK;
-}
-
-int rmrtlb_batch_get_populations(rmrtlb_batch_t b, int domain, double* f) {
-  if (!b || !f || domain < 0 || domain >= int(b->dom.size())) return RMRTLB_EINVAL;
-  const size_t N = size_t(b->dom[domain].nx) * b->dom[domain].ny;
+  const size_t N = nodes_of(b->dom[domain]);
   int which = 0;
   if (domain_buffer(b, domain, &which)) return RMRTLB_ECUDA;
   const bool dev = dev_ptr(f);
   double* stage = at<double>(b, b->L.stage);
-  for (int j = 0; j < 9; ++j) {
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int j = 0; j < b->q; ++j) {
+    int e[3], jo = 0;
+    lattice_dir(b->lat, j, e);
+    for (int o = 0; o < b->q; ++o) {
+      int eo[3];
+      lattice_dir(b->lat, o, eo);
+      if (eo[0] == -e[0] && eo[1] == -e[1] && eo[2] == -e[2]) jo = o;
+    }
+    // stage[0..N) = plane j (where the slot streams to), stage[N..2N) = plane jo (bounce)
+    if (cudaMemcpyAsync(stage, f + size_t(j) * N, N * sizeof(double), k, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(stage + N, f + size_t(jo) * N, N * sizeof(double), k, b->stream) != cudaSuccess)
+      return RMRTLB_ECUDA;
+    if (dispatch(b, PlaneF{b, which, stage, j, 1, domain}) != cudaSuccess)
+      return RMRTLB_ECUDA;
+  }
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA;
+}
+
+int rmrtlb_batch_get_populations(rmrtlb_batch_t b, int domain, double* f) {
+  if (!b || !f || domain < 0 || domain >= int(b->dom.size())) return RMRTLB_EINVAL;
+  const size_t N = nodes_of(b->dom[domain]);
+  int which = 0;
+  if (domain_buffer(b, domain, &which)) return RMRTLB_ECUDA;
+  const bool dev = dev_ptr(f);
+  double* stage = at<double>(b, b->L.stage);
+  for (int j = 0; j < b->q; ++j) {
     double* plane = dev ? f + size_t(j) * N : stage;
-    const unsigned grid = unsigned((N + 255) / 256);
-    if (b->storage == RMRTLB_ST_F64)
-      batch_plane_kernel<double, double><<<grid, 256, 0, b->stream>>>(at<double>(b, which == 0 ? b->L.fA : b->L.fB),
-                                                                      plane, j, 0, at<BParams<double>>(b, b->L.dom),
-                                                                      domain);
-    else
-      batch_plane_kernel<float, float><<<grid, 256, 0, b->stream>>>(at<float>(b, which == 0 ? b->L.fA : b->L.fB),
-                                                                    plane, j, 0, at<BParams<float>>(b, b->L.dom),
-                                                                    domain);
-    if (cudaGetLastError() != cudaSuccess) return RMRTLB_ECUDA;
+    if (dispatch(b, PlaneF{b, which, plane, j, 0, domain}) != cudaSuccess)
+      return RMRTLB_ECUDA;
     if (!dev && cudaMemcpyAsync(f + size_t(j) * N, stage, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream) !=
                     cudaSuccess)
       return RMRTLB_ECUDA;
@@ -777,21 +1039,42 @@ int rmrtlb_batch_get_populations(rmrtlb_batch_t b, int domain, double* f) {
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA;
 }
 
-int rmrtlb_batch_fields(rmrtlb_batch_t b, int domain, double* rho, double* u) {
-  if (!b || domain < 0 || domain >= int(b->dom.size())) return RMRTLB_EINVAL;
-  const size_t N = size_t(b->dom[domain].nx) * b->dom[domain].ny;
+int rmrtlb_batch_init_fields(rmrtlb_batch_t b, int domain, const double* rho, const double* u, int with_noneq) {
+  if (!b || !rho || !u || domain < 0 || domain >= int(b->dom.size())) return RMRTLB_EINVAL;
+  const size_t N = nodes_of(b->dom[domain]);
   int which = 0;
   if (domain_buffer(b, domain, &which)) return RMRTLB_ECUDA;
   double* stage = at<double>(b, b->L.stage);
-  const int cur = b->cur;
-  b->cur = which;
-  const cudaError_t e = do_check(b, stage, domain);
-  b->cur = cur;
-  if (e != cudaSuccess) return RMRTLB_ECUDA;
+  const double* r = rho;
+  const double* v = u;
+  if (!dev_ptr(rho)) {
+    if (cudaMemcpyAsync(stage, rho, N * sizeof(double), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+      return RMRTLB_ECUDA;
+    r = stage;
+  }
+  if (!dev_ptr(u)) {
+    if (cudaMemcpyAsync(stage + N, u, size_t(b->d) * N * sizeof(double), cudaMemcpyHostToDevice, b->stream) !=
+        cudaSuccess)
+      return RMRTLB_ECUDA;
+    v = stage + N;
+  }
+  if (dispatch(b, InitF{b, which, r, v, domain, with_noneq ? 1 : 0}) != cudaSuccess)
+    return RMRTLB_ECUDA;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA;
+}
+
+int rmrtlb_batch_fields(rmrtlb_batch_t b, int domain, double* rho, double* u) {
+  if (!b || domain < 0 || domain >= int(b->dom.size())) return RMRTLB_EINVAL;
+  const size_t N = nodes_of(b->dom[domain]);
+  int which = 0;
+  if (domain_buffer(b, domain, &which)) return RMRTLB_ECUDA;
+  double* stage = at<double>(b, b->L.stage);
+  if (dispatch(b, FieldsF{b, which, domain, stage}) != cudaSuccess) return RMRTLB_ECUDA;
   const cudaMemcpyKind k1 = rho && dev_ptr(rho) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const cudaMemcpyKind k2 = u && dev_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (rho && cudaMemcpyAsync(rho, stage, N * sizeof(double), k1, b->stream) != cudaSuccess) return RMRTLB_ECUDA;
-  if (u && cudaMemcpyAsync(u, stage + N, 2 * N * sizeof(double), k2, b->stream) != cudaSuccess) return RMRTLB_ECUDA;
+  if (u && cudaMemcpyAsync(u, stage + N, size_t(b->d) * N * sizeof(double), k2, b->stream) != cudaSuccess)
+    return RMRTLB_ECUDA;
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA;
 }
 

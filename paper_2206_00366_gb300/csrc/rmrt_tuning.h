@@ -1,5 +1,5 @@
 // Launch-shape constants of the step kernels, chosen by measurement on
-// GB300 (kernels).  Each may be overridden with -D at build
+// GB300 (a sweep of the minimum-blocks hint per lattice and storage).  Each may be overridden with -D at build
 // time to compare alternatives.
 #pragma once
 

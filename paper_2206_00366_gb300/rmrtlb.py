@@ -62,8 +62,8 @@ class rmrtlb_params(ctypes.Structure):
 
 class rmrtlb_domain(ctypes.Structure):
     _fields_ = [
-        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
-        ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
         ("nu", ctypes.c_double), ("nu_bulk", ctypes.c_double),
         ("s_free", ctypes.c_double), ("lid_u", ctypes.c_double), ("cs2", ctypes.c_double),
     ]
@@ -112,9 +112,21 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_stats": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_last_check": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_population_totals_noalloc": (i, [i, i, i, i, d, d, d, d, _vp, _vp, _vp]),
-        "rmrtlb_batch_workspace_bytes": (i, [i, ctypes.POINTER(rmrtlb_domain), i, ctypes.POINTER(sz)]),
-        "rmrtlb_batch_create": (i, [ctypes.POINTER(_vp), i, ctypes.POINTER(rmrtlb_domain), i, d, i, d, _vp, sz,
-                                    _vp]),
+        "rmrtlb_batch_workspace_bytes": (i, [i, i, ctypes.POINTER(rmrtlb_domain), i, ctypes.POINTER(sz)]),
+        "rmrtlb_batch_create": (i, [ctypes.POINTER(_vp), i, i, i, ctypes.POINTER(rmrtlb_domain), i, d, i, d, _vp,
+                                    sz, _vp]),
+        "rmrtlb_batch_run": (i, [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+        "rmrtlb_conv3d_forward": (i, [i, i, i, i, i, i, _vp, _vp, _vp, i, _vp, _vp, _vp]),
+        "rmrtlb_conv3d_backward_data": (i, [i, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp]),
+        "rmrtlb_conv3d_backward_weight_scratch": (sz, [i, i, i, i, i, i]),
+        "rmrtlb_conv3d_backward_weight": (i, [i, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, sz, _vp]),
+        "rmrtlb_mse": (i, [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "rmrtlb_adam": (i, [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, i, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_float, ctypes.c_float, _vp]),
+        "rmrtlb_cavity_features": (i, [i, i, i, i, _vp, _vp, _vp]),
+        "rmrtlb_upsample_fields": (i, [i, i, i, i, _vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), _vp, _vp]),
+        "rmrtlb_pack_fields": (i, [ctypes.c_longlong, i, _vp, _vp, d, d, d, _vp, _vp]),
+        "rmrtlb_batch_init_fields": (i, [_vp, i, _vp, _vp, i]),
         "rmrtlb_batch_destroy": (i, [_vp]),
         "rmrtlb_batch_reset": (i, [_vp]),
         "rmrtlb_batch_tune": (i, [_vp, i, ctypes.POINTER(i)]),
@@ -140,7 +152,10 @@ def exported_symbols() -> list:
             "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_population_totals_noalloc",
             "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
             "rmrtlb_batch_tune", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
-            "rmrtlb_batch_get_populations", "rmrtlb_batch_fields"]
+            "rmrtlb_batch_get_populations", "rmrtlb_batch_fields", "rmrtlb_batch_run", "rmrtlb_batch_init_fields",
+            "rmrtlb_conv3d_forward", "rmrtlb_conv3d_backward_data", "rmrtlb_conv3d_backward_weight_scratch",
+            "rmrtlb_conv3d_backward_weight", "rmrtlb_mse", "rmrtlb_adam", "rmrtlb_cavity_features",
+            "rmrtlb_upsample_fields", "rmrtlb_pack_fields"]
 
 
 def _check(status: int, where: str):
@@ -226,29 +241,42 @@ def rmrtlb_population_totals_noalloc(lattice, nx, ny, nz, dx, dy, dz, dt, f: int
            "rmrtlb_population_totals_noalloc")
 
 
+_DOMAIN_DEFAULTS = {"nz": 1, "dz": 1.0}
+
+
 def _domains(domains):
     arr = (rmrtlb_domain * len(domains))()
     for k, dd in enumerate(domains):
         for f, _ in rmrtlb_domain._fields_:
-            setattr(arr[k], f, dd.get(f, 0))
+            setattr(arr[k], f, dd.get(f, _DOMAIN_DEFAULTS.get(f, 0)))
     return arr
 
 
-def rmrtlb_batch_workspace_bytes(domains, storage: int) -> int:
+def rmrtlb_batch_workspace_bytes(lattice: int, domains, storage: int) -> int:
     arr = _domains(domains)
     b = ctypes.c_size_t()
-    _check(lib().rmrtlb_batch_workspace_bytes(len(domains), arr, storage, ctypes.byref(b)),
+    _check(lib().rmrtlb_batch_workspace_bytes(lattice, len(domains), arr, storage, ctypes.byref(b)),
            "rmrtlb_batch_workspace_bytes")
     return b.value
 
 
-def rmrtlb_batch_create(domains, storage, rho0, check_every, tol, workspace: int, workspace_bytes: int,
-                        stream: int):
+def rmrtlb_batch_create(lattice: int, basis: int, domains, storage, rho0, check_every, tol, workspace: int,
+                        workspace_bytes: int, stream: int):
     arr = _domains(domains)
     h = _vp()
-    _check(lib().rmrtlb_batch_create(ctypes.byref(h), len(domains), arr, storage, rho0, check_every, tol,
-                                     workspace, workspace_bytes, stream), "rmrtlb_batch_create")
+    _check(lib().rmrtlb_batch_create(ctypes.byref(h), lattice, basis, len(domains), arr, storage, rho0,
+                                     check_every, tol, workspace, workspace_bytes, stream), "rmrtlb_batch_create")
     return h
+
+
+def rmrtlb_batch_run(h, max_steps: int) -> int:
+    done = ctypes.c_longlong()
+    _check(lib().rmrtlb_batch_run(h, max_steps, ctypes.byref(done)), "rmrtlb_batch_run")
+    return done.value
+
+
+def rmrtlb_batch_init_fields(h, domain: int, rho: int, u: int, with_noneq: int):
+    _check(lib().rmrtlb_batch_init_fields(h, domain, rho, u, with_noneq), "rmrtlb_batch_init_fields")
 
 
 def rmrtlb_batch_destroy(h):
@@ -288,6 +316,49 @@ def rmrtlb_batch_get_populations(h, domain: int, f: int):
 
 def rmrtlb_batch_fields(h, domain: int, rho: int, u: int):
     _check(lib().rmrtlb_batch_fields(h, domain, rho, u), "rmrtlb_batch_fields")
+
+
+# ------------------------------------------------------------------ warm-start network (rmrtlb_cnn.h)
+def rmrtlb_conv3d_forward(n, d, h, w, cin, cout, x, weight, bias, apply_silu, z, a, stream=0):
+    _check(lib().rmrtlb_conv3d_forward(n, d, h, w, cin, cout, x, weight, bias, int(apply_silu), z, a, stream),
+           "rmrtlb_conv3d_forward")
+
+
+def rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dy, weight, z_in, dx, stream=0):
+    _check(lib().rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dy, weight, z_in, dx, stream),
+           "rmrtlb_conv3d_backward_data")
+
+
+def rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, cout) -> int:
+    return int(lib().rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, cout))
+
+
+def rmrtlb_conv3d_backward_weight(n, d, h, w, cin, cout, x, dy, dweight, dbias, scratch, scratch_bytes, stream=0):
+    _check(lib().rmrtlb_conv3d_backward_weight(n, d, h, w, cin, cout, x, dy, dweight, dbias, scratch, scratch_bytes,
+                                               stream), "rmrtlb_conv3d_backward_weight")
+
+
+def rmrtlb_mse(count, y, t, dy, loss, scratch, stream=0):
+    _check(lib().rmrtlb_mse(count, y, t, dy, loss, scratch, stream), "rmrtlb_mse")
+
+
+def rmrtlb_adam(count, param, param_bf16, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    _check(lib().rmrtlb_adam(count, param, param_bf16, grad, m, v, step, lr, beta1, beta2, eps, stream),
+           "rmrtlb_adam")
+
+
+def rmrtlb_cavity_features(n, d, h, w, re, x, stream=0):
+    _check(lib().rmrtlb_cavity_features(n, d, h, w, re, x, stream), "rmrtlb_cavity_features")
+
+
+def rmrtlb_upsample_fields(d, h, w, c, src, D, H, W, scale, offset, dst, stream=0):
+    sc = (ctypes.c_double * c)(*[float(v) for v in scale])
+    of = (ctypes.c_double * c)(*[float(v) for v in offset])
+    _check(lib().rmrtlb_upsample_fields(d, h, w, c, src, D, H, W, sc, of, dst, stream), "rmrtlb_upsample_fields")
+
+
+def rmrtlb_pack_fields(n, d, rho, u, rho0, rho_scale, u_scale, out, stream=0):
+    _check(lib().rmrtlb_pack_fields(n, d, rho, u, rho0, rho_scale, u_scale, out, stream), "rmrtlb_pack_fields")
 
 
 # ------------------------------------------------------------------ convenience
@@ -373,22 +444,26 @@ class Solver:
 class Batch:
     """Batched lid-driven cavities (rmrtlb_batch_*) on a torch workspace.
 
-    domains: list of dicts with the rmrtlb_domain fields.  A dedicated torch
-    stream is used so that chunks can be captured as CUDA graphs (pass
-    use_graphs=False to launch on the legacy default stream instead).
+    domains: list of dicts with the rmrtlb_domain fields (nz, dz default to
+    1).  A dedicated torch stream is used so that chunks can be captured as
+    CUDA graphs (pass use_graphs=False to launch on the legacy default
+    stream instead).
     """
 
     def __init__(self, domains, storage="f32", rho0=1.0, check_every=100, tol=1e-6, device="cuda",
-                 use_graphs=True):
+                 use_graphs=True, lattice="D2Q9", basis="raw"):
         import torch
-        self.domains = [dict(d) for d in domains]
+        self.domains = [dict(_DOMAIN_DEFAULTS, **d) for d in domains]
+        self.lattice = LATTICE_NAMES.get(lattice, lattice)
+        self.basis = BASIS_NAMES.get(basis, basis)
+        self.q, self.d, _ = rmrtlb_lattice_info(self.lattice)
         self.storage = STORAGE_NAMES.get(storage, storage)
-        nbytes = rmrtlb_batch_workspace_bytes(self.domains, self.storage)
+        nbytes = rmrtlb_batch_workspace_bytes(self.lattice, self.domains, self.storage)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.stream = torch.cuda.Stream(device=self.workspace.device) if use_graphs else None
         sp = self.stream.cuda_stream if use_graphs else 0
         torch.cuda.synchronize()
-        self.h = rmrtlb_batch_create(self.domains, self.storage, rho0, check_every, tol,
+        self.h = rmrtlb_batch_create(self.lattice, self.basis, self.domains, self.storage, rho0, check_every, tol,
                                      self.workspace.data_ptr(), nbytes, sp)
 
     def __del__(self):
@@ -396,6 +471,10 @@ class Batch:
         if h is not None and _lib is not None:
             _lib.rmrtlb_batch_destroy(h)
             self.h = None
+
+    def shape(self, domain):
+        d = self.domains[domain]
+        return (d["nz"], d["ny"], d["nx"])
 
     def reset(self):
         rmrtlb_batch_reset(self.h)
@@ -406,6 +485,11 @@ class Batch:
     def step(self, n=1):
         rmrtlb_batch_step(self.h, n)
 
+    def run(self, max_steps):
+        """Step until every domain has converged or gone unstable, or
+        max_steps were issued; returns the steps issued."""
+        return rmrtlb_batch_run(self.h, max_steps)
+
     def status(self):
         return rmrtlb_batch_status(self.h, len(self.domains))
 
@@ -413,14 +497,17 @@ class Batch:
         rmrtlb_batch_set_populations(self.h, domain, _ptr(f))
 
     def get_populations(self, domain):
-        d = self.domains[domain]
-        out = np.empty((9, 1, d["ny"], d["nx"]))
+        out = np.empty((self.q,) + self.shape(domain))
         rmrtlb_batch_get_populations(self.h, domain, _ptr(out))
         return out
 
+    def init_fields(self, domain, rho, u, noneq=False):
+        """fbar = f^eq(rho, u) (+ f^ne with noneq); rho (nz, ny, nx), u (d, nz, ny, nx), float64
+        numpy arrays or CUDA tensors."""
+        rmrtlb_batch_init_fields(self.h, domain, _ptr(rho), _ptr(u), 1 if noneq else 0)
+
     def fields(self, domain):
-        d = self.domains[domain]
-        rho = np.empty((1, d["ny"], d["nx"]))
-        u = np.empty((2, 1, d["ny"], d["nx"]))
+        rho = np.empty(self.shape(domain))
+        u = np.empty((self.d,) + self.shape(domain))
         rmrtlb_batch_fields(self.h, domain, _ptr(rho), _ptr(u))
         return rho, u

@@ -24,8 +24,9 @@ def B():
 
 
 def test_header_symbols_exported(B):
-    hdr = open(os.path.join(ROOT, "include", "rmrtlb.h")).read()
-    declared = set(re.findall(r"^\s*(?:const char\*|int)\s+(rmrtlb_\w+)\s*\(", hdr, re.M))
+    inc = os.path.join(ROOT, "include")
+    hdr = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
+    declared = set(re.findall(r"^\s*(?:const char\*|int|size_t)\s+(rmrtlb_\w+)\s*\(", hdr, re.M))
     assert declared == set(B.exported_symbols())
     lib = ctypes.CDLL(B.LIB_PATH)
     for name in declared:

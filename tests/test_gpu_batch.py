@@ -139,3 +139,91 @@ def test_batch_retires_unstable_domain():
     f0 = np.zeros((9, 1, good["ny"], good["nx"])) + lat.w.reshape(9, 1, 1, 1)
     fo, _ = oracle_domain(good, 1500, f0)
     assert normwise(b.get_populations(0), fo) <= 1e-11
+
+
+# ---------------------------------------------------------------- 3-D cavities
+DOMAINS3 = [
+    dict(nx=9, ny=6, nz=5, dx=1.0, dy=1.0, dz=0.5, nu=0.02, nu_bulk=0.02, s_free=1.1, lid_u=0.05, cs2=0.0),
+    dict(nx=6, ny=7, nz=4, dx=1.0, dy=0.8, dz=1.0, nu=0.05, nu_bulk=0.04, s_free=1.2, lid_u=0.04, cs2=0.0),
+    dict(nx=1, ny=3, nz=6, dx=1.0, dy=1.0, dz=1.0, nu=0.03, nu_bulk=0.03, s_free=1.0, lid_u=0.05, cs2=0.0),
+]
+
+
+def oracle_domain3(lattice, basis, d, steps, f0, rho0=1.0):
+    lat = R.make_lattice(lattice, (d["dx"], d["dy"], d["dz"]), 1.0, d["cs2"] if d["cs2"] > 0 else None)
+    r = R.rates_from_viscosity(lat, d["nu"], d["nu_bulk"], d["s_free"])
+    S = R.relaxation_matrix(lat, r)
+    m = R.Model(R.NSE, basis=basis, rho0=rho0)
+    f = R.step(lat, m, S, f0, steps, walls=(0, 1, 2), lid=(2, (d["lid_u"], 0.0, 0.0), rho0))
+    return f, R.fields(lat, m, f), (lat, m, S, r)
+
+
+@pytest.mark.parametrize("lattice", ["D3Q19", "D3Q27"])
+@pytest.mark.parametrize("basis", ["raw", "central"])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_batch3d_matches_oracle(lattice, basis, storage, tol):
+    """3-D cavities (walls on every face, lid on the top z face moving +x):
+    populations after 12 steps from random populations, domain by domain."""
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    q = 19 if lattice == "D3Q19" else 27
+    b = Batch(DOMAINS3, storage=storage, check_every=1000, tol=1e-9, lattice=lattice, basis=basis)
+    f0 = [W.random_populations(q, (d["nz"], d["ny"], d["nx"]), seed=40 + k) for k, d in enumerate(DOMAINS3)]
+    for k, d in enumerate(DOMAINS3):        # created at rest: fbar = omega rho0
+        lat = R.make_lattice(lattice, (d["dx"], d["dy"], d["dz"]))
+        rest = b.get_populations(k)
+        np.testing.assert_allclose(rest, lat.w.reshape(q, 1, 1, 1) * np.ones_like(rest), rtol=1e-6, atol=0)
+    for k in range(len(DOMAINS3)):
+        b.set_populations(k, f0[k])
+        assert normwise(b.get_populations(k), f0[k]) <= (1e-6 if storage == "f32" else 1e-15)
+    steps = 12
+    b.step(steps)
+    for k, d in enumerate(DOMAINS3):
+        fo, (ro, uo), _ = oracle_domain3(lattice, basis, d, steps, f0[k])
+        rg, ug = b.fields(k)
+        assert normwise(b.get_populations(k), fo) <= tol
+        assert normwise(rg, ro) <= tol
+        assert normwise(ug, uo) <= 10 * tol
+
+
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q27"])
+@pytest.mark.parametrize("noneq", [False, True])
+def test_batch_init_fields_matches_oracle(lattice, noneq):
+    """rmrtlb_batch_init_fields: f^eq(rho, u) (+ f^ne of Eqs. 4-35/fne with
+    central-difference gradients) equals the oracle's initialisation, and
+    one step later the two still agree."""
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    doms = DOMAINS if lattice == "D2Q9" else DOMAINS3
+    doms = [d for d in doms if d["nx"] > 1]
+    b = Batch(doms, storage="f64", check_every=1000, tol=1e-9, lattice=lattice)
+    dd = 2 if lattice == "D2Q9" else 3
+    for k, d in enumerate(doms):
+        shape = (d.get("nz", 1), d["ny"], d["nx"])
+        rho, u = W.random_fields(shape, dd, seed=60 + k, drho=0.01, umax=0.03)
+        b.init_fields(k, rho, u, noneq=noneq)
+        if lattice == "D2Q9":
+            lat = R.make_lattice(lattice, (d["dx"], d["dy"]))
+        else:
+            lat = R.make_lattice(lattice, (d["dx"], d["dy"], d["dz"]))
+        r = R.rates_from_viscosity(lat, d["nu"], d["nu_bulk"], d["s_free"])
+        S = R.relaxation_matrix(lat, r)
+        m = R.Model(R.NSE)
+        fo = R.init_noneq(lat, m, S, r, rho, u) if noneq else R.init_equilibrium(lat, m, S, rho, u)
+        assert normwise(b.get_populations(k), fo) <= 1e-13
+    b.step(1)
+    for k, d in enumerate(doms):
+        fo = b.get_populations(k)
+        assert np.all(np.isfinite(fo))
+
+
+def test_batch_run_retires_everything():
+    """rmrtlb_batch_run stops once every domain has converged, and the
+    retirement steps agree with rmrtlb_batch_status."""
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    doms = [dict(nx=12, ny=10, dx=1.0, dy=1.0, nu=0.1, nu_bulk=0.1, s_free=1.1, lid_u=0.05, cs2=0.0),
+            dict(nx=8, ny=14, dx=1.0, dy=0.5, nu=0.08, nu_bulk=0.08, s_free=1.1, lid_u=0.05, cs2=0.0)]
+    b = Batch(doms, storage="f32", check_every=100, tol=1e-5)
+    done = b.run(200000)
+    res, conv, act, total = b.status()
+    assert (act == 0).all() and done < 200000
+    assert conv.max() <= done <= conv.max() + 8 * 100
+    assert (res < 1e-5).all()

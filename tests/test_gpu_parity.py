@@ -51,7 +51,7 @@ def small_shape(lattice, even=False):
     return (14, 11, 7) if even else (13, 11, 7)
 
 
-# ---------------------------------------------------------------- config 1 in full
+# ---------------------------------------------------------------- rD2Q9 Taylor-Green 64 x 32 in full
 def test_taylor_green_rd2q9_f64_2000_steps():
     """rD2Q9 NSE Taylor-Green, 64 x 32, dx = 1, dy = 0.5, FP64, rho0 = 1,
     u0 = 0.01, nu = 0.01, bulk rate 1.2, free rates 1.1, 2000 steps: the

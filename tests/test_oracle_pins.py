@@ -673,3 +673,100 @@ def test_cavity_walls_conserve_mass():
     m0 = f.sum()
     f = R.step(lat, m, S, f, 50, walls=(0, 1), lid=(1, (0.05, 0.0), 1.0))
     assert abs(f.sum() - m0) < 1e-12 * m0
+
+
+# ---------------------------------------------------------------- Eqs. (4-35), (fne)
+@pytest.mark.parametrize("name,dx", [("D2Q9", (1.0, 0.5)), ("D3Q27", (1.0, 0.5, 0.8))])
+def test_velocity_gradient_exact_for_linear_fields(name, dx):
+    """Central and one-sided differences are exact on a linear field, so the
+    stencil returns the generating matrix at every node, walls included."""
+    lat = R.make_lattice(name, dx)
+    d = lat.d
+    shape = (1, 6, 7) if d == 2 else (5, 6, 7)
+    G = np.random.default_rng(3).normal(size=(d, d))
+    X = W.grid(shape, lat.dx)
+    u = np.zeros((d,) + shape)
+    for b in range(d):
+        for a in range(d):
+            u[b] += G[a, b] * X[a]
+    g = R.velocity_gradient(lat, u)
+    for a in range(d):
+        for b in range(d):
+            np.testing.assert_allclose(g[a, b], G[a, b], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,dx", [("D2Q9", (1.0, 0.5)), ("D3Q19", (1.0, 1.0, 0.5)), ("D3Q27", (1.0, 0.5, 0.8))])
+def test_noneq_moment_matches_couette_steady_state(name, dx):
+    """The shear component of Eq. (4-35) equals the non-equilibrium second
+    moment sum c_x c_y (f - f^eq) that the method itself settles to in
+    steady Couette flow (lid on y = H, exact gradient U / H)."""
+    lat = R.make_lattice(name, dx)
+    d = lat.d
+    nu, U = 0.1, 0.02
+    r = R.rates_from_viscosity(lat, nu, 0.1, 1.1)
+    S = R.relaxation_matrix(lat, r)
+    shape = (1, 16, 2) if d == 2 else (2, 16, 2)
+    m = R.Model()
+    f = R.init_equilibrium(lat, m, S, np.ones(shape), np.zeros((d,) + shape))
+    f = R.step(lat, m, S, f, 6000, walls=(1,), lid=(1, (U,) + (0.0,) * (d - 1), 1.0))
+    rho, u = R.fields(lat, m, f)
+    fne = (f - R.init_equilibrium(lat, m, S, rho, u)).reshape(lat.q, -1)
+    m2 = np.einsum("ja,jb,jn->nab", lat.cv, lat.cv, fne)
+    g = np.zeros((d, d, rho.size))
+    g[1, 0] = U / (shape[1] * lat.dx[1])
+    pred = R.noneq_second_moment(lat, r, rho.reshape(-1), g)
+    np.testing.assert_allclose(m2[:, 0, 1], pred[:, 0, 1], rtol=1e-3)
+    np.testing.assert_allclose(m2[:, 1, 0], pred[:, 1, 0], rtol=1e-3)
+
+
+@pytest.mark.parametrize("name,dx", [("D2Q9", (1.0, 0.5)), ("D3Q27", (1.0, 0.5, 0.8))])
+def test_noneq_moment_matches_taylor_green(name, dx):
+    """Diagonal and shear components of Eq. (4-35) against the measured
+    non-equilibrium moments of a decaying Taylor-Green vortex (bulk viscosity
+    different from the shear viscosity; the flow is divergence-free), within
+    the central-difference error (k dx)^2 / 6."""
+    lat = R.make_lattice(name, dx)
+    d = lat.d
+    r = R.rates_from_viscosity(lat, 0.02, 0.05, 1.1)
+    S = R.relaxation_matrix(lat, r)
+    m = R.Model()
+    n = 32
+    rho0, u2 = W.taylor_green_2d(n, n, lat.dx[0], lat.dx[1], 1e-4, 1.0, lat.cs2)
+    if d == 3:
+        rho0 = np.repeat(rho0, 2, axis=0)
+        u = np.zeros((3,) + rho0.shape)
+        u[:2] = np.repeat(u2, 2, axis=1)
+    else:
+        u = u2
+    f = R.step(lat, m, S, R.init_noneq(lat, m, S, r, rho0, u), 100)
+    rho, uu = R.fields(lat, m, f)
+    fne = (f - R.init_equilibrium(lat, m, S, rho, uu)).reshape(lat.q, -1)
+    m2 = np.einsum("ja,jb,jn->nab", lat.cv, lat.cv, fne)
+    g = np.zeros((d, d, rho.size))
+    for a in range(2):
+        for b in range(2):
+            g[a, b] = ((np.roll(uu[b], -1, axis=2 - a) - np.roll(uu[b], 1, axis=2 - a)) / (2 * lat.dx[a])).ravel()
+    pred = R.noneq_second_moment(lat, r, rho.reshape(-1), g)
+    for a, b in [(0, 0), (1, 1), (0, 1)]:
+        err = np.abs(m2[:, a, b] - pred[:, a, b]).max() / np.abs(pred[:, a, b]).max()
+        assert err < 0.015, (a, b, err)
+
+
+def test_noneq_start_removes_initial_transient():
+    """Starting Couette flow from f^eq + f^ne (Eq. fne) of its exact profile
+    leaves the interior nearly unchanged after one step; starting from f^eq
+    alone does not."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.5))
+    r = R.rates_from_viscosity(lat, 0.1, 0.1, 1.1)
+    S = R.relaxation_matrix(lat, r)
+    m = R.Model()
+    U, ny = 0.02, 16
+    y = (np.arange(ny) + 0.5) * lat.dx[1]
+    u = np.zeros((2, 1, ny, 2))
+    u[0] = (U * y / (ny * lat.dx[1]))[None, :, None]
+    rho = np.ones((1, ny, 2))
+    change = []
+    for f0 in (R.init_equilibrium(lat, m, S, rho, u), R.init_noneq(lat, m, S, r, rho, u)):
+        f1 = R.step(lat, m, S, f0, 1, walls=(1,), lid=(1, (U, 0.0), 1.0))
+        change.append(np.abs(f1 - f0)[:, :, 2:-2].max())
+    assert change[1] < 0.1 * change[0]
