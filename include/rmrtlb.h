@@ -77,9 +77,18 @@ enum rmrtlb_eq_kind {
     RMRTLB_EQ_NCDE_QUAD = 3
 };
 
-/* Moment basis of the relaxation: raw moments (Eq. 5-2) or central moments
- * about the local velocity (Eq. 5-1-2 with N = N(u)). */
-enum rmrtlb_basis { RMRTLB_BASIS_RAW = 0, RMRTLB_BASIS_CENTRAL = 1 };
+/* Moment basis of the relaxation, Mbar = N M (Eqs. 5-1-1, 5-1-2): raw
+ * moments (Eq. 5-2, N = I); central moments about the local velocity
+ * (N = N(u)); Hermite moments, the tensor products of P_0 = 1, P_1 = c,
+ * P_2 = c^2 - c_s^2 per axis; central-Hermite moments, the same polynomials
+ * of c - u.  The relaxation matrix Sbar has the same blocks in every basis
+ * (rates of Eq. 4-31, S_2 block of Eq. 5-8-1, s_free for orders >= 3). */
+enum rmrtlb_basis {
+    RMRTLB_BASIS_RAW = 0,
+    RMRTLB_BASIS_CENTRAL = 1,
+    RMRTLB_BASIS_HERMITE = 2,
+    RMRTLB_BASIS_CENTRAL_HERMITE = 3
+};
 
 /* Population storage.  Every kind stores the deviation fbar_j - omega_j rho0;
  * F16 and BF16 store it times the power of two nearest 1/omega_j (exact to
@@ -186,6 +195,19 @@ int rmrtlb_step(rmrtlb_t solver, int n);
  * rho (or phi) one plane, u d planes (the advection velocity for the
  * NCDE).  Either pointer may be NULL. */
 int rmrtlb_moments(rmrtlb_t solver, double* rho, double* u);
+
+/* Local viscous stress and strain rate of the current state, NSE kinds
+ * only (RMRTLB_EINVAL otherwise), Eqs. (4-32) and (4-33): with
+ *   X = sum_k c_k c_k f_k^ne + (dt/2)(u Fbar + Fbar u + c_s^2 Sbar I),
+ *   stress_ab = K_mu,ab (d_a u_b + d_b u_a) = -(1 - s_ab/2) X_ab,
+ *   strain_ab = (d_a u_b + d_b u_a)/2 = stress_ab / (2 K_mu,ab),
+ * every product entry by entry, s_aa = s_sa, s_ab the off-diagonal rates,
+ * K_mu of Eq. (4-29a) at the local density, f^ne from the node's own
+ * populations (no finite differences).  Each output is d(d+1)/2 FP64
+ * planes of nz*ny*nx in the order xx, yy, (zz), xy, (xz, yz), DEVICE
+ * memory (RMRTLB_EINVAL for a host pointer); either may be NULL.
+ * Asynchronous on the solver's stream. */
+int rmrtlb_stress(rmrtlb_t solver, double* stress, double* strain_rate);
 
 /* Run the FP64 check on the current populations now and return, after
  * synchronising the stream:

@@ -23,6 +23,7 @@ paper's order and notation:
 * forced moment-space step .......... Eqs. (2-3), (2-2-3), (2-4-1), (2-4-2)
 * propagation ....................... Eq. (2-2b)
 * non-equilibrium initialisation .... Eqs. (4-29), (4-35), (fne)
+* local stress and strain rate ...... Eqs. (4-32), (4-33)
 
 Matrices are built numerically (M from the monomial list over the velocity
 set, M^-1 and the S_2 block by numerical inversion, m^eq = M f^eq from the
@@ -198,20 +199,26 @@ def moment_matrix(lat: Lattice) -> np.ndarray:
     return M
 
 
-def central_moment_matrices(lat: Lattice, u: np.ndarray) -> np.ndarray:
-    """Per-node central-moment matrices Mbar(u) = N(u) M, shape (n, q, q).
+def central_moment_matrices(lat: Lattice, u: np.ndarray, hermite: bool = False) -> np.ndarray:
+    """Per-node moment matrices Mbar(u) = N(u) M of Sec. V, shape (n, q, q).
 
-    Row k is (c_{jx}-u_x)^m (c_{jy}-u_y)^n (c_{jz}-u_z)^p over j, the
-    central-moment (cascaded) basis that Sec. V, Eqs. (5-1-1)/(5-1-2) relate
-    to the raw basis through a lower-triangular N.  u has shape (n, d).
+    Row k of the monomial (m, n, p) is evaluated over the velocities j as
+    prod_a P_k_a(c_ja - u_a): with P_k(xi) = xi^k the central-moment
+    (cascaded) basis; with hermite, P_0 = 1, P_1 = xi, P_2 = xi^2 - c_s^2
+    (the Hermite polynomials with the lattice's c_s^2), which gives the
+    Hermite basis at u = 0 and the central-Hermite basis at the local u.
+    Both are raw moments times a lower-triangular N (Eq. 5-1-1).  u (n, d).
     """
     mons = monomials(lat.name)
     n = u.shape[0]
     Mb = np.ones((n, len(mons), lat.q))
     for k, a in enumerate(mons):
         for al in range(lat.d):
-            if a[al]:
-                Mb[:, k, :] *= (lat.cv[None, :, al] - u[:, al, None]) ** a[al]
+            xi = lat.cv[None, :, al] - u[:, al, None]
+            if hermite:
+                Mb[:, k, :] *= (1.0, xi, xi * xi - lat.cs2)[a[al]] if a[al] else 1.0
+            elif a[al]:
+                Mb[:, k, :] *= xi ** a[al]
     return Mb
 
 
@@ -361,7 +368,7 @@ def s2_apply(lat: Lattice, S: np.ndarray, X: np.ndarray) -> np.ndarray:
 # Model closures (Sec. IV)
 # --------------------------------------------------------------------------
 NSE, NSE_HELUO, NCDE_LINEAR, NCDE_QUAD = "nse", "nse_heluo", "ncde_linear", "ncde_quad"
-RAW, CENTRAL = "raw", "central"
+RAW, CENTRAL, HERMITE, CENTRAL_HERMITE = "raw", "central", "hermite", "central_hermite"
 
 
 @dataclass
@@ -491,6 +498,9 @@ def collide(lat: Lattice, m: Model, S: np.ndarray, fbar: np.ndarray) -> np.ndarr
                    matrix Mbar(u) = N(u) M and S by Sbar (Eq. 5-1-2), so the
                    collision matrix is Lambda = Mbar^-1 Sbar Mbar; Mbar is
                    inverted numerically at every node.
+    Hermite and central-Hermite bases: Mbar = N M with the Hermite rows of
+                   central_moment_matrices at u = 0 or at the local u (the
+                   other bases Sec. V names as special cases of Eq. 5-1-2).
     """
     dt = lat.dt
     rho, u = macroscopic(lat, m, fbar)
@@ -501,7 +511,9 @@ def collide(lat: Lattice, m: Model, S: np.ndarray, fbar: np.ndarray) -> np.ndarr
         mb, meq, mG, mF = M @ fbar, M @ feq, M @ G, M @ F
         mstar = mb - S @ (mb - meq) + dt * (mG + (I - 0.5 * S) @ mF)
         return np.linalg.solve(M, mstar)
-    Mb = central_moment_matrices(lat, u)
+    shifted = m.basis in (CENTRAL, CENTRAL_HERMITE)
+    Mb = central_moment_matrices(lat, u if shifted else np.zeros_like(u),
+                                 hermite=m.basis in (HERMITE, CENTRAL_HERMITE))
     k = np.einsum("nkj,jn->kn", Mb, fbar)
     keq = np.einsum("nkj,jn->kn", Mb, feq)
     kG = np.einsum("nkj,jn->kn", Mb, G)
@@ -585,6 +597,47 @@ def init_equilibrium(lat: Lattice, m: Model, S: np.ndarray, rho: np.ndarray, u: 
     uu = u.reshape(lat.d, -1).T.astype(np.float64)
     feq, _, _ = equilibrium_and_sources(lat, m, S, r, uu)
     return feq.reshape((lat.q,) + shp)
+
+
+def local_stress(lat: Lattice, m: Model, r: Rates, fbar: np.ndarray):
+    """Local viscous stress and strain rate of the NSE, Eqs. (4-32), (4-33).
+
+    With X = sum_k c_k c_k f_k^ne + (dt/2)(u Fbar + Fbar u + c_s^2 Sbar I),
+    the stress K_mu (grad u + grad u^T) = -(I - S_2/2) X and the strain rate
+    (grad u + grad u^T)/2 = -(K_mu^-1/2)(I - S_2/2) X, every product taken
+    entry by entry, S_2 the matrix of entries s_sa (diagonal) and s_ab,
+    K_mu of Eq. (4-29a) with the local density.  f^ne = f - f^eq with
+    f = fbar + dt F/2 (Eq. 2-3); the second moment of F = g^eq(Sbar, Fbar,
+    -c_s^2 Sbar I) vanishes (Eq. 3-5), so sum c c f^ne = sum c c (fbar - f^eq).
+    fbar (q, nz, ny, nx); returns (stress, strain), each (d, d, nz, ny, nx).
+    """
+    d, cs2, dt, c = lat.d, lat.cs2, lat.dt, lat.c
+    shp = fbar.shape[1:]
+    fl = fbar.reshape(lat.q, -1)
+    n = fl.shape[1]
+    if m.kind not in (NSE, NSE_HELUO):
+        raise ValueError("the local stress is defined for the NSE")
+    rho, u = macroscopic(lat, m, fl)
+    fc = m.rho0 * np.ones(n) if m.kind == NSE_HELUO else rho
+    feq = geq(lat, rho, fc[:, None] * u, fc[:, None, None] * np.einsum("na,nb->nab", u, u))
+    m2 = np.einsum("ja,jb,jn->abn", lat.cv, lat.cv, fl - feq)
+    F = force_of(m, d, n)
+    Sb = source_of(m, n)
+    X = m2 + 0.5 * dt * (np.einsum("na,nb->abn", u, F) + np.einsum("na,nb->abn", F, u))
+    X += 0.5 * dt * cs2 * Sb[None, None, :] * np.eye(d)[:, :, None]
+    stress = np.zeros((d, d, n))
+    strain = np.zeros((d, d, n))
+    for a in range(d):
+        for b in range(d):
+            if a == b:
+                s = r.s_shear[a]
+                K = 0.5 * (1.0 / s - 0.5) * rho * (c[a] * c[a] - cs2) * dt
+            else:
+                s = r.s_off[a, b]
+                K = (1.0 / s - 0.5) * rho * cs2 * dt
+            stress[a, b] = -(1.0 - 0.5 * s) * X[a, b]
+            strain[a, b] = stress[a, b] / (2.0 * K)
+    return stress.reshape((d, d) + shp), strain.reshape((d, d) + shp)
 
 
 def velocity_gradient(lat: Lattice, u: np.ndarray) -> np.ndarray:

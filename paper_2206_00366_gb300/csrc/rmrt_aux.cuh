@@ -178,4 +178,67 @@ __global__ void __launch_bounds__(CHECK_THREADS) check_kernel(
   if (flag && flags) atomicOr(flags, flag);
 }
 
+// Local viscous stress and strain rate of the NSE (Eqs. 4-32, 4-33), in
+// FP64 from the decoded populations of each node:
+//   X = sum_k c_k c_k (fbar_k - f^eq_k) + (dt/2)(u Fbar + Fbar u + c_s^2 Sbar I)
+//   stress_ab = -(1 - s_ab/2) X_ab,  strain_ab = stress_ab / (2 K_mu,ab)
+// with s_aa = s_sa, K_mu of Eq. (4-29a) at the local density.  The second
+// moment of F vanishes, so fbar's moments serve for f's.  Output planes
+// xx, yy, (zz), xy, (xz, yz).  grid (ceil(nx / bx), ny, nz).
+template <int LAT, typename ST, typename CT>
+__global__ void stress_kernel(const ST* __restrict__ fin, double* __restrict__ stress, double* __restrict__ strain,
+                              const KParams<CT> p) {
+  using L = Lat<LAT>;
+  constexpr int D = L::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= p.nx) return;
+  const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
+  const size_t N = p.N;
+  double s0 = 0.0, s1[3] = {0.0, 0.0, 0.0}, s2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    const int sx = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
+    const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
+    const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
+    const double dj = double(load_st<ST, CT>(fin + j * N + (size_t(sz) * p.ny + sy) * p.nx + sx)) * double(p.sinv[j]);
+    const int e[3] = {ex, ey, ez};
+    s0 += dj;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s1[a] += e[a] * dj;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) s2[a][b] += e[a] * e[b] * dj;
+    }
+  });
+  const double dt = double(p.dt), cs2 = double(p.cs2), rho0 = p.rho0d, src = double(p.source);
+  const double rho = rho0 + s0 + 0.5 * dt * src;
+  const double fc = p.kind == KIND_NSE_HELUO ? rho0 : rho;
+  double u[3], F[3], c[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    c[a] = double(p.c[a]);
+    F[a] = double(p.force[a]);
+    u[a] = a < D ? (s1[a] * c[a] + 0.5 * dt * F[a]) / fc : 0.0;
+  }
+  const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+  int k = 0;
+  for (int q = 0; q < 6; ++q) {
+    const int a = pa[q], b = pb[q];
+    if (a >= D || b >= D) continue;
+    // sum c c fbar (the rest state omega rho0 contributes rho0 c_s^2 delta)
+    const double m2 = c[a] * c[b] * s2[a][b] + (a == b ? rho0 * cs2 : 0.0);
+    const double meq = (a == b ? rho * cs2 : 0.0) + fc * u[a] * u[b];
+    const double X = m2 - meq + 0.5 * dt * (u[a] * F[b] + F[a] * u[b] + (a == b ? cs2 * src : 0.0));
+    const double s = a == b ? p.ssd[a] : p.soffd[a + b - 1];   // xy -> 0, xz -> 1, yz -> 2
+    const double K = a == b ? 0.5 * (1.0 / s - 0.5) * rho * (c[a] * c[a] - cs2) * dt : (1.0 / s - 0.5) * rho * cs2 * dt;
+    const double tau = -(1.0 - 0.5 * s) * X;
+    const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
+    if (stress) stress[size_t(k) * N + own] = tau;
+    if (strain) strain[size_t(k) * N + own] = tau / (2.0 * K);
+    ++k;
+  }
+}
+
 }  // namespace rmrt

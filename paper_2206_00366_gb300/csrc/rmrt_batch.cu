@@ -699,7 +699,7 @@ struct InitF {
 template <typename F>
 cudaError_t dispatch(rmrtlb_batch* b, const F& f) {
   const bool f64 = b->storage == RMRTLB_ST_F64;
-  switch (b->lat * 2 + b->central) {
+  switch (b->lat * 2 + (b->central != 0 ? 1 : 0)) {
     case 0: return f64 ? f.template run<LAT_D2Q9, false, double, double>() : f.template run<LAT_D2Q9, false, float, float>();
     case 1: return f64 ? f.template run<LAT_D2Q9, true, double, double>() : f.template run<LAT_D2Q9, true, float, float>();
     case 2: return f64 ? f.template run<LAT_D3Q19, false, double, double>() : f.template run<LAT_D3Q19, false, float, float>();
@@ -828,7 +828,7 @@ int rmrtlb_batch_create(rmrtlb_batch_t* out, int lattice, int basis, int ndomain
   size_t need = 0;
   int rc = rmrtlb_batch_workspace_bytes(lattice, ndomains, domains, storage, &need);
   if (rc) return rc;
-  if (basis < 0 || basis > 1) return RMRTLB_EINVAL;
+  if (basis < 0 || basis > 3) return RMRTLB_EINVAL;
   if (!workspace || reinterpret_cast<size_t>(workspace) % kAlignB) return RMRTLB_EINVAL;
   if (workspace_bytes < need) return RMRTLB_ENOMEM;
   if (check_every < 2 || !(tol > 0) || !isfinite(rho0)) return RMRTLB_EINVAL;

@@ -242,7 +242,7 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
                   size_t workspace_bytes, void* stream) {
   if (!solver || !params || !valid_dims(lattice, nx, ny, nz)) return RMRTLB_EINVAL;
   *solver = nullptr;
-  if (eq_kind < 0 || eq_kind > 3 || basis < 0 || basis > 1 || storage < 0 || storage > 3) return RMRTLB_EINVAL;
+  if (eq_kind < 0 || eq_kind > 3 || basis < 0 || basis > 3 || storage < 0 || storage > 3) return RMRTLB_EINVAL;
   if (!(dt > 0) || !(dx > 0) || !(dy > 0) || (lattice != RMRTLB_D2Q9 && !(dz > 0))) return RMRTLB_EINVAL;
   if (!workspace || (reinterpret_cast<size_t>(workspace) % kAlign) != 0) return RMRTLB_EINVAL;
   const Layout L = make_layout(lattice, nx, ny, nz, storage);
@@ -404,6 +404,18 @@ int rmrtlb_moments(rmrtlb_t s, double* rho, double* u) {
     return RMRTLB_ECUDA;
   if ((!rdev || !udev) && cudaStreamSynchronize(s->stream) != cudaSuccess) return RMRTLB_ECUDA;
   return RMRTLB_OK;
+}
+
+int rmrtlb_stress(rmrtlb_t s, double* stress, double* strain) {
+  if (!s) return RMRTLB_EINVAL;
+  if (s->k.kind != RMRTLB_EQ_NSE && s->k.kind != RMRTLB_EQ_NSE_HELUO) return RMRTLB_EINVAL;
+  if ((stress && !is_device_ptr(stress)) || (strain && !is_device_ptr(strain))) return RMRTLB_EINVAL;
+  if (!stress && !strain) return RMRTLB_OK;
+  LaunchArgs a = base_args(s, OP_STRESS);
+  a.fin = pop_ptr(s, s->cur);
+  a.stress = stress;
+  a.strain = strain;
+  return launch(s, a) == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA;
 }
 
 int rmrtlb_stats(rmrtlb_t s, double out[8]) {

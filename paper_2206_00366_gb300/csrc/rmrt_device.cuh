@@ -243,6 +243,30 @@ __device__ __forceinline__ constexpr bool absent(int a, int b, int c) {
 template <typename P>
 using PScalar = typename std::remove_cv<typename std::remove_reference<decltype(P::rho0)>::type>::type;
 
+// Hermite moments from raw moments along every axis (BACK: the inverse):
+// with P_2(e) = e^2 - mu (mu = c_s^2 / c_a^2 in index units), the 1-D map
+// (m0, m1, m2) -> (m0, m1, m2 - mu m0) is unit lower-triangular.
+template <bool BACK, int LAT, typename V, typename P>
+__device__ __forceinline__ void hermite_axes(Cube<LAT, V>& q, const P& p) {
+  using S = PScalar<P>;
+  constexpr int NZ = Lat<LAT>::NZ;
+  const S sg = BACK ? S(1) : S(-1);
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < NZ; ++c) q.v[2][b][c] = fmav(q.v[0][b][c], V(sg * p.mu2[0]), q.v[2][b][c]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < NZ; ++c) q.v[a][2][c] = fmav(q.v[a][0][c], V(sg * p.mu2[1]), q.v[a][2][c]);
+  if constexpr (NZ == 3) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) q.v[a][b][2] = fmav(q.v[a][b][0], V(sg * p.mu2[2]), q.v[a][b][2]);
+  }
+}
+
 template <int LAT, typename V, typename P>
 __device__ __forceinline__ V meq_moment(int a, int b, int c, V A, const V B[3], const V M[6], const P& p) {
   using S = PScalar<P>;
@@ -459,10 +483,14 @@ __device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p) {
       for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int c = 0; c < NZ; ++c) k.v[a][b][c] = X[a][b][c];
-    k.template shift<false>(mc.u);
+    // Mbar = N M (Eq. 5-1-1): N = shift to central moments (bit 0 of
+    // p.basis), then Hermite polynomials (bit 1); uniform branches
+    if (p.basis & 1) k.template shift<false>(mc.u);
+    if (p.basis & 2) hermite_axes<false>(k, p);
     Cube<LAT, V> sk;
     relax<LAT, NSE, false>(sk.v, k.v, p);
-    sk.template shift<true>(mc.u);
+    if (p.basis & 2) hermite_axes<true>(sk, p);
+    if (p.basis & 1) sk.template shift<true>(mc.u);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll

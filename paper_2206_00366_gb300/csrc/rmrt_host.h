@@ -137,6 +137,7 @@ inline KParams<CT> to_kparams(const Consts& k) {
   memset(&p, 0, sizeof(p));
   p.nx = k.nx; p.ny = k.ny; p.nz = k.nz;
   p.kind = k.kind; p.forced = k.forced; p.N = k.N;
+  p.basis = k.central;
   p.rho0 = CT(k.rho0); p.cs2 = CT(k.cs2); p.dt = CT(k.dt); p.source = CT(k.source);
   p.rho0d = k.rho0;
   double c[3], c2[3];
@@ -175,6 +176,10 @@ inline KParams<CT> to_kparams(const Consts& k) {
     }
   }
   p.s0 = CT(k.s0); p.sfree = CT(k.sfree);
+  for (int a = 0; a < 3; ++a) {
+    p.ssd[a] = k.ss[a];
+    p.soffd[a] = k.soff[a];
+  }
   return p;
 }
 

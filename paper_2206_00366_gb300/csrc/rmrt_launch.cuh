@@ -50,6 +50,10 @@ static cudaError_t launch_typed(const LaunchArgs& a, const KParams<CT>& p) {
           static_cast<const ST*>(a.fin), a.rho_out, a.u_out, a.uprev, a.use_prev, a.write_prev, a.partials,
           a.flags, p);
       break;
+    case OP_STRESS:
+      stress_kernel<LAT, ST, CT><<<a.grid, a.block, 0, a.stream>>>(static_cast<const ST*>(a.fin), a.stress, a.strain,
+                                                                   p);
+      break;
     default:
       return cudaErrorInvalidValue;
   }

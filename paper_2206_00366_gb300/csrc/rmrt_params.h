@@ -19,7 +19,7 @@ struct KParams {
   int nx, ny, nz;
   int kind;        // KIND_*
   int forced;      // nonzero when force or source is nonzero
-  int pad_;
+  int basis;       // RMRTLB_BASIS_*: bit 0 central shift N(u), bit 1 Hermite polynomials
   size_t N;        // nodes = nx * ny * nz
   CT rho0, cs2, dt, source;
   CT c[3];                             // c_a
@@ -31,9 +31,10 @@ struct KParams {
   CT q19h[3];                          // rD3Q19 fourth-moment term in index units
   double wd[27];                       // omega_j in FP64 (population set/get)
   double rho0d;
+  double ssd[3], soffd[3];             // s_sa and s_ab (xy, xz, yz) in FP64 (local stress output)
 };
 
-enum Op { OP_STEP = 0, OP_INIT_EQ = 1, OP_PLANE = 2, OP_CHECK = 3 };
+enum Op { OP_STEP = 0, OP_INIT_EQ = 1, OP_PLANE = 2, OP_CHECK = 3, OP_STRESS = 4 };
 
 struct LaunchArgs {
   Op op;
@@ -48,6 +49,8 @@ struct LaunchArgs {
   int j, to_storage;
   double* rho_out;         // OP_CHECK
   double* u_out;
+  double* stress;          // OP_STRESS (d(d+1)/2 planes each, either may be NULL)
+  double* strain;
   double* uprev;
   int use_prev, write_prev;
   double* partials;

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "librmrtlb.so")
 
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
 EQ_NSE, EQ_NSE_HELUO, EQ_NCDE_LINEAR, EQ_NCDE_QUAD = 0, 1, 2, 3
-BASIS_RAW, BASIS_CENTRAL = 0, 1
+BASIS_RAW, BASIS_CENTRAL, BASIS_HERMITE, BASIS_CENTRAL_HERMITE = 0, 1, 2, 3
 ST_F64, ST_F32, ST_F16, ST_BF16 = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETOOBIG = 0, -1, -2, -3, -4, -5
 NOALLOC_MAX_NODES = 67108864
@@ -31,7 +31,8 @@ LATTICE_NAMES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}
 STORAGE_NAMES = {"f64": ST_F64, "f32": ST_F32, "f16": ST_F16, "bf16": ST_BF16}
 EQ_NAMES = {"nse": EQ_NSE, "nse_heluo": EQ_NSE_HELUO, "ncde_linear": EQ_NCDE_LINEAR,
             "ncde_quad": EQ_NCDE_QUAD}
-BASIS_NAMES = {"raw": BASIS_RAW, "central": BASIS_CENTRAL}
+BASIS_NAMES = {"raw": BASIS_RAW, "central": BASIS_CENTRAL, "hermite": BASIS_HERMITE,
+               "central_hermite": BASIS_CENTRAL_HERMITE}
 
 
 class RmrtlbError(RuntimeError):
@@ -111,6 +112,7 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_moments": (i, [_vp, _vp, _vp]),
         "rmrtlb_stats": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_last_check": (i, [_vp, ctypes.POINTER(d)]),
+        "rmrtlb_stress": (i, [_vp, _vp, _vp]),
         "rmrtlb_population_totals_noalloc": (i, [i, i, i, i, d, d, d, d, _vp, _vp, _vp]),
         "rmrtlb_batch_workspace_bytes": (i, [i, i, ctypes.POINTER(rmrtlb_domain), i, ctypes.POINTER(sz)]),
         "rmrtlb_batch_create": (i, [ctypes.POINTER(_vp), i, i, i, ctypes.POINTER(rmrtlb_domain), i, d, i, d, _vp,
@@ -149,7 +151,7 @@ def exported_symbols() -> list:
     return ["rmrtlb_strerror", "rmrtlb_lattice_info", "rmrtlb_workspace_bytes", "rmrtlb_create",
             "rmrtlb_destroy", "rmrtlb_get_constants", "rmrtlb_init_equilibrium",
             "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
-            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_population_totals_noalloc",
+            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_stress", "rmrtlb_population_totals_noalloc",
             "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
             "rmrtlb_batch_tune", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
             "rmrtlb_batch_get_populations", "rmrtlb_batch_fields", "rmrtlb_batch_run", "rmrtlb_batch_init_fields",
@@ -318,6 +320,10 @@ def rmrtlb_batch_fields(h, domain: int, rho: int, u: int):
     _check(lib().rmrtlb_batch_fields(h, domain, rho, u), "rmrtlb_batch_fields")
 
 
+def rmrtlb_stress(h, stress: int, strain: int):
+    _check(lib().rmrtlb_stress(h, stress, strain), "rmrtlb_stress")
+
+
 # ------------------------------------------------------------------ warm-start network (rmrtlb_cnn.h)
 def rmrtlb_conv3d_forward(n, d, h, w, cin, cout, x, weight, bias, apply_silu, z, a, stream=0):
     _check(lib().rmrtlb_conv3d_forward(n, d, h, w, cin, cout, x, weight, bias, int(apply_silu), z, a, stream),
@@ -439,6 +445,18 @@ class Solver:
 
     def last_check(self, allow_unstable=False):
         return rmrtlb_last_check(self.h, allow_unstable)
+
+    def stress(self):
+        """(stress, strain rate) as numpy arrays (d(d+1)/2, nz, ny, nx),
+        components xx, yy, (zz), xy, (xz, yz); Eqs. (4-32), (4-33)."""
+        import torch
+        k = self.d * (self.d + 1) // 2
+        shp = (k, self.shape[2], self.shape[1], self.shape[0])
+        st = torch.empty(shp, dtype=torch.float64, device=self.workspace.device)
+        sr = torch.empty(shp, dtype=torch.float64, device=self.workspace.device)
+        rmrtlb_stress(self.h, st.data_ptr(), sr.data_ptr())
+        self.stream.synchronize()
+        return st.cpu().numpy(), sr.cpu().numpy()
 
 
 class Batch:

@@ -236,6 +236,9 @@ def warm_fields(net, re, coarse, fine, dom, rho0=1.0):
     d, h, w = coarse
     B.rmrtlb_upsample_fields(d, h, w, 4, _ptr(y), D, H, W, [1.0 / rs, 1.0 / us, 1.0 / us, 1.0 / us],
                              [rho0, 0.0, 0.0, 0.0], _ptr(dst))
+    # the network runs on the legacy stream; the solver reads the fields on
+    # its own (non-blocking) stream
+    torch.cuda.synchronize()
     return dst[0], dst[1:4]
 
 

@@ -159,7 +159,7 @@ def oracle_domain3(lattice, basis, d, steps, f0, rho0=1.0):
 
 
 @pytest.mark.parametrize("lattice", ["D3Q19", "D3Q27"])
-@pytest.mark.parametrize("basis", ["raw", "central"])
+@pytest.mark.parametrize("basis", ["raw", "central", "hermite", "central_hermite"])
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
 def test_batch3d_matches_oracle(lattice, basis, storage, tol):
     """3-D cavities (walls on every face, lid on the top z face moving +x):

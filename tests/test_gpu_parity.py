@@ -79,7 +79,7 @@ KINDS = ["nse", "nse_heluo", "ncde_linear", "ncde_quad"]
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("forced", [False, True])
 @pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("basis", ["raw", "central"])
+@pytest.mark.parametrize("basis", ["raw", "central", "hermite", "central_hermite"])
 @pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19", "D3Q27"])
 @pytest.mark.parametrize("even", [False, True])
 def test_random_populations(even, lattice, basis, kind, forced, storage):
@@ -308,3 +308,45 @@ def test_stats_large_grid_stride(lattice, shape):
     np.testing.assert_allclose(st[1:1 + case.d], mom, rtol=0, atol=1e-12 * r.sum() * 0.02)
     ke = 0.5 * (r[None] * uu * uu).sum()
     assert abs(st[4] - ke) <= 1e-10 * ke
+
+
+# ---------------------------------------------------------------- local stress, Eqs. (4-32), (4-33)
+@pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19", "D3Q27"])
+@pytest.mark.parametrize("kind", ["nse", "nse_heluo"])
+@pytest.mark.parametrize("forced", [False, True])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-11), ("f32", 2e-4)])
+def test_local_stress_matches_oracle(lattice, kind, forced, storage, tol):
+    """rmrtlb_stress on random populations (a few steps evolved) against
+    the oracle's Eqs. (4-32)/(4-33), every component, normwise."""
+    import oracle.rmrt as R
+    import workloads as W
+    from paper_2206_00366_gb300.rmrtlb import Solver
+    d3 = lattice != "D2Q9"
+    shape = (9, 7, 5) if d3 else (13, 11, 1)
+    sp = (1.0, 0.8, 0.6) if d3 else (1.0, 0.6)
+    q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}[lattice]
+    force = (1e-5, -2e-5, 1.5e-5) if forced else (0.0, 0.0, 0.0)
+    src = 1e-6 if forced else 0.0
+    params = dict(nu=0.02, nu_bulk=0.03, s_free=1.1, rho0=1.0, force=force, source=src)
+    s = Solver(lattice, shape, sp, params=params, eq_kind=kind, storage=storage)
+    nz, ny, nx = shape[2], shape[1], shape[0]
+    f0 = W.random_populations(q, (nz, ny, nx), seed=5, amp=0.02)
+    s.set_populations(f0)
+    s.step(3)
+    f = s.get_populations()
+    st, sr = s.stress()
+    lat = R.make_lattice(lattice, sp)
+    r = R.rates_from_viscosity(lat, 0.02, 0.03, 1.1)
+    m = R.Model(R.NSE if kind == "nse" else R.NSE_HELUO, rho0=1.0, force=force[:lat.d], source=src)
+    ost, osr = R.local_stress(lat, m, r, f)
+    comps = [(0, 0), (1, 1), (0, 1)] if not d3 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    for k, (a, b) in enumerate(comps):
+        assert normwise(st[k], ost[a, b]) <= tol, (k, a, b)
+        assert normwise(sr[k], osr[a, b]) <= tol, (k, a, b)
+
+
+def test_local_stress_rejects_ncde():
+    from paper_2206_00366_gb300.rmrtlb import RmrtlbError, Solver
+    s = Solver("D2Q9", (8, 8), (1.0, 1.0), params=dict(diffusivity=0.01, s_free=1.1), eq_kind="ncde_linear")
+    with pytest.raises(RmrtlbError):
+        s.stress()

@@ -293,7 +293,7 @@ def test_reduces_to_lallemand_luo_mrt():
 
 # ---------------------------------------------------------------- invariants
 @pytest.mark.parametrize("name", R.LATTICES)
-@pytest.mark.parametrize("basis", [R.RAW, R.CENTRAL])
+@pytest.mark.parametrize("basis", [R.RAW, R.CENTRAL, R.HERMITE, R.CENTRAL_HERMITE])
 def test_collision_invariants(name, basis):
     """Eq. (4-18-1): mass and momentum are collision invariants; with
     forcing the increments are exactly dt Sbar and dt Fbar (Eq. 2-4-2)."""
@@ -382,6 +382,75 @@ def test_central_equals_raw_at_rest_and_unit_rates():
     feq, _, _ = R.equilibrium_and_sources(lat, R.Model(), one, rho, u)
     np.testing.assert_allclose(a, feq, atol=1e-15)
     np.testing.assert_allclose(b, feq, atol=1e-15)
+
+
+@pytest.mark.parametrize("name,dx", [("D2Q9", (1.0, 0.6)), ("D3Q27", (1.0, 0.7, 0.5))])
+def test_hermite_basis_orthogonal(name, dx):
+    """On the tensor-product lattices the Hermite polynomials P_0 = 1,
+    P_1 = xi, P_2 = xi^2 - c_s^2 of each axis are orthogonal under the 1-D
+    weights (1 - c_s^2/c^2, c_s^2/(2c^2), c_s^2/(2c^2)), so the Hermite
+    basis rows are orthogonal under omega_j: sum_j omega_j H_k H_l = 0,
+    k != l, with H_k H_k summing to the product over axes of 1, c_s^2 and
+    c_s^2 (c_a^2 - c_s^2) (2 c_s^4 on the standard lattice)."""
+    lat = R.make_lattice(name, dx)
+    H = R.central_moment_matrices(lat, np.zeros((1, lat.d)), hermite=True)[0]
+    G = H @ np.diag(lat.w) @ H.T
+    mons = R.monomials(lat.name)
+    want = np.array([np.prod([(1.0, lat.cs2, lat.cs2 * (lat.c[al] ** 2 - lat.cs2))[a[al]] for al in range(lat.d)])
+                     for a in mons])
+    np.testing.assert_allclose(G, np.diag(want), atol=1e-14)
+
+
+@pytest.mark.parametrize("name", R.LATTICES)
+@pytest.mark.parametrize("basis", [R.HERMITE, R.CENTRAL_HERMITE])
+def test_hermite_bases_structure_and_limits(name, basis):
+    """Eq. (5-1-1) for the Hermite bases: Mbar = N M with N unit
+    lower-triangular in moment order; with every non-conserved rate equal
+    the collision is BGK and independent of the basis; the Hermite basis at
+    u = 0 equals the central-Hermite basis."""
+    lat = rand_lattice(name, RNG)
+    u = np.array([[0.04, -0.03, 0.02][: lat.d]])
+    M = R.moment_matrix(lat)
+    Mb = R.central_moment_matrices(lat, u if basis == R.CENTRAL_HERMITE else 0 * u, hermite=True)[0]
+    N = Mb @ np.linalg.inv(M)
+    order = R.moment_order(lat.name)
+    for k in range(lat.q):
+        for l in range(lat.q):
+            if order[l] > order[k] or (order[l] == order[k] and l != k):
+                assert abs(N[k, l]) < 1e-12
+        assert abs(N[k, k] - 1) < 1e-12
+    f = W.random_populations(lat.q, (10,), seed=12)
+    s = 1.3
+    bgk = R.relaxation_matrix(lat, R.Rates(s, np.full(lat.d, s), np.full(lat.d, s), np.full(lat.d, s),
+                                           np.full((lat.d, lat.d), s), s))
+    a = R.collide(lat, R.Model(basis=R.RAW), bgk, f)
+    b = R.collide(lat, R.Model(basis=basis), bgk, f)
+    np.testing.assert_allclose(a, b, atol=1e-14)
+    rho = f.sum(0)
+    mom = (lat.cv.T @ f) / rho
+    f0 = f - R.geq(lat, np.zeros(10), (rho * mom).T, np.zeros((10, lat.d, lat.d)))
+    r = R.rates_from_viscosity(lat, 0.02, 0.04, 1.1)
+    S = R.relaxation_matrix(lat, r)
+    np.testing.assert_allclose(R.collide(lat, R.Model(basis=R.HERMITE), S, f0),
+                               R.collide(lat, R.Model(basis=R.CENTRAL_HERMITE), S, f0), atol=1e-15)
+
+
+def test_hermite_basis_differs_from_raw_only_through_high_orders():
+    """Hermite moments of order <= 2 of a non-equilibrium part with no mass
+    or momentum are its raw moments, so the viscosity is unchanged: with
+    s_free equal to the second-order rates where they coincide (standard
+    lattice, nu_bulk chosen so all second-order rates agree), Hermite and
+    raw collisions coincide; with a different s_free they differ."""
+    lat = R.make_lattice("D2Q9", (1.0, 1.0), cs2=1.0 / 3.0)
+    f = W.random_populations(9, (10,), seed=13)
+    s_nu = 1.0 / (0.02 / (lat.cs2) + 0.5)
+    nu_b = (1.0 / s_nu - 0.5) * (1.0 - lat.cs2) / 2.0    # makes s_b = s_s = s_nu on the standard lattice
+    for s_free, same in ((s_nu, True), (1.1, False)):
+        r = R.rates_from_viscosity(lat, 0.02, nu_b, s_free)
+        S = R.relaxation_matrix(lat, r)
+        a = R.collide(lat, R.Model(basis=R.RAW), S, f)
+        b = R.collide(lat, R.Model(basis=R.HERMITE), S, f)
+        assert (np.abs(a - b).max() < 1e-14) == same
 
 
 def test_streaming_direction():
@@ -770,3 +839,50 @@ def test_noneq_start_removes_initial_transient():
         f1 = R.step(lat, m, S, f0, 1, walls=(1,), lid=(1, (U, 0.0), 1.0))
         change.append(np.abs(f1 - f0)[:, :, 2:-2].max())
     assert change[1] < 0.1 * change[0]
+
+
+# ---------------------------------------------------------------- Eqs. (4-32), (4-33)
+@pytest.mark.parametrize("name,dx", [("D2Q9", (1.0, 0.5)), ("D3Q19", (1.0, 1.0, 0.5)), ("D3Q27", (1.0, 0.5, 0.8))])
+def test_local_stress_couette(name, dx):
+    """Steady Couette flow (lid U on y = H): the local strain rate of
+    Eq. (4-33) is U / (2H) at every node and the stress of Eq. (4-32) is
+    rho nu U / H, with no normal components."""
+    lat = R.make_lattice(name, dx)
+    d = lat.d
+    nu, U = 0.1, 0.02
+    r = R.rates_from_viscosity(lat, nu, 0.1, 1.1)
+    S = R.relaxation_matrix(lat, r)
+    shape = (1, 16, 2) if d == 2 else (2, 16, 2)
+    m = R.Model()
+    f = R.init_equilibrium(lat, m, S, np.ones(shape), np.zeros((d,) + shape))
+    f = R.step(lat, m, S, f, 6000, walls=(1,), lid=(1, (U,) + (0.0,) * (d - 1), 1.0))
+    rho, _ = R.fields(lat, m, f)
+    stress, strain = R.local_stress(lat, m, r, f)
+    H = shape[1] * lat.dx[1]
+    np.testing.assert_allclose(strain[0, 1], U / (2 * H), rtol=1e-5)
+    np.testing.assert_allclose(strain[1, 0], U / (2 * H), rtol=1e-5)
+    np.testing.assert_allclose(stress[0, 1], rho * nu * U / H, rtol=1e-5)
+    assert np.abs(strain[0, 0]).max() < 1e-2 * U / H
+
+
+def test_local_stress_taylor_green():
+    """Decaying Taylor-Green vortex on the rectangular rD2Q9 lattice: the
+    local strain rate equals the analytic velocity gradients of the decayed
+    vortex (normal and shear components) within 1%."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.5))
+    r = R.rates_from_viscosity(lat, 0.02, 0.05, 1.1)
+    S = R.relaxation_matrix(lat, r)
+    m = R.Model()
+    n, u0 = 32, 1e-3
+    rho0, uinit = W.taylor_green_2d(n, n, 1.0, 0.5, u0, 1.0, lat.cs2)
+    f = R.step(lat, m, S, R.init_noneq(lat, m, S, r, rho0, uinit), 100)
+    _, u = R.fields(lat, m, f)
+    _, strain = R.local_stress(lat, m, r, f)
+    kx, ky = 2 * np.pi / n, 2 * np.pi / (n * 0.5)
+    X, Y, _ = W.grid((1, n, n), (1.0, 0.5))
+    a = np.abs(u[0]).max()               # decayed amplitude
+    gxx = a * kx * np.sin(kx * X) * np.sin(ky * Y)
+    gxy = 0.5 * a * (kx * kx / ky - ky) * np.cos(kx * X) * np.cos(ky * Y)
+    assert np.abs(strain[0, 0] - gxx).max() < 0.01 * np.abs(gxx).max()
+    assert np.abs(strain[1, 1] + gxx).max() < 0.01 * np.abs(gxx).max()
+    assert np.abs(strain[0, 1] - gxy).max() < 0.01 * np.abs(gxy).max()
