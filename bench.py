@@ -43,6 +43,8 @@ VARIANTS = [
     ("rD3Q27-central-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "central", "nse"),
     ("rD3Q27-raw-f16", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "raw", "nse"),
     ("rD3Q27-central-f16", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "central", "nse"),
+    ("rD3Q27-hermite-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "hermite", "nse"),
+    ("rD3Q27-central-hermite-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "central_hermite", "nse"),
 ]
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 ESIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
@@ -361,7 +363,8 @@ def run_batched(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     res, conv, act, done = b.status()
-    out["throughput"] = {"domains": len(doms), "nodes": nodes, "tile_width": width, "steps": nsteps,
+    out["throughput"] = {"domains": len(doms), "nodes": nodes, "tile_width": width, "tile_rows": b.tile_rows,
+                         "steps": nsteps,
                          "mlups": round(nodes * nsteps / (ms * 1e-3) / 1e6, 1),
                          "achieved_gbs": round(72 * nodes * nsteps / (ms * 1e-3) / 1e9, 1),
                          "unstable_domains": int((act == -1).sum()),

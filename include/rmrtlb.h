@@ -264,8 +264,8 @@ int rmrtlb_batch_workspace_bytes(int lattice, int ndomains, const rmrtlb_domain*
  * longer stepped and keeps its state.  With a non-NULL stream, each chunk
  * of check_every steps plus its check is captured once as a CUDA graph and
  * replayed; the legacy NULL stream launches directly (capture needs a
- * created stream).  The tile list starts with 128-node row tiles (see
- * rmrtlb_batch_tune).  RMRTLB_EINVAL for invalid rates or weights of a
+ * created stream).  The tile list starts with 128-node single-row tiles
+ * (see rmrtlb_batch_tune).  RMRTLB_EINVAL for invalid rates or weights of a
  * domain (as rmrtlb_create), RMRTLB_ENOMEM for a short workspace. */
 int rmrtlb_batch_create(rmrtlb_batch_t* batch, int lattice, int basis, int ndomains,
                         const rmrtlb_domain* domains, int storage, double rho0,
@@ -276,10 +276,11 @@ int rmrtlb_batch_destroy(rmrtlb_batch_t batch);
 /* Every domain back at rest, active, step 0. */
 int rmrtlb_batch_reset(rmrtlb_batch_t batch);
 
-/* Time `steps` steps with each tile width (32, 64, 128, 256 nodes per
- * row tile and threads per block), keep the fastest, then reset.  Writes
- * the chosen width. */
-int rmrtlb_batch_tune(rmrtlb_batch_t batch, int steps, int* tile_width);
+/* Autotuner: time `steps` steps with each tile shape — width 32, 64, 128
+ * or 256 nodes (threads per block) times 1, 2 or 4 rows per block — keep
+ * the fastest, then reset.  Writes the chosen width and rows (either
+ * pointer may be NULL).  The batch starts with 128 x 1 tiles. */
+int rmrtlb_batch_tune(rmrtlb_batch_t batch, int steps, int* tile_width, int* tile_rows);
 
 /* Advance every active domain n steps (asynchronous). */
 int rmrtlb_batch_step(rmrtlb_batch_t batch, int n);

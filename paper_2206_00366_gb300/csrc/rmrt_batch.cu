@@ -24,15 +24,31 @@
 
 namespace rmrt {
 
-// Per-domain parameter block: the collision constants of the shared
-// derivation (weights of Sec. III, rates of Eq. 4-31, S_2 of Eq. 5-8-1) plus
-// what the walls, the lid and the non-equilibrium initialisation need.
+// Per-domain constants every step reads, copied to shared memory by each
+// block: the collision constants of the shared derivation (weights of
+// Sec. III, rates of Eq. 4-31, S_2 of Eq. 5-8-1; the KParams fields the
+// collision reads, by the same names), the geometry, the lid terms.
+template <typename CT>
+struct CParams {
+  int nx, ny, nz, kind, basis, pad_;
+  unsigned long long N;
+  CT rho0, cs2, dt, source;
+  CT c[3], mu2[3];
+  CT s0, s1[3], s2h[3][3], soff[3], sfree;
+  CT fh[3], advh[3], q19h[3];
+};
 template <typename CT>
 struct BParams {
-  KParams<CT> k;
+  CParams<CT> k;
   unsigned long long off;   // element offset of the domain's population block
   unsigned long long uoff;  // element offset of its residual snapshot (d planes)
   CT lid[27];               // 2 omega_j rho0 c_x e_jx U / c_s^2: lid term of a population arriving from the lid
+};
+// Constants only the population set/get and the initialisation read (from
+// global memory).
+struct BCold {
+  double wd[27];            // omega_j
+  double rho0d;
   double ned[3];            // (c_a^2 - c_s^2) dt / s_sa: diagonal of Eq. (4-35) per unit rho and du_a/dx_a
   double neo[3];            // c_s^2 dt / s_ab (xy, xz, yz): off-diagonal of Eq. (4-35)
 };
@@ -56,6 +72,11 @@ __device__ __forceinline__ void load_params(BParams<CT>& sp, const BParams<CT>* 
   for (int i = threadIdx.x; i < W; i += blockDim.x) dst[i] = __ldg(src + i);
   __syncthreads();
 }
+
+// A tile is (domain, first row, first x, width | rows << 16): `rows`
+// consecutive rows (numbered z * ny + y) of `width` nodes from x.
+__device__ __forceinline__ int tile_width(const int4& t) { return t.w & 0xffff; }
+__device__ __forceinline__ int tile_rows(const int4& t) { return t.w >> 16; }
 
 // Node coordinates of a tile thread: rows are numbered z * ny + y.
 struct NodeXYZ {
@@ -96,7 +117,7 @@ __device__ __forceinline__ CT gather(const ST* __restrict__ base, const NodeXYZ&
   return v;
 }
 
-template <int LAT, bool CENTRAL, typename ST, typename CT>
+template <int LAT, int BASIS, typename ST, typename CT>
 __global__ void __launch_bounds__(256) batch_step_kernel(const ST* __restrict__ fin, ST* __restrict__ fout,
                                                          const BParams<CT>* __restrict__ dom,
                                                          const int4* __restrict__ tiles,
@@ -106,31 +127,34 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const ST* __restrict__ 
   if (active[t.x] != 1) return;      // retired: its last state stays in buffer A
   __shared__ BParams<CT> sp;
   load_params(sp, dom, t.x);
-  if (int(threadIdx.x) >= t.w) return;
-  const NodeXYZ n = node_of(t.z + int(threadIdx.x), t.y, sp);
+  if (int(threadIdx.x) >= tile_width(t)) return;
   const ST* base = fin + sp.off;
-  Cube<LAT, CT> q;
-  if constexpr (LAT == LAT_D3Q19) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) q.v[a][b][c] = CT(0);
-  }
-  static_for<L::Q>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-    q.v[ex + 1][ey + 1][zi<LAT>(ez)] = gather<LAT, CT, ST, j>(base, n, sp);
-  });
-  collide<LAT, CENTRAL, false, true>(q, sp.k);
   const size_t N = sp.k.N;
-  ST* out = fout + sp.off + n.own;
-  static_for<L::Q>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-    out[size_t(j) * N] = ST(q.v[ex + 1][ey + 1][zi<LAT>(ez)]);
-  });
+  const int rows = tile_rows(t);
+  for (int r = 0; r < rows; ++r) {
+    const NodeXYZ n = node_of(t.z + int(threadIdx.x), t.y + r, sp);
+    Cube<LAT, CT> q;
+    if constexpr (LAT == LAT_D3Q19) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) q.v[a][b][c] = CT(0);
+    }
+    static_for<L::Q>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+      q.v[ex + 1][ey + 1][zi<LAT>(ez)] = gather<LAT, CT, ST, j>(base, n, sp);
+    });
+    collide<LAT, BASIS, false, true>(q, sp.k);
+    ST* out = fout + sp.off + n.own;
+    static_for<L::Q>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+      out[size_t(j) * N] = ST(q.v[ex + 1][ey + 1][zi<LAT>(ez)]);
+    });
+  }
 }
 
 // Density and velocity of a node from its gathered populations.
@@ -172,25 +196,27 @@ __global__ void __launch_bounds__(256) batch_check_kernel(const ST* __restrict__
   if (active[t.x] == 1) {
     __shared__ BParams<CT> sp;
     load_params(sp, dom, t.x);
-    if (int(threadIdx.x) < t.w) {
-      const NodeXYZ n = node_of(t.z + int(threadIdx.x), t.y, sp);
-      CT s0;
-      double u[3];
-      node_fields<LAT, ST, CT>(fin + sp.off, n, sp, s0, u);
+    if (int(threadIdx.x) < tile_width(t)) {
       const size_t N = sp.k.N;
       double* up = uprev + sp.uoff;
-      double du2 = 0.0, u2 = 0.0;
+      for (int r = 0; r < tile_rows(t); ++r) {
+        const NodeXYZ n = node_of(t.z + int(threadIdx.x), t.y + r, sp);
+        CT s0;
+        double u[3];
+        node_fields<LAT, ST, CT>(fin + sp.off, n, sp, s0, u);
+        double du2 = 0.0, u2 = 0.0;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const double dlt = u[a] - (use_prev ? up[a * N + n.own] : 0.0);
-        up[a * N + n.own] = u[a];
-        du2 += dlt * dlt;
-        u2 += u[a] * u[a];
+        for (int a = 0; a < D; ++a) {
+          const double dlt = u[a] - (use_prev ? up[a * N + n.own] : 0.0);
+          up[a * N + n.own] = u[a];
+          du2 += dlt * dlt;
+          u2 += u[a] * u[a];
+        }
+        acc[0] += du2;
+        acc[1] += u2;
+        acc[2] += double(s0);
+        acc[3] = fmax(acc[3], isfinite(u2) && isfinite(double(s0)) ? u2 : INFINITY);
       }
-      acc[0] = du2;
-      acc[1] = u2;
-      acc[2] = double(s0);
-      acc[3] = isfinite(acc[1]) && isfinite(acc[2]) ? acc[1] : INFINITY;
     }
   }
   // block reduction in a fixed order (blockDim is a multiple of 32, <= 256);
@@ -326,7 +352,7 @@ __device__ __forceinline__ void dir_of(int j, int& ex, int& ey, int& ez, int& jo
 // bounces back into jo).  from_storage: plane = fbar_j = gather.
 template <int LAT, typename ST, typename CT>
 __global__ void batch_plane_kernel(ST* __restrict__ f, double* __restrict__ plane, int j, int to_storage,
-                                   const BParams<CT>* __restrict__ dom, int d) {
+                                   const BParams<CT>* __restrict__ dom, const BCold* __restrict__ cold, int d) {
   __shared__ BParams<CT> sp;
   load_params(sp, dom, d);
   const int nx = sp.k.nx, ny = sp.k.ny, nz = sp.k.nz;
@@ -334,7 +360,7 @@ __global__ void batch_plane_kernel(ST* __restrict__ f, double* __restrict__ plan
   ST* base = f + sp.off;   // storage holds fbar - omega rho0 (omega_j = omega_opp(j))
   int ex = 0, ey = 0, ez = 0, jo = 0;
   dir_of<LAT>(j, ex, ey, ez, jo);
-  const double rest = sp.k.wd[j] * sp.k.rho0d;
+  const double rest = cold[d].wd[j] * cold[d].rho0d;
   for (size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x; n < N; n += size_t(gridDim.x) * blockDim.x) {
     const int x = int(n % nx), y = int((n / nx) % ny), z = int(n / (size_t(nx) * ny));
     if (to_storage) {
@@ -379,12 +405,14 @@ __device__ __forceinline__ double grad_at(const double* __restrict__ ub, size_t 
 // value goes to the slot the next pull gather reads it from.
 template <int LAT, typename ST, typename CT>
 __global__ void batch_init_kernel(ST* __restrict__ f, const double* __restrict__ rho, const double* __restrict__ u,
-                                  const BParams<CT>* __restrict__ dom, int d, int with_ne) {
+                                  const BParams<CT>* __restrict__ dom, const BCold* __restrict__ cold, int d,
+                                  int with_ne) {
   using L = Lat<LAT>;
   constexpr int D = L::D, NZ = L::NZ;
   __shared__ BParams<CT> sp;
   load_params(sp, dom, d);
-  const KParams<CT>& p = sp.k;
+  const CParams<CT>& p = sp.k;
+  const BCold& cd = cold[d];
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const size_t N = p.N;
   ST* base = f + sp.off;
@@ -395,9 +423,16 @@ __global__ void batch_init_kernel(ST* __restrict__ f, const double* __restrict__
 #pragma unroll
     for (int a = 0; a < D; ++a) uh[a] = CT(u[a * N + n] / double(p.c[a]));
     Macro<CT> mc;
-    mc.dA = CT(r - p.rho0d);
+    mc.dA = CT(r - cd.rho0d);
     mc.rho = CT(r);
-    eq_args(mc, CT(r), uh, p);
+    // g^eq(rho, rho u, rho u u) of the NSE in index units (Eq. NSEfeq)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      mc.u[a] = uh[a];
+      mc.B[a] = CT(r) * uh[a];
+    }
+    mc.M[0] = CT(r) * uh[0] * uh[0]; mc.M[1] = CT(r) * uh[1] * uh[1]; mc.M[2] = CT(r) * uh[2] * uh[2];
+    mc.M[3] = CT(r) * uh[0] * uh[1]; mc.M[4] = CT(r) * uh[0] * uh[2]; mc.M[5] = CT(r) * uh[1] * uh[2];
     if (with_ne) {
       const int idx[3] = {x, y, z}, len[3] = {nx, ny, nz};
       const size_t stride[3] = {1, size_t(nx), size_t(nx) * ny};
@@ -411,14 +446,14 @@ __global__ void batch_init_kernel(ST* __restrict__ f, const double* __restrict__
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         const double ca = double(p.c[a]);
-        mc.M[a] += CT(-r * sp.ned[a] * g[a][a] / (ca * ca));
+        mc.M[a] += CT(-r * cd.ned[a] * g[a][a] / (ca * ca));
       }
       const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int a = pa[k], b = pb[k];
         if (a < D && b < D)
-          mc.M[3 + k] += CT(-r * sp.neo[k] * (g[a][b] + g[b][a]) / (double(p.c[a]) * double(p.c[b])));
+          mc.M[3 + k] += CT(-r * cd.neo[k] * (g[a][b] + g[b][a]) / (double(p.c[a]) * double(p.c[b])));
       }
     }
     Cube<LAT, CT> q;
@@ -455,20 +490,24 @@ namespace {
 constexpr size_t kAlignB = 256;
 size_t align_b(size_t v) { return (v + kAlignB - 1) / kAlignB * kAlignB; }
 const int kWidths[4] = {32, 64, 128, 256};
+const int kRows[3] = {1, 2, 4};
 
 size_t nodes_of(const rmrtlb_domain& x) { return size_t(x.nx) * x.ny * x.nz; }
 size_t rows_of(const rmrtlb_domain& x) { return size_t(x.ny) * x.nz; }
 
 struct BatchLayout {
-  size_t fA, fB, uprev, dom, tiles, partials, tile_begin, active, status, conv, counters, cs2, stage, total;
+  size_t fA, fB, uprev, dom, cold, tiles, partials, tile_begin, active, status, conv, counters, cs2, stage, total;
   size_t pop_elems;          // elements of one population lattice (all domains)
   size_t max_tiles;
   size_t max_n;              // largest domain
 };
 
-size_t tiles_for(const std::vector<rmrtlb_domain>& d, int width) {
+size_t tiles_of(const rmrtlb_domain& x, int width, int rows) {
+  return size_t((x.nx + width - 1) / width) * ((rows_of(x) + rows - 1) / rows);
+}
+size_t tiles_for(const std::vector<rmrtlb_domain>& d, int width, int rows) {
   size_t t = 0;
-  for (const auto& x : d) t += size_t((x.nx + width - 1) / width) * rows_of(x);
+  for (const auto& x : d) t += tiles_of(x, width, rows);
   return t;
 }
 
@@ -485,14 +524,15 @@ BatchLayout batch_layout(int lat, const std::vector<rmrtlb_domain>& d, int stora
   }
   L.pop_elems = elems;
   L.max_n = maxn;
-  L.max_tiles = tiles_for(d, kWidths[0]);
+  L.max_tiles = tiles_for(d, kWidths[0], 1);
   const size_t nd = d.size();
   const size_t psize = storage == RMRTLB_ST_F64 ? sizeof(BParams<double>) : sizeof(BParams<float>);
   L.fA = 0;
   L.fB = L.fA + align_b(elems * es);
   L.uprev = L.fB + align_b(elems * es);
   L.dom = L.uprev + align_b(unodes * sizeof(double));
-  L.tiles = L.dom + align_b(nd * psize);
+  L.cold = L.dom + align_b(nd * psize);
+  L.tiles = L.cold + align_b(nd * sizeof(BCold));
   L.partials = L.tiles + align_b(L.max_tiles * sizeof(int4));
   L.tile_begin = L.partials + align_b(L.max_tiles * 4 * sizeof(double));
   L.active = L.tile_begin + align_b((nd + 1) * sizeof(int));
@@ -515,9 +555,10 @@ bool domain_ok(int lat, const rmrtlb_domain& x) {
 // Parameters of one cavity from the same derivation as rmrtlb_create, plus
 // the lid terms and the Eq. (4-35) coefficients.
 template <typename CT>
-int domain_params(int lat, int basis, int storage, const rmrtlb_domain& D, double rho0, BParams<CT>& p,
+int domain_params(int lat, int basis, int storage, const rmrtlb_domain& D, double rho0, BParams<CT>& p, BCold& cold,
                   double* cs2_out) {
   memset(&p, 0, sizeof(p));
+  memset(&cold, 0, sizeof(cold));
   if (!domain_ok(lat, D) || !(D.nu > 0) || !(D.nu_bulk > 0)) return RMRTLB_EINVAL;
   rmrtlb_params rp;
   memset(&rp, 0, sizeof(rp));
@@ -530,15 +571,27 @@ int domain_params(int lat, int basis, int storage, const rmrtlb_domain& D, doubl
   const int rc = make_consts(k, lat, D.nx, D.ny, D.nz, D.dx, D.dy, lat == RMRTLB_D2Q9 ? 1.0 : D.dz, 1.0, rp,
                              RMRTLB_EQ_NSE, basis, storage);
   if (rc) return rc;
-  p.k = to_kparams<CT>(k);
+  const KParams<CT> kp = to_kparams<CT>(k);
+  CParams<CT>& c = p.k;
+  c.nx = kp.nx; c.ny = kp.ny; c.nz = kp.nz; c.kind = kp.kind; c.basis = kp.basis;
+  c.N = kp.N;
+  c.rho0 = kp.rho0; c.cs2 = kp.cs2; c.dt = kp.dt; c.source = kp.source;
+  for (int a = 0; a < 3; ++a) {
+    c.c[a] = kp.c[a]; c.mu2[a] = kp.mu2[a]; c.s1[a] = kp.s1[a]; c.soff[a] = kp.soff[a];
+    c.fh[a] = kp.fh[a]; c.advh[a] = kp.advh[a]; c.q19h[a] = kp.q19h[a];
+    for (int b = 0; b < 3; ++b) c.s2h[a][b] = kp.s2h[a][b];
+  }
+  c.s0 = kp.s0; c.sfree = kp.sfree;
   for (int j = 0; j < k.q; ++j) {
     int e[3];
     lattice_dir(lat, j, e);
     p.lid[j] = CT(2.0 * k.w[j] * rho0 * k.c[0] * e[0] * D.lid_u / k.cs2);
+    cold.wd[j] = k.w[j];
   }
+  cold.rho0d = rho0;
   for (int a = 0; a < 3; ++a) {
-    p.ned[a] = a < k.d ? (k.c[a] * k.c[a] - k.cs2) * k.dt / k.ss[a] : 0.0;
-    p.neo[a] = k.cs2 * k.dt / k.soff[a];
+    cold.ned[a] = a < k.d ? (k.c[a] * k.c[a] - k.cs2) * k.dt / k.ss[a] : 0.0;
+    cold.neo[a] = k.cs2 * k.dt / k.soff[a];
   }
   *cs2_out = k.cs2;
   return RMRTLB_OK;
@@ -565,6 +618,7 @@ struct rmrtlb_batch {
   char* ws;
   cudaStream_t stream;
   int width;                        // tile width (threads per block)
+  int rows;                         // rows per tile
   size_t ntiles;
   int check_every;
   double tol;
@@ -582,20 +636,25 @@ template <typename T> T* at(rmrtlb_batch* b, size_t off) { return reinterpret_ca
 // Row tiles of every domain (act == NULL) or of the domains still stepping
 // (act[d] == 1); tile_begin[d] .. tile_begin[d + 1] are domain d's tiles
 // (an empty range for a domain left out).
-cudaError_t build_tiles(rmrtlb_batch* b, int width, const std::vector<int>* act = nullptr) {
+cudaError_t build_tiles(rmrtlb_batch* b, int width, int rows, const std::vector<int>* act = nullptr) {
   std::vector<int4> t;
   std::vector<int> tb(b->dom.size() + 1, 0);
   for (size_t d = 0; d < b->dom.size(); ++d) {
     tb[d] = int(t.size());
     if (act && (*act)[d] != 1) continue;
     const auto& D = b->dom[d];
-    const int rows = int(rows_of(D));
-    for (int r = 0; r < rows; ++r)
-      for (int x0 = 0; x0 < D.nx; x0 += width) t.push_back(make_int4(int(d), r, x0, D.nx - x0 < width ? D.nx - x0 : width));
+    const int nr = int(rows_of(D));
+    for (int r = 0; r < nr; r += rows)
+      for (int x0 = 0; x0 < D.nx; x0 += width) {
+        const int w = D.nx - x0 < width ? D.nx - x0 : width;
+        const int h = nr - r < rows ? nr - r : rows;
+        t.push_back(make_int4(int(d), r, x0, w | (h << 16)));
+      }
   }
   tb[b->dom.size()] = int(t.size());
   b->ntiles = t.size();
   b->width = width;
+  b->rows = rows;
   b->tile_begin_host = tb;
   if (t.empty()) return cudaSuccess;
   cudaError_t e = cudaMemcpyAsync(at<int4>(b, b->L.tiles), t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice,
@@ -616,19 +675,19 @@ void drop_graph(rmrtlb_batch* b) {
 // instance for the batch's lattice, basis and storage.
 struct StepF {
   rmrtlb_batch* b;
-  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  template <int LAT, int BASIS, typename ST, typename CT>
   cudaError_t run() const {
     if (b->ntiles == 0) return cudaSuccess;
     const ST* fin = at<ST>(b, b->cur == 0 ? b->L.fA : b->L.fB);
     ST* fout = at<ST>(b, b->cur == 0 ? b->L.fB : b->L.fA);
-    batch_step_kernel<LAT, CENTRAL, ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
+    batch_step_kernel<LAT, BASIS, ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
         fin, fout, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active));
     return cudaGetLastError();
   }
 };
 struct CheckF {
   rmrtlb_batch* b;
-  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  template <int LAT, int BASIS, typename ST, typename CT>
   cudaError_t run() const {
     if (b->ntiles == 0) return cudaSuccess;
     const ST* fin = at<ST>(b, b->cur == 0 ? b->L.fA : b->L.fB);
@@ -642,7 +701,7 @@ struct FieldsF {
   rmrtlb_batch* b;
   int which, domain;
   double* fields;
-  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  template <int LAT, int BASIS, typename ST, typename CT>
   cudaError_t run() const {
     const size_t N = nodes_of(b->dom[domain]);
     const unsigned grid = unsigned(N / 256 + 1 < 4096 ? N / 256 + 1 : 4096);
@@ -653,7 +712,7 @@ struct FieldsF {
 };
 struct RestF {
   rmrtlb_batch* b;
-  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  template <int LAT, int BASIS, typename ST, typename CT>
   cudaError_t run() const {
     int maxlayer = 1;
     for (const auto& d : b->dom) {
@@ -671,12 +730,13 @@ struct PlaneF {
   int which;
   double* pl;
   int j, to_storage, domain;
-  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  template <int LAT, int BASIS, typename ST, typename CT>
   cudaError_t run() const {
     const size_t N = nodes_of(b->dom[domain]);
     const unsigned grid = unsigned(N / 256 + 1 < 4096 ? N / 256 + 1 : 4096);
     batch_plane_kernel<LAT, ST, CT><<<grid, 256, 0, b->stream>>>(at<ST>(b, which == 0 ? b->L.fA : b->L.fB), pl, j,
-                                                                to_storage, at<BParams<CT>>(b, b->L.dom), domain);
+                                                                to_storage, at<BParams<CT>>(b, b->L.dom),
+                                                                at<BCold>(b, b->L.cold), domain);
     return cudaGetLastError();
   }
 };
@@ -686,26 +746,37 @@ struct InitF {
   const double* rho;
   const double* u;
   int domain, with_ne;
-  template <int LAT, bool CENTRAL, typename ST, typename CT>
+  template <int LAT, int BASIS, typename ST, typename CT>
   cudaError_t run() const {
     const size_t N = nodes_of(b->dom[domain]);
     const unsigned grid = unsigned(N / 128 + 1 < 8192 ? N / 128 + 1 : 8192);
     batch_init_kernel<LAT, ST, CT><<<grid, 128, 0, b->stream>>>(at<ST>(b, which == 0 ? b->L.fA : b->L.fB), rho, u,
-                                                               at<BParams<CT>>(b, b->L.dom), domain, with_ne);
+                                                               at<BParams<CT>>(b, b->L.dom), at<BCold>(b, b->L.cold),
+                                                               domain, with_ne);
     return cudaGetLastError();
   }
 };
 
+template <int LAT, int BASIS, typename F>
+cudaError_t dispatch_st(rmrtlb_batch* b, const F& f) {
+  return b->storage == RMRTLB_ST_F64 ? f.template run<LAT, BASIS, double, double>()
+                                     : f.template run<LAT, BASIS, float, float>();
+}
+template <int LAT, typename F>
+cudaError_t dispatch_basis(rmrtlb_batch* b, const F& f) {
+  switch (b->central) {
+    case 1: return dispatch_st<LAT, 1>(b, f);
+    case 2: return dispatch_st<LAT, 2>(b, f);
+    case 3: return dispatch_st<LAT, 3>(b, f);
+    default: return dispatch_st<LAT, 0>(b, f);
+  }
+}
 template <typename F>
 cudaError_t dispatch(rmrtlb_batch* b, const F& f) {
-  const bool f64 = b->storage == RMRTLB_ST_F64;
-  switch (b->lat * 2 + (b->central != 0 ? 1 : 0)) {
-    case 0: return f64 ? f.template run<LAT_D2Q9, false, double, double>() : f.template run<LAT_D2Q9, false, float, float>();
-    case 1: return f64 ? f.template run<LAT_D2Q9, true, double, double>() : f.template run<LAT_D2Q9, true, float, float>();
-    case 2: return f64 ? f.template run<LAT_D3Q19, false, double, double>() : f.template run<LAT_D3Q19, false, float, float>();
-    case 3: return f64 ? f.template run<LAT_D3Q19, true, double, double>() : f.template run<LAT_D3Q19, true, float, float>();
-    case 4: return f64 ? f.template run<LAT_D3Q27, false, double, double>() : f.template run<LAT_D3Q27, false, float, float>();
-    default: return f64 ? f.template run<LAT_D3Q27, true, double, double>() : f.template run<LAT_D3Q27, true, float, float>();
+  switch (b->lat) {
+    case RMRTLB_D3Q19: return dispatch_basis<LAT_D3Q19>(b, f);
+    case RMRTLB_D3Q27: return dispatch_basis<LAT_D3Q27>(b, f);
+    default: return dispatch_basis<LAT_D2Q9>(b, f);
   }
 }
 
@@ -757,9 +828,9 @@ cudaError_t chunk(rmrtlb_batch* b) {
 
 cudaError_t reset_state(rmrtlb_batch* b) {
   const size_t es = b->storage == RMRTLB_ST_F64 ? 8 : 4;
-  if (b->ntiles != tiles_for(b->dom, b->width)) {   // a compacted list: every domain steps again
+  if (b->ntiles != tiles_for(b->dom, b->width, b->rows)) {   // a compacted list: every domain steps again
     drop_graph(b);
-    cudaError_t e = build_tiles(b, b->width);
+    cudaError_t e = build_tiles(b, b->width, b->rows);
     if (e != cudaSuccess) return e;
   }
   cudaError_t e = cudaMemsetAsync(b->ws + b->L.fA, 0, b->L.pop_elems * es, b->stream);
@@ -815,7 +886,7 @@ int rmrtlb_batch_workspace_bytes(int lattice, int ndomains, const rmrtlb_domain*
   std::vector<rmrtlb_domain> d(domains, domains + ndomains);
   for (const auto& x : d)
     if (!domain_ok(lattice, x)) return RMRTLB_EINVAL;
-  if (tiles_for(d, kWidths[0]) > size_t(1) << 31) return RMRTLB_EINVAL;
+  if (tiles_for(d, kWidths[0], 1) > size_t(1) << 31) return RMRTLB_EINVAL;
   *bytes = batch_layout(lattice, d, storage).total;
   return RMRTLB_OK;
 }
@@ -853,17 +924,18 @@ int rmrtlb_batch_create(rmrtlb_batch_t* out, int lattice, int basis, int ndomain
   size_t off = 0, uoff = 0;
   const size_t psize = storage == RMRTLB_ST_F64 ? sizeof(BParams<double>) : sizeof(BParams<float>);
   std::vector<char> params(ndomains * psize);
+  std::vector<BCold> cold(ndomains);
   std::vector<double> cs2(ndomains);
   for (int d = 0; d < ndomains; ++d) {
     const size_t n = nodes_of(b->dom[d]);
     if (storage == RMRTLB_ST_F64) {
       BParams<double> p;
-      rc = domain_params(lattice, basis, storage, b->dom[d], rho0, p, &cs2[d]);
+      rc = domain_params(lattice, basis, storage, b->dom[d], rho0, p, cold[d], &cs2[d]);
       p.off = off; p.uoff = uoff;
       memcpy(params.data() + d * psize, &p, psize);
     } else {
       BParams<float> p;
-      rc = domain_params(lattice, basis, storage, b->dom[d], rho0, p, &cs2[d]);
+      rc = domain_params(lattice, basis, storage, b->dom[d], rho0, p, cold[d], &cs2[d]);
       p.off = off; p.uoff = uoff;
       memcpy(params.data() + d * psize, &p, psize);
     }
@@ -874,8 +946,11 @@ int rmrtlb_batch_create(rmrtlb_batch_t* out, int lattice, int basis, int ndomain
   cudaError_t e = cudaMemcpyAsync(b->ws + b->L.dom, params.data(), params.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->ws + b->L.cs2, cs2.data(), cs2.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->ws + b->L.cold, cold.data(), cold.size() * sizeof(BCold), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  if (e == cudaSuccess) e = build_tiles(b, 128);
+  b->rows = 1;
+  if (e == cudaSuccess) e = build_tiles(b, 128, 1);
   if (e == cudaSuccess) e = reset_state(b);
   if (e != cudaSuccess) { delete b; return RMRTLB_ECUDA; }
   *out = b;
@@ -926,13 +1001,13 @@ int rmrtlb_batch_run(rmrtlb_batch_t b, long long max_steps, long long* steps_don
     if (read_active(b, act)) return RMRTLB_ECUDA;
     size_t live = 0;
     for (size_t d = 0; d < act.size(); ++d)
-      if (act[d] == 1) live += size_t((b->dom[d].nx + b->width - 1) / b->width) * rows_of(b->dom[d]);
+      if (act[d] == 1) live += tiles_of(b->dom[d], b->width, b->rows);
     if (live == 0) break;
     // tile queue: once a quarter of the launched tiles belong to retired
     // domains, launch only the tiles of the domains still stepping
     if (4 * live < 3 * b->ntiles) {
       drop_graph(b);
-      if (build_tiles(b, b->width, &act) != cudaSuccess) return RMRTLB_ECUDA;
+      if (build_tiles(b, b->width, b->rows, &act) != cudaSuccess) return RMRTLB_ECUDA;
     }
     const long long left = max_steps - (b->step - start);
     const long long n = left < per_poll ? left : per_poll;
@@ -970,28 +1045,30 @@ int rmrtlb_batch_status(rmrtlb_batch_t b, double* residual, long long* steps_to_
   return RMRTLB_OK;
 }
 
-int rmrtlb_batch_tune(rmrtlb_batch_t b, int steps, int* width_out) {
+int rmrtlb_batch_tune(rmrtlb_batch_t b, int steps, int* width_out, int* rows_out) {
   if (!b || steps < 1) return RMRTLB_EINVAL;
   float best = 1e30f;
-  int best_w = b->width;
+  int best_w = b->width, best_r = b->rows;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RMRTLB_ECUDA;
-  for (int w : kWidths) {
-    if (build_tiles(b, w) != cudaSuccess) return RMRTLB_ECUDA;
-    for (int i = 0; i < 2; ++i) { do_step(b); b->cur ^= 1; }
-    cudaEventRecord(e0, b->stream);
-    for (int i = 0; i < steps; ++i) { do_step(b); b->cur ^= 1; }
-    cudaEventRecord(e1, b->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) return RMRTLB_ECUDA;
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; best_w = w; }
-  }
+  for (int r : kRows)
+    for (int w : kWidths) {
+      if (build_tiles(b, w, r) != cudaSuccess) return RMRTLB_ECUDA;
+      for (int i = 0; i < 2; ++i) { do_step(b); b->cur ^= 1; }
+      cudaEventRecord(e0, b->stream);
+      for (int i = 0; i < steps; ++i) { do_step(b); b->cur ^= 1; }
+      cudaEventRecord(e1, b->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return RMRTLB_ECUDA;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; best_w = w; best_r = r; }
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   drop_graph(b);
-  if (build_tiles(b, best_w) != cudaSuccess || reset_state(b) != cudaSuccess) return RMRTLB_ECUDA;
+  if (build_tiles(b, best_w, best_r) != cudaSuccess || reset_state(b) != cudaSuccess) return RMRTLB_ECUDA;
   if (width_out) *width_out = best_w;
+  if (rows_out) *rows_out = best_r;
   return RMRTLB_OK;
 }
 

@@ -410,7 +410,7 @@ __device__ __forceinline__ Macro<V> macroscopic(V m000, const V jh[3], const P& 
 // Eq. (2-2-3):
 //   m* - m0 = m(delta) + dt (m_G + m_F) - S (m^ne + dt m_F / 2),
 // central variant: S replaced by N(u)^-1 Sbar N(u) (Eq. 5-1-2).
-template <int LAT, bool CENTRAL, bool FORCED, bool NSE, typename V, typename P>
+template <int LAT, int BASIS, bool FORCED, bool NSE, typename V, typename P>
 __device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p) {
   using S = PScalar<P>;
   constexpr int D = Lat<LAT>::D, NZ = Lat<LAT>::NZ;
@@ -475,7 +475,7 @@ __device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p) {
           q.v[a][b][c] = fmav(mG + mF, V(p.dt), q.v[a][b][c]);
         }
       }
-  if constexpr (CENTRAL) {
+  if constexpr (BASIS != 0) {
     Cube<LAT, V> k;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -484,13 +484,13 @@ __device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p) {
 #pragma unroll
         for (int c = 0; c < NZ; ++c) k.v[a][b][c] = X[a][b][c];
     // Mbar = N M (Eq. 5-1-1): N = shift to central moments (bit 0 of
-    // p.basis), then Hermite polynomials (bit 1); uniform branches
-    if (p.basis & 1) k.template shift<false>(mc.u);
-    if (p.basis & 2) hermite_axes<false>(k, p);
+    // BASIS), then Hermite polynomials (bit 1)
+    if constexpr ((BASIS & 1) != 0) k.template shift<false>(mc.u);
+    if constexpr ((BASIS & 2) != 0) hermite_axes<false>(k, p);
     Cube<LAT, V> sk;
     relax<LAT, NSE, false>(sk.v, k.v, p);
-    if (p.basis & 2) hermite_axes<true>(sk, p);
-    if (p.basis & 1) sk.template shift<true>(mc.u);
+    if constexpr ((BASIS & 2) != 0) hermite_axes<true>(sk, p);
+    if constexpr ((BASIS & 1) != 0) sk.template shift<true>(mc.u);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -521,7 +521,7 @@ __device__ __forceinline__ constexpr bool scaled_storage() { return sizeof(ST) =
 // ------------------------------------------------------------------ kernels
 // One time step: pull gather from fin (post-collision of the previous step,
 // x - e_j), collide, store the post-collision state of node x in fout.
-template <int LAT, typename ST, typename CT, bool CENTRAL, bool FORCED, bool NSE>
+template <int LAT, typename ST, typename CT, int BASIS, bool FORCED, bool NSE>
 __global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, ST* __restrict__ fout,
                                                    const KParams<CT> p) {
   using L = Lat<LAT>;
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, S
     if constexpr (scaled_storage<ST>()) v *= p.sinv[j];
     q.v[ex + 1][ey + 1][zi<LAT>(ez)] = v;
   });
-  collide<LAT, CENTRAL, FORCED, NSE>(q, p);
+  collide<LAT, BASIS, FORCED, NSE>(q, p);
   const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
@@ -607,8 +607,8 @@ __device__ __forceinline__ void store_pair<__nv_bfloat16, float>(__nv_bfloat16* 
 // loads to the last pair and store nothing.  With FP32 compute the pair is
 // collided as one F2 value (packed FP32 arithmetic); FP64 collides the two
 // nodes one after the other.
-template <int LAT, typename ST, typename CT, bool CENTRAL, bool FORCED, bool NSE>
-__global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), CENTRAL>::X2_MIN_BLOCKS)
+template <int LAT, typename ST, typename CT, int BASIS, bool FORCED, bool NSE>
+__global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>::X2_MIN_BLOCKS)
     step_kernel_x2(const ST* __restrict__ fin, ST* __restrict__ fout, const KParams<CT> p) {
   using L = Lat<LAT>;
   constexpr bool PACKED = std::is_same<CT, float>::value;
@@ -669,8 +669,8 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), CENTRAL>::X2
       qb.v[ex + 1][ey + 1][zi<LAT>(ez)] = vb;
     }
   });
-  collide<LAT, CENTRAL, FORCED, NSE>(qa, p);
-  if constexpr (!PACKED) collide<LAT, CENTRAL, FORCED, NSE>(qb, p);
+  collide<LAT, BASIS, FORCED, NSE>(qa, p);
+  if constexpr (!PACKED) collide<LAT, BASIS, FORCED, NSE>(qb, p);
   if (!active) return;
   const int own = (z * p.ny + y) * p.nx + x0;
   static_for<L::Q>([&](auto J) {

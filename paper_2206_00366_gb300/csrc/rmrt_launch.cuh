@@ -8,22 +8,26 @@
 
 namespace rmrt {
 
+template <int LAT, typename ST, typename CT, int BASIS, bool NSE>
+static void launch_basis(const LaunchArgs& a, const KParams<CT>& p, const ST* fin, ST* fout) {
+  if (a.pairs) {
+    if (p.forced) step_kernel_x2<LAT, ST, CT, BASIS, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+    else step_kernel_x2<LAT, ST, CT, BASIS, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+  } else {
+    if (p.forced) step_kernel<LAT, ST, CT, BASIS, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+    else step_kernel<LAT, ST, CT, BASIS, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+  }
+}
+
+// a.central carries the basis (RMRTLB_BASIS_*): raw, central, Hermite,
+// central-Hermite, each a compile-time variant.
 template <int LAT, typename ST, typename CT, bool NSE>
 static void launch_step(const LaunchArgs& a, const KParams<CT>& p, const ST* fin, ST* fout) {
-  if (a.pairs) {
-    if (a.central) {
-      if (p.forced) step_kernel_x2<LAT, ST, CT, true, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-      else step_kernel_x2<LAT, ST, CT, true, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-    } else {
-      if (p.forced) step_kernel_x2<LAT, ST, CT, false, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-      else step_kernel_x2<LAT, ST, CT, false, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-    }
-  } else if (a.central) {
-    if (p.forced) step_kernel<LAT, ST, CT, true, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-    else step_kernel<LAT, ST, CT, true, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-  } else {
-    if (p.forced) step_kernel<LAT, ST, CT, false, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
-    else step_kernel<LAT, ST, CT, false, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+  switch (a.central) {
+    case 1: launch_basis<LAT, ST, CT, 1, NSE>(a, p, fin, fout); break;
+    case 2: launch_basis<LAT, ST, CT, 2, NSE>(a, p, fin, fout); break;
+    case 3: launch_basis<LAT, ST, CT, 3, NSE>(a, p, fin, fout); break;
+    default: launch_basis<LAT, ST, CT, 0, NSE>(a, p, fin, fout); break;
   }
 }
 

@@ -39,7 +39,7 @@ enum Op { OP_STEP = 0, OP_INIT_EQ = 1, OP_PLANE = 2, OP_CHECK = 3, OP_STRESS = 4
 struct LaunchArgs {
   Op op;
   int storage;     // ST_*
-  int central;     // 1: central-moment relaxation
+  int central;     // basis of the relaxation, RMRTLB_BASIS_* (0 raw)
   int pairs;       // OP_STEP: two nodes per thread (nx even)
   const void* fin;
   void* fout;

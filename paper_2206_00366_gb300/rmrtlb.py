@@ -131,7 +131,7 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_batch_init_fields": (i, [_vp, i, _vp, _vp, i]),
         "rmrtlb_batch_destroy": (i, [_vp]),
         "rmrtlb_batch_reset": (i, [_vp]),
-        "rmrtlb_batch_tune": (i, [_vp, i, ctypes.POINTER(i)]),
+        "rmrtlb_batch_tune": (i, [_vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "rmrtlb_batch_step": (i, [_vp, i]),
         "rmrtlb_batch_status": (i, [_vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]),
@@ -289,10 +289,10 @@ def rmrtlb_batch_reset(h):
     _check(lib().rmrtlb_batch_reset(h), "rmrtlb_batch_reset")
 
 
-def rmrtlb_batch_tune(h, steps: int) -> int:
-    w = ctypes.c_int()
-    _check(lib().rmrtlb_batch_tune(h, steps, ctypes.byref(w)), "rmrtlb_batch_tune")
-    return w.value
+def rmrtlb_batch_tune(h, steps: int):
+    w, r = ctypes.c_int(), ctypes.c_int()
+    _check(lib().rmrtlb_batch_tune(h, steps, ctypes.byref(w), ctypes.byref(r)), "rmrtlb_batch_tune")
+    return w.value, r.value
 
 
 def rmrtlb_batch_step(h, n: int):
@@ -498,7 +498,10 @@ class Batch:
         rmrtlb_batch_reset(self.h)
 
     def tune(self, steps=20):
-        return rmrtlb_batch_tune(self.h, steps)
+        """Autotune the tile shape; returns the width (threads per block),
+        the rows per tile are kept in self.tile_rows."""
+        w, self.tile_rows = rmrtlb_batch_tune(self.h, steps)
+        return w
 
     def step(self, n=1):
         rmrtlb_batch_step(self.h, n)
