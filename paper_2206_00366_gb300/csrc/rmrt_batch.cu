@@ -78,27 +78,42 @@ __device__ __forceinline__ void load_params(BParams<CT>& sp, const BParams<CT>* 
 __device__ __forceinline__ int tile_width(const int4& t) { return t.w & 0xffff; }
 __device__ __forceinline__ int tile_rows(const int4& t) { return t.w >> 16; }
 
-// Node coordinates of a tile thread: rows are numbered z * ny + y.
+// A node inside its domain: index (x fastest, 32-bit: q N < 2^31 per
+// domain), which neighbours x -/+ 1 along each axis lie inside the box, and
+// whether the node sits in the layer under the lid.
 struct NodeXYZ {
-  int x, y, z;
-  size_t own;
+  int own;
+  bool xm, xp, ym, yp, zm, zp;
+  bool top;
 };
-template <typename CT>
-__device__ __forceinline__ NodeXYZ node_of(int x, int row, const BParams<CT>& sp) {
+template <int LAT, typename CT>
+__device__ __forceinline__ NodeXYZ node_at(int x, int y, int z, const BParams<CT>& sp) {
   NodeXYZ r;
-  r.x = x;
-  r.y = row % sp.k.ny;
-  r.z = row / sp.k.ny;
-  r.own = size_t(row) * sp.k.nx + x;
+  const int nx = sp.k.nx, ny = sp.k.ny, nz = sp.k.nz;
+  r.own = (z * ny + y) * nx + x;
+  r.xm = x > 0; r.xp = x < nx - 1;
+  r.ym = y > 0; r.yp = y < ny - 1;
+  r.zm = z > 0; r.zp = z < nz - 1;
+  r.top = Lat<LAT>::D == 2 ? y == ny - 1 : z == nz - 1;
   return r;
 }
 
-// True when x - e crosses the lid: the face beyond the last node of the
-// last axis (y on rD2Q9, z on the 3-D lattices).
+// True when a source coordinate lies beyond the lid: the face after the
+// last node of the last axis (y on rD2Q9, z on the 3-D lattices).
 template <int LAT>
 __device__ __forceinline__ bool from_lid(int sy, int sz, int ny, int nz) {
   return Lat<LAT>::D == 2 ? sy >= ny : sz >= nz;
 }
+
+// Row r of a tile (rows numbered z * ny + y) as (y, z), advanced by one row
+// with a carry.
+struct RowYZ {
+  int y, z;
+  __device__ __forceinline__ RowYZ(int row, int ny) : y(row % ny), z(row / ny) {}
+  __device__ __forceinline__ void next(int ny) {
+    if (++y == ny) { y = 0; ++z; }
+  }
+};
 
 // Population j arriving at a node: pulled from x - e_j inside the domain,
 // else bounced back from the node itself (half-way bounce-back), with the
@@ -107,13 +122,13 @@ template <int LAT, typename CT, typename ST, int j>
 __device__ __forceinline__ CT gather(const ST* __restrict__ base, const NodeXYZ& n, const BParams<CT>& sp) {
   constexpr int ex = Lat<LAT>::EX[j], ey = Lat<LAT>::EY[j], ez = Lat<LAT>::EZ[j];
   constexpr int jo = opposite_dir<LAT>(j);
-  const int nx = sp.k.nx, ny = sp.k.ny, nz = sp.k.nz;
-  const int sx = n.x - ex, sy = n.y - ey, sz = n.z - ez;
-  const bool inside = unsigned(sx) < unsigned(nx) && unsigned(sy) < unsigned(ny) && unsigned(sz) < unsigned(nz);
-  const size_t N = sp.k.N;
-  const size_t idx = inside ? size_t(j) * N + (size_t(sz) * ny + sy) * nx + sx : size_t(jo) * N + n.own;
+  constexpr bool up_lid = Lat<LAT>::D == 2 ? ey < 0 : ez < 0;   // source one layer beyond the last
+  const bool inside = (ex > 0 ? n.xm : (ex < 0 ? n.xp : true)) && (ey > 0 ? n.ym : (ey < 0 ? n.yp : true)) &&
+                      (ez > 0 ? n.zm : (ez < 0 ? n.zp : true));
+  const int N = int(sp.k.N), nx = sp.k.nx, nxy = sp.k.nx * sp.k.ny;
+  const int idx = inside ? j * N + n.own - ex - ey * nx - ez * nxy : jo * N + n.own;
   CT v = CT(__ldg(base + idx));
-  if (ex != 0 && from_lid<LAT>(sy, sz, ny, nz)) v += sp.lid[j];
+  if (ex != 0 && up_lid && n.top) v += sp.lid[j];
   return v;
 }
 
@@ -129,10 +144,11 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const ST* __restrict__ 
   load_params(sp, dom, t.x);
   if (int(threadIdx.x) >= tile_width(t)) return;
   const ST* base = fin + sp.off;
-  const size_t N = sp.k.N;
-  const int rows = tile_rows(t);
-  for (int r = 0; r < rows; ++r) {
-    const NodeXYZ n = node_of(t.z + int(threadIdx.x), t.y + r, sp);
+  const int N = int(sp.k.N);
+  const int rows = tile_rows(t), x = t.z + int(threadIdx.x);
+  RowYZ yz(t.y, sp.k.ny);
+  for (int r = 0; r < rows; ++r, yz.next(sp.k.ny)) {
+    const NodeXYZ n = node_at<LAT>(x, yz.y, yz.z, sp);
     Cube<LAT, CT> q;
     if constexpr (LAT == LAT_D3Q19) {
 #pragma unroll
@@ -152,7 +168,7 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const ST* __restrict__ 
     static_for<L::Q>([&](auto J) {
       constexpr int j = decltype(J)::value;
       constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-      out[size_t(j) * N] = ST(q.v[ex + 1][ey + 1][zi<LAT>(ez)]);
+      out[j * N] = ST(q.v[ex + 1][ey + 1][zi<LAT>(ez)]);
     });
   }
 }
@@ -199,8 +215,9 @@ __global__ void __launch_bounds__(256) batch_check_kernel(const ST* __restrict__
     if (int(threadIdx.x) < tile_width(t)) {
       const size_t N = sp.k.N;
       double* up = uprev + sp.uoff;
-      for (int r = 0; r < tile_rows(t); ++r) {
-        const NodeXYZ n = node_of(t.z + int(threadIdx.x), t.y + r, sp);
+      RowYZ yz(t.y, sp.k.ny);
+      for (int r = 0; r < tile_rows(t); ++r, yz.next(sp.k.ny)) {
+        const NodeXYZ n = node_at<LAT>(t.z + int(threadIdx.x), yz.y, yz.z, sp);
         CT s0;
         double u[3];
         node_fields<LAT, ST, CT>(fin + sp.off, n, sp, s0, u);
@@ -250,7 +267,7 @@ __global__ void batch_fields_kernel(const ST* __restrict__ fin, const BParams<CT
   const size_t N = sp.k.N;
   for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += size_t(gridDim.x) * blockDim.x) {
     const int row = int(i / sp.k.nx);
-    const NodeXYZ n = node_of(int(i % sp.k.nx), row, sp);
+    const NodeXYZ n = node_at<LAT>(int(i % sp.k.nx), row % sp.k.ny, row / sp.k.ny, sp);
     CT s0;
     double u[3];
     node_fields<LAT, ST, CT>(fin + sp.off, n, sp, s0, u);
