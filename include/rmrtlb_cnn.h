@@ -30,8 +30,12 @@ extern "C" {
 
 /* Forward convolution, channel pairs (cin, cout) = (8, 32), (32, 32),
  * (32, 4):  z[v, co] = bias[co] + sum_t sum_ci x[v + tap_t, ci] w[t, ci, co]
- * in FP32 from BF16 x and w.  Writes z (FP32, NULL to skip) and
- * a = silu(z) (apply_silu != 0) or z, rounded to BF16 (NULL to skip). */
+ * in FP32 from BF16 x and w, as an implicit GEMM on the tensor cores
+ * (tcgen05.mma kind::f16, FP32 accumulator in tensor memory; M = 128 voxels,
+ * N = cout, K = 27 taps x cin).  Writes z (FP32, NULL to skip) and
+ * a = silu(z) (apply_silu != 0) or z, rounded to BF16 (NULL to skip).
+ * Every wait for tensor-core completion is bounded; a wait that gives up
+ * leaves the output unwritten and is reported by rmrtlb_cnn_check. */
 int rmrtlb_conv3d_forward(int n, int d, int h, int w, int cin, int cout,
                           const uint16_t* x, const uint16_t* weight, const float* bias,
                           int apply_silu, float* z, uint16_t* a, void* stream);
@@ -39,7 +43,8 @@ int rmrtlb_conv3d_forward(int n, int d, int h, int w, int cin, int cout,
 /* Gradient with respect to the input, channel pairs (32, 32), (32, 4):
  * dx[v, ci] = sum_t sum_co dy[v - tap_t, co] w[t, ci, co], multiplied by
  * silu'(z_in[v, ci]) when z_in (the FP32 pre-activation that produced x)
- * is not NULL.  dy, z_in, dx FP32. */
+ * is not NULL; the same tensor-core implicit GEMM with dy rounded to BF16
+ * (nearest even) on the way in.  dy, z_in, dx FP32. */
 int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout,
                                 const float* dy, const uint16_t* weight, const float* z_in,
                                 float* dx, void* stream);
@@ -83,6 +88,12 @@ int rmrtlb_cavity_features(int n, int d, int h, int w, const double* re, uint16_
  * (I + 1/2) n / N - 1/2, clamped to [0, n - 1]. */
 int rmrtlb_upsample_fields(int d, int h, int w, int c, const float* src, int D, int H, int W,
                            const double* scale, const double* offset, double* dst, void* stream);
+
+/* Synchronises `stream` and returns RMRTLB_ECUDA if any tensor-core
+ * convolution since the last call gave up waiting for its MMAs (a bounded
+ * wait; the kernel then skips its outputs) or if the stream reports an
+ * error, else RMRTLB_OK.  Clears the condition. */
+int rmrtlb_cnn_check(void* stream);
 
 /* Training targets of one cavity from its fields: for each of n nodes,
  * out[4 i + 0] = (rho[i] - rho0) * rho_scale, out[4 i + 1 + a] =

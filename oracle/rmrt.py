@@ -43,6 +43,7 @@ from itertools import product
 import numpy as np
 
 LATTICES = ("D2Q9", "D3Q19", "D3Q27")
+AXIS_LATTICES = ("D2Q5", "D3Q7")     # rDdQ(2d+1): rest and axis directions only (Remark I of Sec. III)
 
 
 # --------------------------------------------------------------------------
@@ -58,7 +59,13 @@ def velocity_indices(name: str) -> np.ndarray:
     (-c1,0,-c3) twice each; it is read as (c1,0,c3), (-c1,0,c3),
     (-c1,0,-c3), (c1,0,-c3), the same sign pattern as the yz block.  rD3Q19
     is the rD3Q27 set without the corners (j >= 19), as Sec. III states.
+    rD2Q5 and rD3Q7 (Remark I) are the rest and axis directions, the first
+    5 of rD2Q9 and the first 7 of rD3Q27.
     """
+    if name == "D2Q5":
+        return velocity_indices("D2Q9")[:5]
+    if name == "D3Q7":
+        return velocity_indices("D3Q27")[:7]
     if name == "D2Q9":
         ex = [0, 1, 0, -1, 0, 1, -1, -1, 1]
         ey = [0, 0, 1, 0, -1, 1, 1, -1, -1]
@@ -86,12 +93,18 @@ def weights(name: str, c: np.ndarray, cs2: float) -> np.ndarray:
     (0, c_s^2 / (8 c_alpha^2)); it is fixed to c_s^6 / (8 c1^2 c2^2 c3^2),
     the value for which every weight factors into one-dimensional weights.
     rD3Q19: Eq. (3-3-8) with omega_19 = 0 (Sec. III, special case (1)).
+    rD2Q5 (type I, omega_5 = 0) and rD3Q7: omega_alpha = c_s^2 / (2 c_alpha^2)
+    for the two directions along axis alpha (Remark I of Sec. III).
     omega_0 = 1 - sum_{j>0} omega_j in every case (Eqs. 3-1, 3-2).
     """
     e = velocity_indices(name)
     q = e.shape[0]
     w = np.zeros(q)
-    if name == "D2Q9":
+    if name in AXIS_LATTICES:
+        for j in range(1, q):
+            al = int(np.flatnonzero(e[j])[0])
+            w[j] = cs2 / (2.0 * c[al] * c[al])
+    elif name == "D2Q9":
         c1, c2 = c
         w5 = cs2 * cs2 / (4.0 * c1 * c1 * c2 * c2)
         w1 = cs2 / (2.0 * c1 * c1) - 2.0 * w5
@@ -145,17 +158,20 @@ class Lattice:
 
 
 def make_lattice(name: str, dx, dt: float = 1.0, cs2: float | None = None) -> Lattice:
-    """Build a lattice; c_s^2 defaults to min_alpha c_alpha^2 / 3.
+    """Build a lattice; c_s^2 defaults to min_alpha c_alpha^2 / 3 (rD3Q7:
+    min_alpha c_alpha^2 / 4).
 
     The paper leaves c_s a free parameter subject to 0 < c_s^2 < c_alpha^2
     and omega_j >= 0 (Sec. III).  The default reduces to c^2/3 on the
-    standard lattice.  A configuration with a negative weight, or with
-    c_s^2 >= min c_alpha^2, is rejected.
+    standard lattice; on rD3Q7, c^2/3 would make omega_0 = 0 there (Remark
+    II: the rest velocity drops out), so its default is c^2/4, the usual
+    D3Q7 choice (weights 1/4, 1/8).  A configuration with a negative weight,
+    or with c_s^2 >= min c_alpha^2, is rejected.
     """
-    d = 2 if name == "D2Q9" else 3
+    d = 2 if name in ("D2Q9", "D2Q5") else 3
     c = np.array([float(v) for v in dx[:d]]) / dt
     if cs2 is None or cs2 <= 0:
-        cs2 = float(np.min(c * c)) / 3.0
+        cs2 = float(np.min(c * c)) / (4.0 if name == "D3Q7" else 3.0)
     lat = Lattice(name, tuple(dx), dt, float(cs2))
     if not np.all(cs2 < c * c):
         raise ValueError("c_s^2 must be below every c_alpha^2")
@@ -176,9 +192,15 @@ def monomials(name: str) -> list:
     rD3Q19: the paper prints no rD3Q19 basis; it is read as the 19 monomials
     of Eq. (5-2) that have at least one zero exponent (every other monomial
     vanishes on the rD3Q19 velocities).
+    rD2Q5, rD3Q7: 1, the first powers and the squares of each axis (the
+    raw moments that do not vanish identically on axis-only velocities).
     """
     if name == "D2Q9":
         return [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2), (1, 1), (1, 2), (2, 1), (2, 2)]
+    if name == "D2Q5":
+        return [(0, 0), (1, 0), (0, 1), (2, 0), (0, 2)]
+    if name == "D3Q7":
+        return [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2)]
     allm = sorted(product(range(3), repeat=3), key=lambda a: (sum(a), [-v for v in a]))
     if name == "D3Q19":
         allm = [a for a in allm if min(a) == 0]
@@ -368,6 +390,10 @@ def s2_apply(lat: Lattice, S: np.ndarray, X: np.ndarray) -> np.ndarray:
 # Model closures (Sec. IV)
 # --------------------------------------------------------------------------
 NSE, NSE_HELUO, NCDE_LINEAR, NCDE_QUAD = "nse", "nse_heluo", "ncde_linear", "ncde_quad"
+# the simplified NCDE of Eq. (4-16): linear EDF, G from the time derivative of B
+NCDE_SIMPLE_LINEAR, NCDE_SIMPLE_QUAD = "ncde_simple_linear", "ncde_simple_quad"
+NCDE_SIMPLE = (NCDE_SIMPLE_LINEAR, NCDE_SIMPLE_QUAD)
+NCDE_KINDS = (NCDE_LINEAR, NCDE_QUAD) + NCDE_SIMPLE
 RAW, CENTRAL, HERMITE, CENTRAL_HERMITE = "raw", "central", "hermite", "central_hermite"
 
 
@@ -411,10 +437,16 @@ def ncde_flux(m: Model, phi: np.ndarray, d: int):
     D = phi I, beta = 1 and C = int B' B' dphi (first case of Eq. 4-11):
       linear:     B = u phi,        C = u u phi,          B' = u
       quadratic:  B = u phi^2 / 2,  C = u u phi^3 / 3,    B' = u phi
-    with u the constant advection velocity.
+    with u the constant advection velocity.  The simplified kinds of
+    Eq. (4-16) take C = 0 with the same B.
     """
     u = np.asarray(m.adv[:d], dtype=np.float64)
     uu = np.outer(u, u)
+    if m.kind in NCDE_SIMPLE:
+        lin = m.kind == NCDE_SIMPLE_LINEAR
+        B = (phi if lin else 0.5 * phi * phi)[:, None] * u[None, :]
+        Bp = np.broadcast_to(u, (phi.size, d)).copy() if lin else phi[:, None] * u[None, :]
+        return B, np.zeros((phi.size, d, d)), Bp
     if m.kind == NCDE_LINEAR:
         B = phi[:, None] * u[None, :]
         C = phi[:, None, None] * uu[None]
@@ -439,7 +471,7 @@ def macroscopic(lat: Lattice, m: Model, fbar: np.ndarray):
     dt, d = lat.dt, lat.d
     n = fbar.shape[1]
     rho = fbar.sum(axis=0) + 0.5 * dt * source_of(m, n)
-    if m.kind in (NCDE_LINEAR, NCDE_QUAD):
+    if m.kind in NCDE_KINDS:
         u = np.broadcast_to(np.asarray(m.adv[:d], float), (rho.size, d)).copy()
         return rho, u
     F = force_of(m, d, n)
@@ -448,7 +480,7 @@ def macroscopic(lat: Lattice, m: Model, fbar: np.ndarray):
     return rho, (j / den).T
 
 
-def equilibrium_and_sources(lat: Lattice, m: Model, S: np.ndarray, rho, u):
+def equilibrium_and_sources(lat: Lattice, m: Model, S: np.ndarray, rho, u, dBdt=None):
     """f^eq, G and F on a node list, each of shape (q, n).
 
     NSE (Eqs. NSEfeq, NSEGeq, NSEFeq):
@@ -460,9 +492,20 @@ def equilibrium_and_sources(lat: Lattice, m: Model, S: np.ndarray, rho, u):
     NCDE (Eqs. 4-14, 4-14-1): f^eq = g^eq(phi, B, C) (D = phi I, beta = 1),
       F = g^eq(S, 0, 0) = omega S, G = g^eq(0, M_1G, 0) with
       M_1G = (I - S_1/2) B' S (Eq. 4-11, first case).
+    Simplified NCDE (Eq. 4-16): f^eq = g^eq(phi, B, 0), F = omega S,
+      G = g^eq(0, (I - S_1/2) dB/dt, 0), dB/dt given per node (n, d).
     """
     d, n, cs2 = lat.d, rho.size, lat.cs2
     I = np.eye(d)
+    if m.kind in NCDE_SIMPLE:
+        B, C, _ = ncde_flux(m, rho, d)
+        feq = geq(lat, rho, B, C)
+        Sn = source_of(m, n)
+        F = geq(lat, Sn, np.zeros((n, d)), np.zeros((n, d, d)))
+        s1 = np.array([S[k, k] for k, a in enumerate(monomials(lat.name)) if sum(a) == 1])
+        dB = np.zeros((n, d)) if dBdt is None else dBdt
+        G = geq(lat, np.zeros(n), (1.0 - 0.5 * s1)[None, :] * dB, np.zeros((n, d, d)))
+        return feq, G, F
     if m.kind in (NCDE_LINEAR, NCDE_QUAD):
         B, C, Bp = ncde_flux(m, rho, d)
         feq = geq(lat, rho, B, C)
@@ -489,7 +532,7 @@ def equilibrium_and_sources(lat: Lattice, m: Model, S: np.ndarray, rho, u):
 # --------------------------------------------------------------------------
 # Collision in moment space and propagation (Eqs. 2-2-3, 2-2b)
 # --------------------------------------------------------------------------
-def collide(lat: Lattice, m: Model, S: np.ndarray, fbar: np.ndarray) -> np.ndarray:
+def collide(lat: Lattice, m: Model, S: np.ndarray, fbar: np.ndarray, dBdt=None) -> np.ndarray:
     """Post-collision populations on a node list (q, n), Eq. (2-2-3).
 
     Raw basis:     m*  = mbar - S (mbar - m^eq) + dt (m_G + (I - S/2) m_F),
@@ -504,7 +547,7 @@ def collide(lat: Lattice, m: Model, S: np.ndarray, fbar: np.ndarray) -> np.ndarr
     """
     dt = lat.dt
     rho, u = macroscopic(lat, m, fbar)
-    feq, G, F = equilibrium_and_sources(lat, m, S, rho, u)
+    feq, G, F = equilibrium_and_sources(lat, m, S, rho, u, dBdt)
     I = np.eye(S.shape[0])
     if m.basis == RAW:
         M = moment_matrix(lat)
@@ -569,12 +612,27 @@ def stream(lat: Lattice, fstar: np.ndarray, walls: tuple = (), lid=None) -> np.n
 
 
 def step(lat: Lattice, m: Model, S: np.ndarray, fbar: np.ndarray, nsteps: int = 1,
-         walls: tuple = (), lid=None) -> np.ndarray:
-    """nsteps of collide-and-stream on a field (q, nz, ny, nx)."""
+         walls: tuple = (), lid=None, state: dict | None = None) -> np.ndarray:
+    """nsteps of collide-and-stream on a field (q, nz, ny, nx).
+
+    The simplified NCDE kinds (Eq. 4-16) need B at the previous step: it is
+    kept in `state["B"]` (node list (n, d)) across calls when a dict is
+    passed; with no previous value dB/dt is taken as zero (the first step
+    after initialisation), dB/dt = (B(t) - B(t - dt)) / dt afterwards.
+    """
     shape = fbar.shape
     f = fbar
+    state = {} if state is None else state
     for _ in range(nsteps):
-        fs = collide(lat, m, S, f.reshape(lat.q, -1)).reshape(shape)
+        fl = f.reshape(lat.q, -1)
+        dB = None
+        if m.kind in NCDE_SIMPLE:
+            phi, _ = macroscopic(lat, m, fl)
+            B, _, _ = ncde_flux(m, phi, lat.d)
+            prev = state.get("B")
+            dB = np.zeros_like(B) if prev is None else (B - prev) / lat.dt
+            state["B"] = B
+        fs = collide(lat, m, S, fl, dB).reshape(shape)
         f = stream(lat, fs, walls, lid)
     return f
 

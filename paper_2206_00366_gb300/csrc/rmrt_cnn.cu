@@ -2,11 +2,10 @@
 // convolution forward and backward, MSE, Adam, input features, trilinear
 // upsampling.  BF16 activations and weights, FP32 accumulation.
 //
-// The convolutions run on the FP32 pipes: one thread per output voxel and
-// group of up to 8 output channels, the block's weight slice staged once
-// in shared memory as FP32, input rows read as 16-byte vectors (8 BF16
-// channels).  Every reduction over voxels is done in a fixed order (per
-// block partials, then a fixed-order sum), so results are deterministic.
+// The forward and input-gradient convolutions are implicit GEMMs on the
+// tensor cores (tcgen05, rmrt_cnn_tc.cuh).  The weight gradient runs on the
+// FP32 pipes with a fixed-order reduction over voxels (per-block partials,
+// then a fixed-order sum), so results are deterministic.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -14,6 +13,7 @@
 
 #include "../../include/rmrtlb.h"
 #include "../../include/rmrtlb_cnn.h"
+#include "rmrt_cnn_tc.cuh"
 
 namespace {
 
@@ -53,117 +53,171 @@ __device__ __forceinline__ long long neighbour(const VoxCoord& c, int dz, int dy
   return (((long long)c.s * g.d + z) * g.h + y) * g.w + x;
 }
 
-// ------------------------------------------------------------------ forward
-// grid (ceil(V / 128), COUT / G); thread: one voxel, output channels
-// [G * blockIdx.y, G * blockIdx.y + G), G = min(8, COUT).
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(kThreads) conv_fwd_kernel(Vol g, const uint16_t* __restrict__ x,
-                                                            const uint16_t* __restrict__ wt,
-                                                            const float* __restrict__ bias, int apply_silu,
-                                                            float* __restrict__ z, uint16_t* __restrict__ a) {
-  constexpr int G = COUT < 8 ? COUT : 8;
-  __shared__ float ws[27 * CIN * G];
-  const int co0 = blockIdx.y * G;
-  for (int i = threadIdx.x; i < 27 * CIN * G; i += kThreads) {
-    const int gg = i % G, tc = i / G;   // tc = t * CIN + ci
-    ws[i] = bf2f(wt[size_t(tc) * COUT + co0 + gg]);
-  }
-  __syncthreads();
-  const long long v = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (v >= g.voxels()) return;
-  const VoxCoord c = coord_of(v, g);
-  float acc[G];
-#pragma unroll
-  for (int k = 0; k < G; ++k) acc[k] = bias[co0 + k];
-  for (int t = 0; t < 27; ++t) {
-    const long long nb = neighbour(c, t / 9 - 1, (t / 3) % 3 - 1, t % 3 - 1, g);
-    if (nb < 0) continue;
-    const uint4* src = reinterpret_cast<const uint4*>(x + nb * CIN);
-#pragma unroll
-    for (int q = 0; q < CIN / 8; ++q) {
-      const uint4 pk = __ldg(src + q);
-      const uint32_t wd[4] = {pk.x, pk.y, pk.z, pk.w};
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const float xv = bf2f(uint16_t(wd[e >> 1] >> (16 * (e & 1))));
-        const float* wr = ws + (t * CIN + q * 8 + e) * G;
-#pragma unroll
-        for (int k = 0; k < G; ++k) acc[k] = fmaf(xv, wr[k], acc[k]);
-      }
-    }
-  }
-  if (z) {
-    float4* zo = reinterpret_cast<float4*>(z + v * COUT + co0);
-#pragma unroll
-    for (int k = 0; k < G / 4; ++k) zo[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
-  }
-  if (a) {
-    uint32_t pk[G / 2];
-#pragma unroll
-    for (int k = 0; k < G / 2; ++k) {
-      float p0 = acc[2 * k], p1 = acc[2 * k + 1];
-      if (apply_silu) {
-        p0 *= sigm(p0);
-        p1 *= sigm(p1);
-      }
-      pk[k] = uint32_t(f2bf(p0)) | (uint32_t(f2bf(p1)) << 16);
-    }
-    uint32_t* ao = reinterpret_cast<uint32_t*>(a + v * COUT + co0);
-#pragma unroll
-    for (int k = 0; k < G / 2; ++k) ao[k] = pk[k];
-  }
-}
+// ------------------------------------------------------------------ forward and input gradient
+constexpr int kTcThreads = 128;
+constexpr uint32_t kWaitLimit = 1u << 26;   // mbarrier polls before a kernel gives up
 
-// ------------------------------------------------------------------ backward data
-// grid (ceil(V / 128), CIN / G); thread: one voxel, input channels
-// [G * blockIdx.y, G * blockIdx.y + G).
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(kThreads) conv_bwd_data_kernel(Vol g, const float* __restrict__ dy,
-                                                                 const uint16_t* __restrict__ wt,
-                                                                 const float* __restrict__ zin,
-                                                                 float* __restrict__ dx) {
-  constexpr int G = CIN < 8 ? CIN : 8;
-  __shared__ float ws[27 * COUT * G];   // ws[(t * COUT + co) * G + k] = w[t, ci0 + k, co]
-  const int ci0 = blockIdx.y * G;
-  for (int i = threadIdx.x; i < 27 * COUT * G; i += kThreads) {
-    const int k = i % G, tc = i / G, co = tc % COUT, t = tc / COUT;
-    ws[i] = bf2f(wt[(size_t(t) * CIN + ci0 + k) * COUT + co]);
+template <int KIN, int NOUT>
+struct TcShape {
+  static constexpr int KP = KIN < 16 ? 16 : KIN;     // K per tap, padded to the MMA's 16
+  static constexpr int NP = NOUT < 16 ? 16 : NOUT;   // N padded to 16 (M = 128 needs N % 16 == 0)
+  static constexpr int KC = KP / 8;                  // core matrices along K
+  static constexpr int B_TAP = NP * KP * 2;          // bytes of one tap's weights
+  static constexpr int A_BUF = 128 * KP * 2;         // bytes of one A buffer
+  static constexpr int SMEM = 27 * B_TAP + 2 * A_BUF + 64;
+};
+
+// See rmrt_cnn_tc.cuh.  MODE 0: forward of a layer with cin = KIN, cout =
+// NOUT (in: BF16 x; out: z = acc + bias in FP32 and a = silu(z) or z in
+// BF16).  MODE 1: input gradient of a layer with cin = NOUT, cout = KIN (in:
+// FP32 dy, rounded to BF16; out: dx = acc * silu'(zin) or acc, FP32).
+template <int KIN, int NOUT, int MODE>
+__global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* __restrict__ in,
+                                                             const uint16_t* __restrict__ wt,
+                                                             const float* __restrict__ bias,
+                                                             const float* __restrict__ zin, int apply_silu,
+                                                             float* __restrict__ zout, uint16_t* __restrict__ aout,
+                                                             int* __restrict__ err) {
+  using S = TcShape<KIN, NOUT>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ int s_ok;
+  uint8_t* Bs = smem;
+  uint8_t* As = smem + 27 * S::B_TAP;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(As + 2 * S::A_BUF);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  // weights of every tap, B_t[n][k] K-major in 8 x 16-byte core matrices
+  for (int i = tid; i < 27 * S::NP * S::KP; i += kTcThreads) {
+    const int t = i / (S::NP * S::KP), rem = i % (S::NP * S::KP), n = rem / S::KP, k = rem % S::KP;
+    uint16_t val = 0;
+    if (n < NOUT && k < KIN)
+      val = MODE == 0 ? wt[(size_t(t) * KIN + k) * NOUT + n] : wt[(size_t(t) * NOUT + n) * KIN + k];
+    *reinterpret_cast<uint16_t*>(Bs + t * S::B_TAP + ((n >> 3) * S::KC + (k >> 3)) * 128 + (n & 7) * 16 +
+                                 (k & 7) * 2) = val;
   }
+  if (warp == 0) tc::tmem_alloc(tslot, 32);
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
   __syncthreads();
-  const long long v = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (v >= g.voxels()) return;
-  const VoxCoord c = coord_of(v, g);
-  float acc[G];
+  tc::fence_after();
+  const uint32_t taddr = *tslot;
+  const uint32_t idesc = tc::idesc_bf16(S::NP);
+  const uint32_t lane_base = uint32_t(warp * 32) << 16;
+
+  const long long V = g.voxels();
+  const long long tiles = (V + 127) / 128;
+  uint32_t T = 0;   // taps issued by this CTA (selects the A buffer and the barrier phase)
+  bool ok = true;
+  for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    const long long v = tile * 128 + tid;
+    const bool valid = v < V;
+    const VoxCoord c = coord_of(valid ? v : 0, g);
+    for (int t = 0; t < 27; ++t, ++T) {
+      const int b = int(T & 1);
+      // buffer b is free once the MMAs of tap T - 2 have completed
+      if (tid == 0) s_ok = T < 2 ? 1 : int(tc::mbar_wait(&bar[b], ((T - 2) >> 1) & 1, kWaitLimit));
+      __syncthreads();
+      if (!s_ok) { ok = false; break; }
+      uint4 row[S::KC];
 #pragma unroll
-  for (int k = 0; k < G; ++k) acc[k] = 0.0f;
-  for (int t = 0; t < 27; ++t) {
-    // dy at v - tap_t
-    const long long nb = neighbour(c, 1 - t / 9, 1 - (t / 3) % 3, 1 - t % 3, g);
-    if (nb < 0) continue;
-    const float4* src = reinterpret_cast<const float4*>(dy + nb * COUT);
+      for (int q = 0; q < S::KC; ++q) row[q] = make_uint4(0, 0, 0, 0);
+      if (valid) {
+        const int dz = t / 9 - 1, dyo = (t / 3) % 3 - 1, dxo = t % 3 - 1;
+        const long long nb = MODE == 0 ? neighbour(c, dz, dyo, dxo, g) : neighbour(c, -dz, -dyo, -dxo, g);
+        if (nb >= 0) {
+          if constexpr (MODE == 0) {
+            const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(in) + nb * KIN);
 #pragma unroll
-    for (int q = 0; q < COUT / 4; ++q) {
-      const float4 d4 = __ldg(src + q);
-      const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+            for (int q = 0; q < KIN / 8; ++q) row[q] = __ldg(src + q);
+          } else {
+            const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(in) + nb * KIN);
+            uint32_t pk[S::KP / 2];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float* wr = ws + (t * COUT + q * 4 + e) * G;
+            for (int q = 0; q < S::KP / 2; ++q) pk[q] = 0;
 #pragma unroll
-        for (int k = 0; k < G; ++k) acc[k] = fmaf(dv[e], wr[k], acc[k]);
+            for (int q = 0; q < KIN / 4; ++q) {
+              const float4 f = __ldg(src + q);
+              pk[2 * q] = uint32_t(f2bf(f.x)) | (uint32_t(f2bf(f.y)) << 16);
+              pk[2 * q + 1] = uint32_t(f2bf(f.z)) | (uint32_t(f2bf(f.w)) << 16);
+            }
+#pragma unroll
+            for (int q = 0; q < S::KC; ++q) row[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+          }
+        }
+      }
+      uint8_t* Ab = As + b * S::A_BUF;
+#pragma unroll
+      for (int q = 0; q < S::KC; ++q)
+        *reinterpret_cast<uint4*>(Ab + ((tid >> 3) * S::KC + q) * 128 + (tid & 7) * 16) = row[q];
+      tc::fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after();
+#pragma unroll
+        for (int kk = 0; kk < S::KP / 16; ++kk) {
+          const uint64_t ad = tc::smem_desc(tc::smem_u32(Ab) + kk * 256, 128, S::KC * 128);
+          const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + t * S::B_TAP) + kk * 256, 128, S::KC * 128);
+          tc::mma_bf16(taddr, ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&bar[b]);
+      }
+    }
+    if (!ok) break;
+    // the last commit covers every MMA issued before it
+    if (tid == 0) s_ok = int(tc::mbar_wait(&bar[(T - 1) & 1], ((T - 1) >> 1) & 1, kWaitLimit));
+    __syncthreads();
+    if (!s_ok) { ok = false; break; }
+    tc::fence_after();
+    float acc[32];
+    tc::tmem_ld16(taddr + lane_base, *reinterpret_cast<float(*)[16]>(acc));
+    if constexpr (S::NP == 32) tc::tmem_ld16(taddr + lane_base + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+    tc::fence_before();
+    if (valid) {
+      if constexpr (MODE == 0) {
+#pragma unroll
+        for (int n = 0; n < NOUT; ++n) acc[n] += bias[n];
+        if (zout) {
+          float4* zo = reinterpret_cast<float4*>(zout + v * NOUT);
+#pragma unroll
+          for (int q = 0; q < NOUT / 4; ++q) zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+        if (aout) {
+          uint32_t* ao = reinterpret_cast<uint32_t*>(aout + v * NOUT);
+#pragma unroll
+          for (int q = 0; q < NOUT / 2; ++q) {
+            float p0 = acc[2 * q], p1 = acc[2 * q + 1];
+            if (apply_silu) {
+              p0 *= sigm(p0);
+              p1 *= sigm(p1);
+            }
+            ao[q] = uint32_t(f2bf(p0)) | (uint32_t(f2bf(p1)) << 16);
+          }
+        }
+      } else {
+        if (zin) {
+          const float* zr = zin + v * NOUT;
+#pragma unroll
+          for (int n = 0; n < NOUT; ++n) {
+            const float zz = zr[n], sg = sigm(zz);
+            acc[n] *= sg * (1.0f + zz * (1.0f - sg));
+          }
+        }
+        float4* dx = reinterpret_cast<float4*>(zout + v * NOUT);
+#pragma unroll
+        for (int q = 0; q < NOUT / 4; ++q) dx[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
       }
     }
   }
-  if (zin) {
-    const float* zr = zin + v * CIN + ci0;
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-      const float zz = zr[k], s = sigm(zz);
-      acc[k] *= s * (1.0f + zz * (1.0f - s));
-    }
-  }
-  float4* out = reinterpret_cast<float4*>(dx + v * CIN + ci0);
-#pragma unroll
-  for (int k = 0; k < G / 4; ++k) out[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+  if (!ok && tid == 0) atomicExch(err, 1);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, 32);
 }
 
 // ------------------------------------------------------------------ backward weight
@@ -362,20 +416,40 @@ bool vol_ok(int n, int d, int h, int w) {
 int status_of(cudaError_t e) { return e == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA; }
 unsigned blocks_for(long long items, int per) { return unsigned((items + per - 1) / per); }
 
-template <int CIN, int COUT>
-int fwd(Vol g, const uint16_t* x, const uint16_t* w, const float* b, int silu, float* z, uint16_t* a,
-        cudaStream_t s) {
-  constexpr int G = COUT < 8 ? COUT : 8;
-  conv_fwd_kernel<CIN, COUT><<<dim3(blocks_for(g.voxels(), kThreads), COUT / G), kThreads, 0, s>>>(g, x, w, b, silu,
-                                                                                                    z, a);
-  return status_of(cudaGetLastError());
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  }
+  return n;
 }
 
-template <int CIN, int COUT>
-int bwd_data(Vol g, const float* dy, const uint16_t* w, const float* zin, float* dx, cudaStream_t s) {
-  constexpr int G = CIN < 8 ? CIN : 8;
-  conv_bwd_data_kernel<CIN, COUT><<<dim3(blocks_for(g.voxels(), kThreads), CIN / G), kThreads, 0, s>>>(g, dy, w,
-                                                                                                        zin, dx);
+// Device word the tensor-core kernels set when an mbarrier wait gives up.
+int* tc_error_word() {
+  static int* p = nullptr;
+  if (!p && cudaMalloc(&p, sizeof(int)) == cudaSuccess) cudaMemset(p, 0, sizeof(int));
+  return p;
+}
+
+template <int KIN, int NOUT, int MODE>
+int launch_tc(Vol g, const void* in, const uint16_t* w, const float* bias, const float* zin, int silu, float* zout,
+              uint16_t* aout, cudaStream_t s) {
+  using S = TcShape<KIN, NOUT>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(conv_tc_kernel<KIN, NOUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
+        cudaSuccess)
+      return RMRTLB_ECUDA;
+    attr = true;
+  }
+  int* err = tc_error_word();
+  if (!err) return RMRTLB_ECUDA;
+  const long long tiles = (g.voxels() + 127) / 128;
+  const long long cap = 3LL * sm_count();
+  const unsigned grid = unsigned(tiles < cap ? tiles : cap);
+  conv_tc_kernel<KIN, NOUT, MODE><<<grid, kTcThreads, S::SMEM, s>>>(g, in, w, bias, zin, silu, zout, aout, err);
   return status_of(cudaGetLastError());
 }
 
@@ -405,9 +479,9 @@ int rmrtlb_conv3d_forward(int n, int d, int h, int w, int cin, int cout, const u
   if ((z && !aligned16(z)) || (a && (reinterpret_cast<size_t>(a) & 7))) return RMRTLB_EINVAL;
   const Vol g{n, d, h, w};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cin == 8 && cout == 32) return fwd<8, 32>(g, x, weight, bias, apply_silu, z, a, s);
-  if (cin == 32 && cout == 32) return fwd<32, 32>(g, x, weight, bias, apply_silu, z, a, s);
-  if (cin == 32 && cout == 4) return fwd<32, 4>(g, x, weight, bias, apply_silu, z, a, s);
+  if (cin == 8 && cout == 32) return launch_tc<8, 32, 0>(g, x, weight, bias, nullptr, apply_silu, z, a, s);
+  if (cin == 32 && cout == 32) return launch_tc<32, 32, 0>(g, x, weight, bias, nullptr, apply_silu, z, a, s);
+  if (cin == 32 && cout == 4) return launch_tc<32, 4, 0>(g, x, weight, bias, nullptr, apply_silu, z, a, s);
   return RMRTLB_EINVAL;
 }
 
@@ -416,8 +490,8 @@ int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout, c
   if (!vol_ok(n, d, h, w) || !aligned16(dy) || !weight || !aligned16(dx)) return RMRTLB_EINVAL;
   const Vol g{n, d, h, w};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cin == 32 && cout == 32) return bwd_data<32, 32>(g, dy, weight, z_in, dx, s);
-  if (cin == 32 && cout == 4) return bwd_data<32, 4>(g, dy, weight, z_in, dx, s);
+  if (cin == 32 && cout == 32) return launch_tc<32, 32, 1>(g, dy, weight, nullptr, z_in, 0, dx, nullptr, s);
+  if (cin == 32 && cout == 4) return launch_tc<4, 32, 1>(g, dy, weight, nullptr, z_in, 0, dx, nullptr, s);
   return RMRTLB_EINVAL;
 }
 
@@ -483,6 +557,17 @@ int rmrtlb_upsample_fields(int d, int h, int w, int c, const float* src, int D, 
   const long long N = (long long)D * H * W;
   upsample_kernel<<<blocks_for(N, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, src, dst);
   return status_of(cudaGetLastError());
+}
+
+int rmrtlb_cnn_check(void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RMRTLB_ECUDA;
+  int* err = tc_error_word();
+  if (!err) return RMRTLB_ECUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return RMRTLB_ECUDA;
+  if (h && cudaMemset(err, 0, sizeof(int)) != cudaSuccess) return RMRTLB_ECUDA;
+  return h ? RMRTLB_ECUDA : RMRTLB_OK;
 }
 
 int rmrtlb_pack_fields(long long n, int d, const double* rho, const double* u, double rho0, double rho_scale,

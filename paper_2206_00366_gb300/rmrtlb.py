@@ -128,6 +128,7 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_cavity_features": (i, [i, i, i, i, _vp, _vp, _vp]),
         "rmrtlb_upsample_fields": (i, [i, i, i, i, _vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), _vp, _vp]),
         "rmrtlb_pack_fields": (i, [ctypes.c_longlong, i, _vp, _vp, d, d, d, _vp, _vp]),
+        "rmrtlb_cnn_check": (i, [_vp]),
         "rmrtlb_batch_init_fields": (i, [_vp, i, _vp, _vp, i]),
         "rmrtlb_batch_destroy": (i, [_vp]),
         "rmrtlb_batch_reset": (i, [_vp]),
@@ -157,7 +158,7 @@ def exported_symbols() -> list:
             "rmrtlb_batch_get_populations", "rmrtlb_batch_fields", "rmrtlb_batch_run", "rmrtlb_batch_init_fields",
             "rmrtlb_conv3d_forward", "rmrtlb_conv3d_backward_data", "rmrtlb_conv3d_backward_weight_scratch",
             "rmrtlb_conv3d_backward_weight", "rmrtlb_mse", "rmrtlb_adam", "rmrtlb_cavity_features",
-            "rmrtlb_upsample_fields", "rmrtlb_pack_fields"]
+            "rmrtlb_upsample_fields", "rmrtlb_pack_fields", "rmrtlb_cnn_check"]
 
 
 def _check(status: int, where: str):
@@ -361,6 +362,10 @@ def rmrtlb_upsample_fields(d, h, w, c, src, D, H, W, scale, offset, dst, stream=
     sc = (ctypes.c_double * c)(*[float(v) for v in scale])
     of = (ctypes.c_double * c)(*[float(v) for v in offset])
     _check(lib().rmrtlb_upsample_fields(d, h, w, c, src, D, H, W, sc, of, dst, stream), "rmrtlb_upsample_fields")
+
+
+def rmrtlb_cnn_check(stream=0):
+    _check(lib().rmrtlb_cnn_check(stream), "rmrtlb_cnn_check")
 
 
 def rmrtlb_pack_fields(n, d, rho, u, rho0, rho_scale, u_scale, out, stream=0):

@@ -217,6 +217,7 @@ def train(net, T, res, shape, epochs, batch=4, lr=2e-3, lr_end=1e-4, seed=0, log
             tb = T[torch.as_tensor(idx, device=T.device)].contiguous()
             acc += net.train_step([res[j] for j in idx], shape, tb, float(rate))
             k += 1
+        B.rmrtlb_cnn_check()
         mean = float(acc.item()) / max(1, n // batch)
         losses.append(mean)
         if log:
@@ -230,6 +231,7 @@ def warm_fields(net, re, coarse, fine, dom, rho0=1.0):
     rho (nz, ny, nx) and u (3, nz, ny, nx)."""
     import torch
     y = net.forward([re], coarse)
+    B.rmrtlb_cnn_check()
     D, H, W = fine
     dst = torch.empty((4, D, H, W), dtype=torch.float64, device=net.device)
     rs, us = scales(dom)

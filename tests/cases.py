@@ -12,7 +12,8 @@ import numpy as np
 
 import oracle.rmrt as R
 
-KIND = {"nse": R.NSE, "nse_heluo": R.NSE_HELUO, "ncde_linear": R.NCDE_LINEAR, "ncde_quad": R.NCDE_QUAD}
+KIND = {"nse": R.NSE, "nse_heluo": R.NSE_HELUO, "ncde_linear": R.NCDE_LINEAR, "ncde_quad": R.NCDE_QUAD,
+        "ncde_simple_linear": R.NCDE_SIMPLE_LINEAR, "ncde_simple_quad": R.NCDE_SIMPLE_QUAD}
 
 
 @dataclass
@@ -36,7 +37,7 @@ class Case:
 
     @property
     def d(self):
-        return 2 if self.lattice == "D2Q9" else 3
+        return 2 if self.lattice in ("D2Q9", "D2Q5") else 3
 
     @property
     def field_shape(self):

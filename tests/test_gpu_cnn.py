@@ -1,5 +1,6 @@
 """Warm-start network kernels (rmrtlb_cnn.h) against the FP64 oracle of
-oracle/cnn.py on the same BF16-rounded inputs.  Tolerances: FP32
+oracle/cnn.py on the same BF16-rounded inputs (the tensor-core kernels take
+BF16 operands: x, w, and dy rounded to nearest even).  Tolerances: FP32
 accumulation of up to 864 products, normwise 1e-5; BF16 outputs within one
 BF16 rounding (2^-8 relative) of the oracle; encodings bit-exact."""
 import numpy as np
@@ -55,7 +56,7 @@ def test_conv_forward(cin, cout, silu):
     bt = dev(b, torch.float32)
     B.rmrtlb_conv3d_forward(n, d, h, w, cin, cout, xg.data_ptr(), wg.data_ptr(), bt.data_ptr(),
                             silu, z.data_ptr(), a.data_ptr())
-    torch.cuda.synchronize()
+    B.rmrtlb_cnn_check()
     zo = C.conv3d(x, wv, b.astype(np.float64))
     assert normwise(host(z), zo) <= 1e-5
     ao = C.silu(zo) if silu else zo
@@ -77,8 +78,9 @@ def test_conv_backward_data(cin, cout, with_z):
     dyt = dev(dy, torch.float32)
     B.rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dyt.data_ptr(), wg.data_ptr(),
                                   zt.data_ptr() if with_z else None, dx.data_ptr())
-    torch.cuda.synchronize()
-    ref = C.conv3d_backward_data(dy.astype(np.float64), wv)
+    B.rmrtlb_cnn_check()
+    dyb = torch.tensor(dy).to(torch.bfloat16).to(torch.float64).numpy()   # the tensor cores take BF16
+    ref = C.conv3d_backward_data(dyb, wv)
     if with_z:
         ref = ref * C.silu_grad(zin.astype(np.float64))
     assert normwise(host(dx), ref) <= 1e-5

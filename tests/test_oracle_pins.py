@@ -626,13 +626,13 @@ def test_poiseuille_profile():
     assert np.max(np.abs(ux - want)) / want.max() < 0.01
 
 
-def hill_error(n_scale, kind=R.NCDE_LINEAR):
+def hill_error(n_scale, kind=R.NCDE_LINEAR, lattice="D2Q9"):
     """Relative L2 error of the advected-diffusing Gaussian hill at t = T."""
     nx, ny = 32 * n_scale, 40 * n_scale
     L = (32.0, 24.0)
     dx = (L[0] / nx, L[1] / ny)
     dt = 1.0 / (n_scale * n_scale)
-    lat = R.make_lattice("D2Q9", dx, dt)
+    lat = R.make_lattice(lattice, dx, dt)
     D = 0.05
     tau = D / (lat.cs2 * dt) + 0.5
     s1 = 1 / tau
@@ -886,3 +886,114 @@ def test_local_stress_taylor_green():
     assert np.abs(strain[0, 0] - gxx).max() < 0.01 * np.abs(gxx).max()
     assert np.abs(strain[1, 1] + gxx).max() < 0.01 * np.abs(gxx).max()
     assert np.abs(strain[0, 1] - gxy).max() < 0.01 * np.abs(gxy).max()
+
+
+# ---------------------------------------------------------------- rD2Q5 / rD3Q7, Eq. (4-16)
+@pytest.mark.parametrize("name,dx", [("D2Q5", (1.0, 1.0)), ("D2Q5", (1.0, 0.6)), ("D3Q7", (1.0, 1.0, 1.0)),
+                                     ("D3Q7", (1.0, 0.8, 0.5))])
+def test_axis_lattice_weights(name, dx):
+    """Remark I of Sec. III: omega_alpha = c_s^2 / (2 c_alpha^2); the standard
+    D2Q5 (c_s^2 = 1/3: 1/3, 1/6) and D3Q7 (c_s^2 = 1/4: 1/4, 1/8) weights;
+    sum omega = 1, first moments 0 and second moments c_s^2 I, so the
+    linear EDF g^eq(phi, B, 0) has moments (phi, B, c_s^2 phi I)."""
+    lat = R.make_lattice(name, dx)
+    if dx == (1.0,) * lat.d:
+        want = [1 / 3, 1 / 6] if name == "D2Q5" else [1 / 4, 1 / 8]
+        np.testing.assert_allclose(lat.w, [want[0]] + [want[1]] * (lat.q - 1), rtol=1e-15)
+    assert abs(lat.w.sum() - 1) < 1e-15
+    np.testing.assert_allclose(lat.cv.T @ lat.w, 0, atol=1e-16)
+    np.testing.assert_allclose(np.einsum("j,ja,jb->ab", lat.w, lat.cv, lat.cv), lat.cs2 * np.eye(lat.d), atol=1e-15)
+    phi = np.array([0.7, 1.3])
+    B = np.array([[0.01, -0.02, 0.03][: lat.d], [0.0, 0.05, -0.01][: lat.d]])
+    g = R.geq(lat, phi, B, np.zeros((2, lat.d, lat.d)))
+    M = R.moment_matrix(lat)
+    mom = M @ g
+    mons = R.monomials(name)
+    for k, a in enumerate(mons):
+        o = sum(a)
+        if o == 0:
+            want = phi
+        elif o == 1:
+            want = B[:, int(np.argmax(a))]
+        else:
+            want = lat.cs2 * phi
+        np.testing.assert_allclose(mom[k], want, atol=1e-15)
+
+
+def test_simple_ncde_bgk_reduction():
+    """Standard D2Q5, no advection, every rate 1/tau: the simplified NCDE
+    collision (Eq. 4-16) is the textbook BGK diffusion step
+    f* = f - (f - omega phi) / tau."""
+    lat = R.make_lattice("D2Q5", (1.0, 1.0))
+    tau = 0.8
+    s = 1 / tau
+    S = R.relaxation_matrix(lat, R.Rates(s, np.full(2, s), np.full(2, s), np.full(2, s), np.full((2, 2), s), s))
+    f = W.random_populations(5, (20,), seed=21)
+    m = R.Model(R.NCDE_SIMPLE_LINEAR, adv=(0.0, 0.0))
+    phi = f.sum(0)
+    want = f - (f - lat.w[:, None] * phi[None, :]) / tau
+    np.testing.assert_allclose(R.collide(lat, m, S, f), want, atol=1e-15)
+
+
+@pytest.mark.parametrize("name,dx", [("D2Q5", (1.0, 0.6)), ("D3Q7", (1.0, 0.8, 0.5)), ("D2Q9", (1.0, 0.6))])
+@pytest.mark.parametrize("kind", [R.NCDE_SIMPLE_LINEAR, R.NCDE_SIMPLE_QUAD])
+def test_simple_ncde_conserves_phi(name, dx, kind):
+    """phi is a collision invariant up to the source (Eq. 4-18-1 for the
+    NCDE: sum f* = sum f + dt S) whatever dB/dt is; on a periodic grid the
+    total is conserved over steps without a source."""
+    lat = R.make_lattice(name, dx)
+    r = R.Rates(1.0, np.full(lat.d, 1.4), np.full(lat.d, 1.1), np.full(lat.d, 1.1),
+                np.full((lat.d, lat.d), 1.1), 1.1)
+    S = R.relaxation_matrix(lat, r)
+    f = W.random_populations(lat.q, (25,), seed=22)
+    m = R.Model(kind, adv=(0.05, 0.02, -0.01), source=2e-5)
+    dB = np.random.default_rng(3).normal(scale=1e-3, size=(25, lat.d))
+    np.testing.assert_allclose(R.collide(lat, m, S, f, dB).sum(0), f.sum(0) + 2e-5, atol=5e-15)
+    m = R.Model(kind, adv=(0.05, 0.02, -0.01))
+    shp = (4, 5, 6) if lat.d == 3 else (1, 5, 6)
+    g = W.random_populations(lat.q, shp, seed=23)
+    g2 = R.step(lat, m, S, g, 10)
+    assert abs(g2.sum() - g.sum()) < 1e-12 * g.sum()
+
+
+def simple_hill_error(n_scale, lattice, adv, with_dB=True):
+    nx, ny = 32 * n_scale, 40 * n_scale
+    L = (32.0, 24.0)
+    dx = (L[0] / nx, L[1] / ny)
+    dt = 1.0 / (n_scale * n_scale)
+    lat = R.make_lattice(lattice, dx, dt)
+    D = 0.05
+    tau = D / (lat.cs2 * dt) + 0.5
+    rr = R.Rates(1.0, np.full(2, 1 / tau), np.full(2, 1.1), np.full(2, 1.1), np.full((2, 2), 1.1), 1.1)
+    S = R.relaxation_matrix(lat, rr)
+    m = R.Model(R.NCDE_SIMPLE_LINEAR, adv=adv)
+    phi0 = W.gaussian_hill((1, ny, nx), dx, 3.0, peak=1.0, adv=adv, diff=D, t=0.0)
+    f = R.init_equilibrium(lat, m, S, phi0, np.zeros((2, 1, ny, nx)))
+    n = int(round(40.0 / dt))
+    if with_dB:
+        f = R.step(lat, m, S, f, n)
+    else:                       # a planted mistake: dB/dt dropped (fresh state every step)
+        for _ in range(n):
+            f = R.step(lat, m, S, f, 1)
+    phi = R.fields(lat, m, f)[0]
+    ref = W.gaussian_hill((1, ny, nx), dx, 3.0, peak=1.0, adv=adv, diff=D, t=40.0)
+    return np.sqrt(((phi - ref) ** 2).sum() / (ref ** 2).sum())
+
+
+def test_simple_ncde_hill_second_order_on_rd2q5():
+    """The simplified NCDE (Eq. 4-16) on the rectangular rD2Q5 lattice
+    follows the closed-form advected, diffusing Gaussian hill at second
+    order under diffusive refinement."""
+    e1 = simple_hill_error(1, "D2Q5", (0.05, 0.02))
+    e2 = simple_hill_error(2, "D2Q5", (0.05, 0.02))
+    assert e1 < 1e-2
+    assert np.log2(e1 / e2) > 1.8
+
+
+def test_simple_ncde_needs_the_dBdt_term():
+    """With faster advection the G = (I - S_1/2) dB/dt term of Eq. (4-16)
+    carries the correction: dropping it makes the hill error several times
+    larger."""
+    e = simple_hill_error(1, "D2Q5", (0.2, 0.1))
+    e_no = simple_hill_error(1, "D2Q5", (0.2, 0.1), with_dB=False)
+    assert e < 0.02 and e < 0.4 * e_no, (e, e_no)
