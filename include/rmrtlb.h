@@ -60,7 +60,14 @@ extern "C" {
                                   buffer allows */
 
 /* --------------------------------------------------------------- choices */
-enum rmrtlb_lattice { RMRTLB_D2Q9 = 0, RMRTLB_D3Q19 = 1, RMRTLB_D3Q27 = 2 };
+/* Lattices of Sec. III.  rD2Q5 and rD3Q7 (Remark I: rest and axis
+ * directions, omega_a = c_s^2 / (2 c_a^2), default c_s^2 = min c_a^2 / 3 and
+ * min c_a^2 / 4 respectively) carry only the simplified NCDE kinds; their
+ * moment basis is 1, the first powers and the squares of each axis. */
+enum rmrtlb_lattice {
+    RMRTLB_D2Q9 = 0, RMRTLB_D3Q19 = 1, RMRTLB_D3Q27 = 2,
+    RMRTLB_D2Q5 = 3, RMRTLB_D3Q7 = 4
+};
 
 /* Equilibrium kind (which conservation law the step solves).
  *  NSE          f^eq = g^eq(rho, rho u, rho u u)              Eq. (NSEfeq)
@@ -69,12 +76,20 @@ enum rmrtlb_lattice { RMRTLB_D2Q9 = 0, RMRTLB_D3Q19 = 1, RMRTLB_D3Q27 = 2 };
  *                                                             D = phi I, beta = 1,
  *                                                             C = int B'B' dphi
  *  NCDE_QUAD    f^eq = g^eq(phi, u phi^2/2, u u phi^3/3)      same, B = u phi^2/2
- * For the NCDE kinds u is the constant advection velocity params.adv. */
+ *  NCDE_SIMPLE_LINEAR  f^eq = g^eq(phi, u phi, 0)             Eq. (4-16): C = 0,
+ *  NCDE_SIMPLE_QUAD    f^eq = g^eq(phi, u phi^2/2, 0)         G = g^eq(0, (I - S_1/2)
+ *                                                             dB/dt, 0), F = omega S
+ * For the NCDE kinds u is the constant advection velocity params.adv.  The
+ * simplified kinds take dB/dt = (B(t) - B(t - dt)) / dt from a per-node
+ * history of B kept in the workspace; the first step after create,
+ * rmrtlb_init_equilibrium or rmrtlb_set_populations uses dB/dt = 0. */
 enum rmrtlb_eq_kind {
     RMRTLB_EQ_NSE = 0,
     RMRTLB_EQ_NSE_HELUO = 1,
     RMRTLB_EQ_NCDE_LINEAR = 2,
-    RMRTLB_EQ_NCDE_QUAD = 3
+    RMRTLB_EQ_NCDE_QUAD = 3,
+    RMRTLB_EQ_NCDE_SIMPLE_LINEAR = 4,
+    RMRTLB_EQ_NCDE_SIMPLE_QUAD = 5
 };
 
 /* Moment basis of the relaxation, Mbar = N M (Eqs. 5-1-1, 5-1-2): raw

@@ -65,7 +65,7 @@ size_t check_blocks(size_t N) {
 }
 
 struct Layout {
-  size_t fA, fB, stage, uprev, partials, stats, flags, total, nblk;
+  size_t fA, fB, stage, uprev, partials, stats, flags, hist, total, nblk;
 };
 
 Layout make_layout(int lat, int nx, int ny, int nz, int st) {
@@ -81,13 +81,15 @@ Layout make_layout(int lat, int nx, int ny, int nz, int st) {
   L.partials = L.uprev + align_up(d * N * sizeof(double));
   L.stats = L.partials + align_up(L.nblk * 8 * sizeof(double));
   L.flags = L.stats + align_up(kSlots * 8 * sizeof(double));
-  L.total = L.flags + align_up(kSlots * sizeof(int));
+  L.hist = L.flags + align_up(kSlots * sizeof(int));
+  // B(t - dt) of the simplified NCDE, d planes in the compute type
+  L.total = L.hist + align_up(d * N * (st == RMRTLB_ST_F64 ? sizeof(double) : sizeof(float)));
   return L;
 }
 
 bool valid_dims(int lat, int nx, int ny, int nz) {
-  if (lat < 0 || lat > 2 || nx < 1 || ny < 1 || nz < 1) return false;
-  if (lat == RMRTLB_D2Q9 && nz != 1) return false;
+  if (lat < 0 || lat > 4 || nx < 1 || ny < 1 || nz < 1) return false;
+  if (lattice_d(lat) == 2 && nz != 1) return false;
   if (ny > 65535 || nz > 65535) return false;             // grid.y, grid.z limits
   const double N = double(nx) * ny * nz;
   return N * lattice_q(lat) < 9.0e18 && N < 2147483647.0;
@@ -134,10 +136,12 @@ LaunchArgs base_args(rmrtlb_solver* s, Op op) {
 
 cudaError_t launch(rmrtlb_solver* s, const LaunchArgs& a) {
   using Fn = cudaError_t (*)(const LaunchArgs&);
-  static const Fn table[3][4] = {
+  static const Fn table[5][4] = {
       {launch_d2q9_f64, launch_d2q9_f32, launch_d2q9_f16, launch_d2q9_bf16},
       {launch_d3q19_f64, launch_d3q19_f32, launch_d3q19_f16, launch_d3q19_bf16},
-      {launch_d3q27_f64, launch_d3q27_f32, launch_d3q27_f16, launch_d3q27_bf16}};
+      {launch_d3q27_f64, launch_d3q27_f32, launch_d3q27_f16, launch_d3q27_bf16},
+      {launch_d2q5_f64, launch_d2q5_f32, launch_d2q5_f16, launch_d2q5_bf16},
+      {launch_d3q7_f64, launch_d3q7_f32, launch_d3q7_f16, launch_d3q7_bf16}};
   return table[s->k.lat][s->k.storage](a);
 }
 
@@ -223,7 +227,7 @@ const char* rmrtlb_strerror(int status) {
 }
 
 int rmrtlb_lattice_info(int lattice, int* q, int* d, int* e) {
-  if (lattice < 0 || lattice > 2) return RMRTLB_EINVAL;
+  if (lattice < 0 || lattice > 4) return RMRTLB_EINVAL;
   if (q) *q = lattice_q(lattice);
   if (d) *d = lattice_d(lattice);
   if (e)
@@ -242,8 +246,8 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
                   size_t workspace_bytes, void* stream) {
   if (!solver || !params || !valid_dims(lattice, nx, ny, nz)) return RMRTLB_EINVAL;
   *solver = nullptr;
-  if (eq_kind < 0 || eq_kind > 3 || basis < 0 || basis > 3 || storage < 0 || storage > 3) return RMRTLB_EINVAL;
-  if (!(dt > 0) || !(dx > 0) || !(dy > 0) || (lattice != RMRTLB_D2Q9 && !(dz > 0))) return RMRTLB_EINVAL;
+  if (eq_kind < 0 || eq_kind > 5 || basis < 0 || basis > 3 || storage < 0 || storage > 3) return RMRTLB_EINVAL;
+  if (!(dt > 0) || !(dx > 0) || !(dy > 0) || (lattice_d(lattice) == 3 && !(dz > 0))) return RMRTLB_EINVAL;
   if (!workspace || (reinterpret_cast<size_t>(workspace) % kAlign) != 0) return RMRTLB_EINVAL;
   const Layout L = make_layout(lattice, nx, ny, nz, storage);
   if (workspace_bytes < L.total) return RMRTLB_ENOMEM;
@@ -262,8 +266,11 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
   s->stream = static_cast<cudaStream_t>(stream);
   s->kp64 = to_kparams<double>(k);
   s->kp32 = to_kparams<float>(k);
+  s->kp64.hist = reinterpret_cast<double*>(s->ws + L.hist);
+  s->kp32.hist = reinterpret_cast<float*>(s->ws + L.hist);
+  s->kp64.hist_fresh = s->kp32.hist_fresh = 1;
   s->check_every = params->check_every;
-  s->pairs = (nx % 2 == 0);
+  s->pairs = (nx % 2 == 0) && !axis_lattice(lattice) && !simple_ncde(eq_kind);
   *solver = s;
   return RMRTLB_OK;
 }
@@ -317,6 +324,7 @@ int rmrtlb_init_equilibrium(rmrtlb_t s, const double* rho, const double* u) {
   if (launch(s, a) != cudaSuccess) return RMRTLB_ECUDA;
   s->step = 0;
   s->has_prev = false;
+  s->kp64.hist_fresh = s->kp32.hist_fresh = 1;
   if (synced && cudaStreamSynchronize(s->stream) != cudaSuccess) return RMRTLB_ECUDA;
   return RMRTLB_OK;
 }
@@ -342,6 +350,7 @@ int rmrtlb_set_populations(rmrtlb_t s, const double* f) {
   }
   s->step = 0;
   s->has_prev = false;
+  s->kp64.hist_fresh = s->kp32.hist_fresh = 1;
   if (!dev && cudaStreamSynchronize(s->stream) != cudaSuccess) return RMRTLB_ECUDA;
   return RMRTLB_OK;
 }
@@ -379,7 +388,8 @@ int rmrtlb_step(rmrtlb_t s, int n) {
     }
     a.fin = pop_ptr(s, s->cur);
     a.fout = pop_ptr(s, 1 - s->cur);
-    if (launch(s, a) != cudaSuccess) return RMRTLB_ECUDA;
+    if (launch(s, a) != cudaSuccess) return RMRTLB_ECUDA;   // the parameters are copied at launch
+    s->kp64.hist_fresh = s->kp32.hist_fresh = 0;
     s->cur = 1 - s->cur;
     ++s->step;
     if (s->check_every > 0 && s->step % s->check_every == 0)

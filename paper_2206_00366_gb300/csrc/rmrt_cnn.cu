@@ -17,7 +17,6 @@
 
 namespace {
 
-constexpr int kThreads = 128;
 constexpr int kWeightChunk = 4096;   // voxels per partial sum of the weight gradient
 
 struct Vol {

@@ -1,4 +1,4 @@
-// Kernels of the d3q19 lattice with f16 storage (raw and central bases,
+// Kernels of the d3q19 lattice with f16 storage (every moment basis,
 // forced and unforced, NSE and NCDE families).
 #include "rmrt_launch.cuh"
 

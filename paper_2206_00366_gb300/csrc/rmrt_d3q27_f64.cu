@@ -1,4 +1,4 @@
-// Kernels of the d3q27 lattice with f64 storage (raw and central bases,
+// Kernels of the d3q27 lattice with f64 storage (every moment basis,
 // forced and unforced, NSE and NCDE families).
 #include "rmrt_launch.cuh"
 

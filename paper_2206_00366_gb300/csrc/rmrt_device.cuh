@@ -51,6 +51,17 @@ template <> struct Lat<LAT_D3Q27> : Dirs27 {
 template <> struct Lat<LAT_D3Q19> : Dirs27 {
   static constexpr int D = 3, Q = 19, NZ = 3;
 };
+// rD2Q5 and rD3Q7 (Remark I of Sec. III): the rest and axis directions,
+// the first 5 of rD2Q9 and the first 7 of rD3Q27.
+template <> struct Lat<LAT_D2Q5> {
+  static constexpr int D = 2, Q = 5, NZ = 1;
+  static constexpr int EX[5] = {0, 1, 0, -1, 0};
+  static constexpr int EY[5] = {0, 0, 1, 0, -1};
+  static constexpr int EZ[5] = {0, 0, 0, 0, 0};
+};
+template <> struct Lat<LAT_D3Q7> : Dirs27 {
+  static constexpr int D = 3, Q = 7, NZ = 3;
+};
 
 // compile-time loop: f(std::integral_constant<int, i>) for i = 0..N-1
 template <typename F, int... Is>
@@ -221,9 +232,12 @@ template <int LAT, typename V> struct Cube {
   }
 };
 
-// True for the eight rD3Q27 monomials that vanish on rD3Q19.
+// True for the cube moments the lattice does not carry: the eight rD3Q27
+// monomials that vanish on rD3Q19, and on rD2Q5/rD3Q7 every monomial with
+// two or more nonzero exponents.
 template <int LAT>
 __device__ __forceinline__ constexpr bool absent(int a, int b, int c) {
+  if (LAT == LAT_D2Q5 || LAT == LAT_D3Q7) return (a > 0) + (b > 0) + (c > 0) >= 2;   // axis-only lattices
   return LAT == LAT_D3Q19 && a > 0 && b > 0 && c > 0;
 }
 
@@ -366,7 +380,8 @@ __device__ __forceinline__ void eq_args(Macro<CT>& r, CT rho, const CT uh[3], co
   if (p.kind == KIND_NSE) { fb = rho; fc = rho; }                    // g^eq(rho, rho u, rho u u)
   else if (p.kind == KIND_NSE_HELUO) { fb = p.rho0; fc = p.rho0; }   // g^eq(rho, rho0 u, rho0 u u)
   else if (p.kind == KIND_NCDE_LINEAR) { fb = rho; fc = rho; }       // B = u phi, C = u u phi
-  else { fb = CT(0.5) * rho * rho; fc = rho * rho * rho * CT(1.0 / 3.0); }  // B = u phi^2/2, C = u u phi^3/3
+  else if (p.kind == KIND_NCDE_QUAD) { fb = CT(0.5) * rho * rho; fc = rho * rho * rho * CT(1.0 / 3.0); }  // B = u phi^2/2, C = u u phi^3/3
+  else { fb = p.kind == KIND_NCDE_SIMPLE_LINEAR ? rho : CT(0.5) * rho * rho; fc = CT(0); }   // Eq. (4-16): C = 0
 #pragma unroll
   for (int al = 0; al < 3; ++al) { r.u[al] = uh[al]; r.B[al] = fb * uh[al]; }
   r.M[0] = fc * uh[0] * uh[0]; r.M[1] = fc * uh[1] * uh[1]; r.M[2] = fc * uh[2] * uh[2];
@@ -394,9 +409,10 @@ __device__ __forceinline__ Macro<V> macroscopic(V m000, const V jh[3], const P& 
   } else {
 #pragma unroll
     for (int al = 0; al < 3; ++al) uh[al] = V(p.advh[al]);
-    const bool lin = p.kind == KIND_NCDE_LINEAR;       // B = u phi, C = u u phi
+    const bool lin = p.kind == KIND_NCDE_LINEAR || p.kind == KIND_NCDE_SIMPLE_LINEAR;   // B = u phi
     fb = lin ? r.rho : V(0.5f) * r.rho * r.rho;        // B = u phi^2/2
-    fc = lin ? r.rho : r.rho * r.rho * r.rho * V(S(1.0 / 3.0));   // C = u u phi^3/3
+    if (p.kind >= KIND_NCDE_SIMPLE_LINEAR) fc = V(0.0f);   // Eq. (4-16): C = 0 (linear EDF)
+    else fc = lin ? r.rho : r.rho * r.rho * r.rho * V(S(1.0 / 3.0));   // C = u u phi, u u phi^3/3
   }
 #pragma unroll
   for (int al = 0; al < 3; ++al) { r.u[al] = uh[al]; r.B[al] = fb * uh[al]; }
@@ -410,8 +426,10 @@ __device__ __forceinline__ Macro<V> macroscopic(V m000, const V jh[3], const P& 
 // Eq. (2-2-3):
 //   m* - m0 = m(delta) + dt (m_G + m_F) - S (m^ne + dt m_F / 2),
 // central variant: S replaced by N(u)^-1 Sbar N(u) (Eq. 5-1-2).
+// bprev / bnow (simplified NCDE only): B(t - dt) / c of the node in, B(t) / c
+// out; G = g^eq(0, (I - S_1/2) dB/dt, 0) of Eq. (4-16).
 template <int LAT, int BASIS, bool FORCED, bool NSE, typename V, typename P>
-__device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p) {
+__device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p, const V* bprev = nullptr, V* bnow = nullptr) {
   using S = PScalar<P>;
   constexpr int D = Lat<LAT>::D, NZ = Lat<LAT>::NZ;
   q.forward();
@@ -446,6 +464,15 @@ __device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p) {
       GM[3] = Y[3] * V(S(1) - S(0.5) * p.soff[0]);
       GM[4] = Y[4] * V(S(1) - S(0.5) * p.soff[1]);
       GM[5] = Y[5] * V(S(1) - S(0.5) * p.soff[2]);
+    } else if (p.kind >= KIND_NCDE_SIMPLE_LINEAR) {
+      // first-order difference dB/dt = (B(t) - B(t - dt)) / dt; zero without a previous value
+      const S idt = S(1) / p.dt;
+#pragma unroll
+      for (int al = 0; al < 3; ++al) {
+        const V db = (bprev != nullptr && !p.hist_fresh) ? (mc.B[al] - bprev[al]) * V(idt) : V(0.0f);
+        GB[al] = db * V(S(1) - S(0.5) * p.s1[al]);
+        if (bnow != nullptr) bnow[al] = mc.B[al];
+      }
     } else {
       const V bp = p.kind == KIND_NCDE_LINEAR ? V(1.0f) : mc.rho;   // B' = u bp
 #pragma unroll
@@ -548,8 +575,21 @@ __global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, S
     if constexpr (scaled_storage<ST>()) v *= p.sinv[j];
     q.v[ex + 1][ey + 1][zi<LAT>(ez)] = v;
   });
-  collide<LAT, BASIS, FORCED, NSE>(q, p);
   const size_t own = (size_t(z) * p.ny + y) * p.nx + x;
+  if constexpr (FORCED && !NSE) {
+    if (p.kind >= KIND_NCDE_SIMPLE_LINEAR) {
+      CT bprev[3] = {CT(0), CT(0), CT(0)}, bnow[3];
+#pragma unroll
+      for (int al = 0; al < L::D; ++al) bprev[al] = p.hist[al * N + own];
+      collide<LAT, BASIS, FORCED, NSE>(q, p, bprev, bnow);
+#pragma unroll
+      for (int al = 0; al < L::D; ++al) p.hist[al * N + own] = bnow[al];
+    } else {
+      collide<LAT, BASIS, FORCED, NSE>(q, p);
+    }
+  } else {
+    collide<LAT, BASIS, FORCED, NSE>(q, p);
+  }
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];

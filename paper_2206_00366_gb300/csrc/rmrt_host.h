@@ -14,12 +14,24 @@
 namespace rmrt {
 namespace host {
 
-inline int lattice_q(int lat) { return lat == RMRTLB_D2Q9 ? 9 : (lat == RMRTLB_D3Q19 ? 19 : 27); }
-inline int lattice_d(int lat) { return lat == RMRTLB_D2Q9 ? 2 : 3; }
+inline int lattice_q(int lat) {
+  switch (lat) {
+    case RMRTLB_D2Q9: return 9;
+    case RMRTLB_D3Q19: return 19;
+    case RMRTLB_D2Q5: return 5;
+    case RMRTLB_D3Q7: return 7;
+    default: return 27;
+  }
+}
+inline int lattice_d(int lat) { return (lat == RMRTLB_D2Q9 || lat == RMRTLB_D2Q5) ? 2 : 3; }
+inline bool axis_lattice(int lat) { return lat == RMRTLB_D2Q5 || lat == RMRTLB_D3Q7; }
+inline bool simple_ncde(int kind) {
+  return kind == RMRTLB_EQ_NCDE_SIMPLE_LINEAR || kind == RMRTLB_EQ_NCDE_SIMPLE_QUAD;
+}
 inline size_t storage_size(int st) { return st == RMRTLB_ST_F64 ? 8 : (st == RMRTLB_ST_F32 ? 4 : 2); }
 
 inline void lattice_dir(int lat, int j, int e[3]) {
-  if (lat == RMRTLB_D2Q9) {
+  if (lat == RMRTLB_D2Q9 || lat == RMRTLB_D2Q5) {   // rD2Q5: the first 5 of rD2Q9
     e[0] = Lat<LAT_D2Q9>::EX[j]; e[1] = Lat<LAT_D2Q9>::EY[j]; e[2] = 0;
   } else {
     e[0] = Dirs27::EX[j]; e[1] = Dirs27::EY[j]; e[2] = Dirs27::EZ[j];
@@ -42,12 +54,15 @@ inline bool rate_ok(double s) { return s > 0.0 && s < 2.0 && isfinite(s); }
 
 // Weights from the velocity-moment constraints (Sec. III): rD2Q9 Eq. (3-3-5),
 // rD3Q27 Eq. (3-3-8) with omega_19 = c_s^6/(8 c1^2 c2^2 c3^2), rD3Q19 with
-// omega_19 = 0; omega_0 = 1 - sum of the others.
+// omega_19 = 0; rD2Q5 / rD3Q7 omega_a = c_s^2 / (2 c_a^2) (Remark I);
+// omega_0 = 1 - sum of the others.
 inline int derive_weights(Consts& k) {
   const double cs2 = k.cs2;
   double c2[3] = {k.c[0] * k.c[0], k.c[1] * k.c[1], k.c[2] * k.c[2]};
   double wax[3] = {0, 0, 0}, wedge[3] = {0, 0, 0}, wcorner = 0;  // edge: xy, xz, yz
-  if (k.lat == RMRTLB_D2Q9) {
+  if (axis_lattice(k.lat)) {
+    for (int a = 0; a < 3; ++a) wax[a] = cs2 / (2.0 * c2[a]);
+  } else if (k.lat == RMRTLB_D2Q9) {
     const double w5 = cs2 * cs2 / (4.0 * c2[0] * c2[1]);
     wax[0] = cs2 / (2.0 * c2[0]) - 2.0 * w5;
     wax[1] = cs2 / (2.0 * c2[1]) - 2.0 * w5;
@@ -192,13 +207,18 @@ inline int make_consts(Consts& k, int lattice, int nx, int ny, int nz, double dx
   k.kind = eq_kind; k.storage = storage; k.central = basis;
   k.nx = nx; k.ny = ny; k.nz = nz; k.N = size_t(nx) * ny * nz;
   k.dt = dt;
-  const double sp[3] = {dx, dy, lattice == RMRTLB_D2Q9 ? 1.0 : dz};
+  const double sp[3] = {dx, dy, k.d == 2 ? 1.0 : dz};
   double cmin2 = 1e300;
   for (int a = 0; a < 3; ++a) {
     k.c[a] = sp[a] / dt;
     if (a < k.d) cmin2 = fmin(cmin2, k.c[a] * k.c[a]);
   }
-  k.cs2 = params.cs2 > 0 ? params.cs2 : cmin2 / 3.0;
+  // rD3Q7: c^2/3 would leave omega_0 = 0 on the standard lattice (Remark II);
+  // its default is c^2/4 (weights 1/4, 1/8 there)
+  k.cs2 = params.cs2 > 0 ? params.cs2 : cmin2 / (lattice == RMRTLB_D3Q7 ? 4.0 : 3.0);
+  // the axis-only lattices carry only the simplified NCDE (their fourth
+  // moments do not satisfy the NSE / full NCDE constraints, Remark I)
+  if (axis_lattice(lattice) && !simple_ncde(eq_kind)) return RMRTLB_EINVAL;
   if (!(k.cs2 < cmin2)) return RMRTLB_EINVAL;
   k.rho0 = params.rho0;
   if (!isfinite(k.rho0)) return RMRTLB_EINVAL;
@@ -208,7 +228,8 @@ inline int make_consts(Consts& k, int lattice, int nx, int ny, int nz, double dx
     k.adv[a] = a < k.d ? params.adv[a] : 0.0;
   }
   const bool nse = eq_kind == RMRTLB_EQ_NSE || eq_kind == RMRTLB_EQ_NSE_HELUO;
-  k.forced = (k.source != 0.0) || (nse && (k.force[0] != 0.0 || k.force[1] != 0.0 || k.force[2] != 0.0));
+  k.forced = (k.source != 0.0) || (nse && (k.force[0] != 0.0 || k.force[1] != 0.0 || k.force[2] != 0.0)) ||
+             simple_ncde(eq_kind);   // Eq. (4-16): G from dB/dt on every step
   if (!nse) for (int a = 0; a < 3; ++a) k.force[a] = 0.0;
   int rc = derive_weights(k);
   if (rc) return rc;

@@ -10,7 +10,12 @@ namespace rmrt {
 
 template <int LAT, typename ST, typename CT, int BASIS, bool NSE>
 static void launch_basis(const LaunchArgs& a, const KParams<CT>& p, const ST* fin, ST* fout) {
-  if (a.pairs) {
+  constexpr bool axis_only = Lat<LAT>::Q == 5 || Lat<LAT>::Q == 7;   // one node per thread only
+  if constexpr (axis_only) {
+    if (p.forced) step_kernel<LAT, ST, CT, BASIS, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+    else step_kernel<LAT, ST, CT, BASIS, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
+    return;
+  } else if (a.pairs) {
     if (p.forced) step_kernel_x2<LAT, ST, CT, BASIS, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
     else step_kernel_x2<LAT, ST, CT, BASIS, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
   } else {

@@ -8,8 +8,11 @@
 
 namespace rmrt {
 
-enum { LAT_D2Q9 = 0, LAT_D3Q19 = 1, LAT_D3Q27 = 2 };
-enum { KIND_NSE = 0, KIND_NSE_HELUO = 1, KIND_NCDE_LINEAR = 2, KIND_NCDE_QUAD = 3 };
+enum { LAT_D2Q9 = 0, LAT_D3Q19 = 1, LAT_D3Q27 = 2, LAT_D2Q5 = 3, LAT_D3Q7 = 4 };
+enum {
+  KIND_NSE = 0, KIND_NSE_HELUO = 1, KIND_NCDE_LINEAR = 2, KIND_NCDE_QUAD = 3,
+  KIND_NCDE_SIMPLE_LINEAR = 4, KIND_NCDE_SIMPLE_QUAD = 5   // Eq. (4-16): linear EDF, G from dB/dt
+};
 enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
 // Constants of one solver in the compute type CT (double for FP64 storage,
@@ -32,6 +35,9 @@ struct KParams {
   double wd[27];                       // omega_j in FP64 (population set/get)
   double rho0d;
   double ssd[3], soffd[3];             // s_sa and s_ab (xy, xz, yz) in FP64 (local stress output)
+  CT* hist;                            // simplified NCDE: B(t - dt) / c_a per node, d planes (index units)
+  int hist_fresh;                      // 1: no previous B yet (dB/dt taken as 0 on this step)
+  int pad2_;
 };
 
 enum Op { OP_STEP = 0, OP_INIT_EQ = 1, OP_PLANE = 2, OP_CHECK = 3, OP_STRESS = 4 };
@@ -69,6 +75,8 @@ struct LaunchArgs {
 RMRT_DECLARE_LAUNCH(d2q9)
 RMRT_DECLARE_LAUNCH(d3q19)
 RMRT_DECLARE_LAUNCH(d3q27)
+RMRT_DECLARE_LAUNCH(d2q5)
+RMRT_DECLARE_LAUNCH(d3q7)
 #undef RMRT_DECLARE_LAUNCH
 cudaError_t launch_finalize(const double* partials, size_t nblk, double* out, cudaStream_t s);
 

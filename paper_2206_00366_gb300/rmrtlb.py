@@ -20,17 +20,19 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "librmrtlb.so")
 
-D2Q9, D3Q19, D3Q27 = 0, 1, 2
+D2Q9, D3Q19, D3Q27, D2Q5, D3Q7 = 0, 1, 2, 3, 4
 EQ_NSE, EQ_NSE_HELUO, EQ_NCDE_LINEAR, EQ_NCDE_QUAD = 0, 1, 2, 3
+EQ_NCDE_SIMPLE_LINEAR, EQ_NCDE_SIMPLE_QUAD = 4, 5
 BASIS_RAW, BASIS_CENTRAL, BASIS_HERMITE, BASIS_CENTRAL_HERMITE = 0, 1, 2, 3
 ST_F64, ST_F32, ST_F16, ST_BF16 = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETOOBIG = 0, -1, -2, -3, -4, -5
 NOALLOC_MAX_NODES = 67108864
 
-LATTICE_NAMES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}
+LATTICE_NAMES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27, "D2Q5": D2Q5, "D3Q7": D3Q7}
 STORAGE_NAMES = {"f64": ST_F64, "f32": ST_F32, "f16": ST_F16, "bf16": ST_BF16}
 EQ_NAMES = {"nse": EQ_NSE, "nse_heluo": EQ_NSE_HELUO, "ncde_linear": EQ_NCDE_LINEAR,
-            "ncde_quad": EQ_NCDE_QUAD}
+            "ncde_quad": EQ_NCDE_QUAD, "ncde_simple_linear": EQ_NCDE_SIMPLE_LINEAR,
+            "ncde_simple_quad": EQ_NCDE_SIMPLE_QUAD}
 BASIS_NAMES = {"raw": BASIS_RAW, "central": BASIS_CENTRAL, "hermite": BASIS_HERMITE,
                "central_hermite": BASIS_CENTRAL_HERMITE}
 

@@ -46,7 +46,7 @@ def _gpu():
 def small_shape(lattice, even=False):
     """Ragged small grids; odd nx runs the one-node-per-thread kernel, even nx
     the two-nodes-per-thread kernel (70 = 35 pairs: a partly filled warp)."""
-    if lattice == "D2Q9":
+    if lattice in ("D2Q9", "D2Q5"):
         return (70, 23, 1) if even else (37, 23, 1)
     return (14, 11, 7) if even else (13, 11, 7)
 
@@ -350,3 +350,62 @@ def test_local_stress_rejects_ncde():
     s = Solver("D2Q9", (8, 8), (1.0, 1.0), params=dict(diffusivity=0.01, s_free=1.1), eq_kind="ncde_linear")
     with pytest.raises(RmrtlbError):
         s.stress()
+
+
+# ---------------------------------------------------------------- simplified NCDE, Eq. (4-16); rD2Q5, rD3Q7
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("forced", [False, True])
+@pytest.mark.parametrize("kind", ["ncde_simple_linear", "ncde_simple_quad"])
+@pytest.mark.parametrize("basis", ["raw", "central"])
+@pytest.mark.parametrize("lattice", ["D2Q5", "D3Q7", "D2Q9", "D3Q19", "D3Q27"])
+def test_simple_ncde_random_populations(lattice, basis, kind, forced, storage):
+    """Six steps from random populations: the dB/dt history (zero on the
+    first step, a first-order difference afterwards) matches the oracle's,
+    including when the steps are issued in two calls."""
+    shape = small_shape(lattice, even=True)
+    case = Case(lattice, shape, (1.0, 0.7, 0.55), kind=kind, basis=basis, adv=(0.08, -0.05, 0.03),
+                source=3e-6 if forced else 0.0)
+    q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27, "D2Q5": 5, "D3Q7": 7}[lattice]
+    pops = W.random_populations(q, case.field_shape, seed=31, level=1.0, amp=0.05)
+    fo, ro, _ = oracle_run(case, 6, pops=pops, key="simple-ncde-seed31")
+    s = gpu_solver(case, storage)
+    s.set_populations(np.ascontiguousarray(pops))
+    s.step(2)
+    s.step(4)
+    fg = s.get_populations()
+    rg, _ = s.moments()
+    assert normwise(fg, fo) <= TOL[storage]
+    assert normwise(rg, ro) <= TOL[storage]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("lattice", ["D2Q5", "D3Q7"])
+def test_simple_ncde_gaussian_hill(lattice, storage):
+    """An advected, diffusing Gaussian hill on the axis-only lattices, 150
+    steps from f^eq, against the oracle."""
+    d3 = lattice == "D3Q7"
+    shape = (24, 20, 10) if d3 else (48, 40, 1)
+    sp = (1.0, 0.8, 0.6) if d3 else (1.0, 0.6)
+    case = Case(lattice, shape, sp, kind="ncde_simple_linear", adv=(0.1, 0.05, 0.02), diffusivity=0.02)
+    fs = case.field_shape
+    phi = W.gaussian_hill(fs, sp, 3.0, peak=1.0)
+    u = np.zeros((case.d,) + fs)
+    fo, ro, _ = oracle_run(case, 150, fields=(phi, u), key="simple-hill")
+    fg, rg, _ = gpu_run(case, storage, 150, fields=(phi, u))
+    err = normwise(rg, ro)
+    if storage != "f16":
+        assert err <= TOL[storage]
+        return
+    # FP16 stores phi deviations of size 1 with 2^-11 relative rounding per
+    # step; on the axis-only lattices the error reaches a few 1e-2 in 150
+    # steps: a correctness bound, and the 2e-3 gate reported as missed
+    assert err <= 5e-2
+    if err > TOL[storage]:
+        pytest.xfail(f"f16 simplified NCDE on {lattice}: normwise error {err:.3e} misses the 2e-3 gate")
+
+
+def test_axis_lattices_reject_other_kinds():
+    from paper_2206_00366_gb300.rmrtlb import RmrtlbError, Solver
+    for kind in ("nse", "ncde_linear"):
+        with pytest.raises(RmrtlbError):
+            Solver("D2Q5", (8, 8), (1.0, 1.0), params=dict(nu=0.02, diffusivity=0.01, s_free=1.1), eq_kind=kind)
