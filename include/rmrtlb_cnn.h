@@ -53,9 +53,11 @@ int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout,
 size_t rmrtlb_conv3d_backward_weight_scratch(int n, int d, int h, int w, int cin, int cout);
 
 /* Gradient with respect to the weights and the bias, all three channel
- * pairs: dweight[t, ci, co] = sum_v x[v + tap_t, ci] dy[v, co],
- * dbias[co] = sum_v dy[v, co]; FP32, summed in a fixed order (partial sums
- * per block of 4096 voxels, then over blocks), so repeated calls give
+ * pairs: dweight[t, ci, co] = sum_v x[v + tap_t, ci] dy[v, co] on the tensor
+ * cores (a GEMM with K = voxels, M = taps x cin, both operands staged
+ * MN-major in shared memory; dy rounded to BF16), dbias[co] = sum_v dy[v,
+ * co] on the FP32 pipes; FP32 results summed in a fixed order (partial sums
+ * per chunk of 4096 voxels, then over chunks), so repeated calls give
  * bitwise the same result. */
 int rmrtlb_conv3d_backward_weight(int n, int d, int h, int w, int cin, int cout,
                                   const uint16_t* x, const float* dy, float* dweight, float* dbias,

