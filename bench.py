@@ -188,6 +188,24 @@ def time_solver(solver, steps, warmup):
     return ev[0].elapsed_time(ev[steps]), statistics.mean(durs)
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest x over the ranks of the initialised process group (x
+    itself on one rank): the timing rule of a replicated run."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(world: int, nodes: int, steps: int, seconds: float) -> float:
+    """Whole-job MLUPS of `world` replicas that each advanced `nodes` nodes
+    `steps` times, timed by the slowest rank."""
+    return world * nodes * steps / seconds / 1e6
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -233,13 +251,10 @@ def run_ours(args):
     durs = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     plain = [d for i, d in enumerate(durs) if (args.warmup + i + 1) % CHECK_EVERY != 0]
     kern_ms = statistics.mean(plain) if plain else total_ms / args.steps
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, "cuda")
     chk = solver.last_check()
     ms_per_step = total_ms / args.steps
-    mlups = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
+    mlups = replica_mlups(world, nodes, args.steps, total_ms * 1e-3)
 
     # end to end through the C ABI with pinned host buffers
     rho_h = torch.from_numpy(rho).pin_memory()
@@ -259,12 +274,9 @@ def run_ours(args):
     e2e_solver.moments(rho_o, u_o)                     # device -> host inside the call
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, "cuda")
     d = 2 if wl["lattice"] == "D2Q9" else 3
-    e2e = {"value": world * nodes * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": replica_mlups(world, nodes, args.steps, e2e_s), "unit": "MLUPS",
            "h2d_bytes_per_step": (1 + d) * nodes * 8 / args.steps,
            "d2h_bytes_per_step": (1 + d) * nodes * 8 / args.steps,
            "note": "init_equilibrium from pinned host rho,u + K steps + moments to pinned host"}
