@@ -503,6 +503,10 @@ def run_only(args):
     import torch
     from paper_2206_00366_gb300 import build as _build
     _build.build()
+    if args.only == "batched-cavities":
+        return run_only_batched(args)
+    if args.only == "warmstart-train-step":
+        return run_only_train_step(args)
     table = {"rD2Q9-f32": ("D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "f32", "raw", "nse")}
     table.update({v[0]: v[1:] for v in VARIANTS})
     lat, shape, sp, st, basis, kind = table[args.only]
@@ -515,6 +519,53 @@ def run_only(args):
     print(json.dumps({"only": args.only, "steps": args.steps, "mlups": round(n * args.steps / (tot * 1e-3) / 1e6, 1),
                       "kernel_ms": round(km, 5), "achieved_gbs": round(b / (km * 1e-3) / 1e9, 1),
                       "bytes_per_launch": b}))
+
+
+def run_only_batched(args):
+    """The 512 seeded rD2Q9 cavities, 128 x 1 tiles (no tuning), direct
+    launches: `steps` steps after `warmup`."""
+    import torch
+
+    import workloads as W
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    doms = W.cavity_domains(512, seed=4)
+    b = Batch(doms, storage="f32", check_every=1000000, tol=1e-6, use_graphs=False)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nodes = sum(d["nx"] * d["ny"] for d in doms)
+    print(json.dumps({"only": args.only, "steps": args.steps, "nodes": nodes,
+                      "mlups": round(nodes * args.steps / (ms * 1e-3) / 1e6, 1),
+                      "achieved_gbs": round(72 * nodes * args.steps / (ms * 1e-3) / 1e9, 1)}))
+
+
+def run_only_train_step(args):
+    """Training steps of the warm-start network on a batch of 4 cavities of
+    32 x 64 x 64 cells (zero targets): 4 forward, 3 input-gradient and 4
+    weight-gradient convolutions on the tensor cores, MSE, Adam."""
+    import torch
+
+    from paper_2206_00366_gb300 import warmstart as WS
+    net = WS.Net(seed=0)
+    shape = (32, 64, 64)
+    T = torch.zeros((4,) + shape + (4,), dtype=torch.float32, device="cuda")
+    re = [200.0, 500.0, 800.0, 1100.0]
+    for _ in range(args.warmup):
+        net.train_step(re, shape, T, 1e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        net.train_step(re, shape, T, 1e-3)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    fl = sum(2.0 * 4 * 32 * 64 * 64 * 27 * WS.CH[k] * WS.CH[k + 1] for k in range(4))
+    print(json.dumps({"only": args.only, "steps": args.steps, "ms_per_step": round(ms, 3),
+                      "conv_tflops": round(3 * fl / (ms * 1e-3) / 1e12, 1)}))
 
 
 def main():
