@@ -997,3 +997,110 @@ def test_simple_ncde_needs_the_dBdt_term():
     e = simple_hill_error(1, "D2Q5", (0.2, 0.1))
     e_no = simple_hill_error(1, "D2Q5", (0.2, 0.1), with_dB=False)
     assert e < 0.02 and e < 0.4 * e_no, (e, e_no)
+
+
+# ---------------------------------------------------------------- brute force in exact arithmetic
+def _exact_step(name, c, cs2, nu, nub, sfree, shape, seed):
+    """One unforced NSE collide-and-stream step in sympy rationals, written
+    from the printed formulas: weights (Eqs. 3-3-5 / 3-3-8 with the tensor
+    omega_19), f^eq (Eq. NSEfeq), rates (Eq. 4-31), the S_2 block as the
+    exact inverse of Eq. (4-27-1), m* = m - S (m - m^eq), f* = M^-1 m*,
+    periodic pull streaming.  Returns (f0, f1) as float arrays."""
+    sp = pytest.importorskip("sympy")
+    R_ = sp.Rational
+    d = len(c)
+    e = R.velocity_indices(name)
+    q = e.shape[0]
+    cv = [[R_(int(e[j, a])) * c[a] for a in range(d)] for j in range(q)]
+    # weights
+    w = [R_(0)] * q
+    for j in range(1, q):
+        nz = [a for a in range(d) if e[j, a] != 0]
+        if name == "D2Q9":
+            w5 = cs2 ** 2 / (4 * c[0] ** 2 * c[1] ** 2)
+            w[j] = w5 if len(nz) == 2 else cs2 / (2 * c[nz[0]] ** 2) - 2 * w5
+        else:
+            w19 = cs2 ** 3 / (8 * c[0] ** 2 * c[1] ** 2 * c[2] ** 2) if name == "D3Q27" else R_(0)
+            edge = {}
+            for (a, b) in ((0, 1), (0, 2), (1, 2)):
+                edge[(a, b)] = cs2 ** 2 / (4 * c[a] ** 2 * c[b] ** 2) - 2 * w19
+            if len(nz) == 3:
+                w[j] = w19
+            elif len(nz) == 2:
+                w[j] = edge[tuple(nz)]
+            else:
+                a = nz[0]
+                w[j] = cs2 / (2 * c[a] ** 2) - 2 * sum(v for k, v in edge.items() if a in k) - 4 * w19
+    w[0] = 1 - sum(w[1:])
+    # rates and S
+    s_ab = 1 / (nu / cs2 + R_(1, 2))
+    ss = [1 / (2 * nu / (c[a] ** 2 - cs2) + R_(1, 2)) for a in range(d)]
+    sb = [1 / (d * nub / (c[a] ** 2 - cs2) + R_(1, 2)) for a in range(d)]
+    av = [(1 / sb[a] - 1 / ss[a]) * (c[a] ** 2 - cs2) for a in range(d)]
+    bv = [1 / (c[a] ** 2 - cs2) for a in range(d)]
+    S2inv = sp.Matrix(d, d, lambda i, k: (1 / ss[i] if i == k else 0) + av[i] * bv[k] / d)
+    S2 = S2inv.inv()
+    mons = R.monomials(name)
+    M = sp.Matrix(q, q, lambda k, j: sp.prod([cv[j][a] ** mons[k][a] for a in range(d)]))
+    S = sp.zeros(q, q)
+    diag2 = {}
+    for k, a in enumerate(mons):
+        o = sum(a)
+        if o == 2 and max(a) == 2:
+            diag2[a.index(2)] = k
+        elif o == 2:
+            S[k, k] = s_ab
+        else:
+            S[k, k] = sfree
+    for al, ka in diag2.items():
+        for be, kb in diag2.items():
+            S[ka, kb] = S2[al, be]
+    Minv = M.inv()
+    rng = np.random.default_rng(seed)
+    nodes = int(np.prod(shape))
+    f0 = [[w[j] * (1 + R_(int(rng.integers(-50, 51)), 1000)) for _ in range(nodes)] for j in range(q)]
+    fstar = [[None] * nodes for _ in range(q)]
+    for n in range(nodes):
+        f = sp.Matrix([f0[j][n] for j in range(q)])
+        rho = sum(f)
+        u = [sum(cv[j][a] * f[j] for j in range(q)) / rho for a in range(d)]
+        feq = []
+        for j in range(q):
+            t = 1 + sum(cv[j][a] * u[a] for a in range(d)) / cs2
+            t += sum(u[a] ** 2 * (cv[j][a] ** 2 - cs2) / (cs2 * (c[a] ** 2 - cs2)) for a in range(d))
+            t += sum(u[a] * u[b] * cv[j][a] * cv[j][b] / (2 * cs2 ** 2) for a in range(d) for b in range(d) if a != b)
+            feq.append(w[j] * rho * t)
+        m = M * f
+        mstar = m - S * (m - M * sp.Matrix(feq))
+        fs = Minv * mstar
+        for j in range(q):
+            fstar[j][n] = fs[j]
+    # periodic pull streaming on (nz, ny, nx)
+    nzs, nys, nxs = shape
+    f1 = [[None] * nodes for _ in range(q)]
+    for j in range(q):
+        ex = int(e[j, 0]); ey = int(e[j, 1]); ez = int(e[j, 2]) if d == 3 else 0
+        for z in range(nzs):
+            for y in range(nys):
+                for x in range(nxs):
+                    src = (((z - ez) % nzs) * nys + (y - ey) % nys) * nxs + (x - ex) % nxs
+                    f1[j][(z * nys + y) * nxs + x] = fstar[j][src]
+    to = lambda F: np.array([[float(v) for v in row] for row in F]).reshape((q,) + shape)
+    return to(f0), to(f1)
+
+
+@pytest.mark.parametrize("name,c,shape", [("D2Q9", (1, (1, 2)), (1, 2, 3)), ("D3Q19", (1, 1, (1, 2)), (2, 2, 3)),
+                                          ("D3Q27", (1, (3, 4), (1, 2)), (2, 2, 3))])
+def test_oracle_matches_exact_rational_step(name, c, shape):
+    """Brute force: the oracle's FP64 step equals one step computed in exact
+    rational arithmetic from the printed formulas (to 1e-14)."""
+    sp = pytest.importorskip("sympy")
+    cr = [sp.Rational(*v) if isinstance(v, tuple) else sp.Rational(v) for v in c]
+    cs2 = min(v * v for v in cr) / 3
+    nu, nub, sfree = sp.Rational(1, 50), sp.Rational(1, 20), sp.Rational(11, 10)
+    f0, f1 = _exact_step(name, cr, cs2, nu, nub, sfree, shape, seed=5)
+    lat = R.make_lattice(name, tuple(float(v) for v in cr))
+    r = R.rates_from_viscosity(lat, float(nu), float(nub), float(sfree))
+    S = R.relaxation_matrix(lat, r)
+    got = R.step(lat, R.Model(), S, f0, 1)
+    np.testing.assert_allclose(got, f1, rtol=0, atol=1e-14)
