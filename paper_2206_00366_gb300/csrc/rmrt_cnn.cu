@@ -58,6 +58,11 @@ __device__ __forceinline__ long long neighbour(const VoxCoord& c, int dz, int dy
 constexpr int kTcThreads = 128;
 constexpr uint32_t kWaitLimit = 1u << 26;   // mbarrier polls before a kernel gives up
 
+// Set by a tensor-core kernel whose bounded wait for its MMAs gave up (one
+// word per device, in the module's static memory; read and cleared by
+// rmrtlb_cnn_check).
+__device__ int g_tc_error;
+
 template <int KIN, int NOUT>
 struct TcShape {
   static constexpr int KP = KIN < 16 ? 16 : KIN;     // K per tap, padded to the MMA's 16
@@ -77,8 +82,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
                                                              const uint16_t* __restrict__ wt,
                                                              const float* __restrict__ bias,
                                                              const float* __restrict__ zin, int apply_silu,
-                                                             float* __restrict__ zout, uint16_t* __restrict__ aout,
-                                                             int* __restrict__ err) {
+                                                             float* __restrict__ zout, uint16_t* __restrict__ aout) {
   using S = TcShape<KIN, NOUT>;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ int s_ok;
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
       }
     }
   }
-  if (!ok && tid == 0) atomicExch(err, 1);
+  if (!ok && tid == 0) atomicExch(&g_tc_error, 1);
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(taddr, 32);
@@ -266,7 +270,7 @@ struct WgShape {
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kTcThreads) conv_wgrad_tc_kernel(Vol g, const uint16_t* __restrict__ x,
                                                                    const float* __restrict__ dy,
-                                                                   float* __restrict__ part, int* __restrict__ err) {
+                                                                   float* __restrict__ part) {
   using S = WgShape<CIN, COUT>;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ int s_ok;
@@ -366,7 +370,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_wgrad_tc_kernel(Vol g, const 
       for (int co = 0; co < COUT; ++co) out[co] = ntiles > 0 ? acc[co] : 0.0f;
     }
   } else if (tid == 0) {
-    atomicExch(err, 1);
+    atomicExch(&g_tc_error, 1);
   }
   tc::fence_before();
   __syncthreads();
@@ -520,39 +524,24 @@ int status_of(cudaError_t e) { return e == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUD
 unsigned blocks_for(long long items, int per) { return unsigned((items + per - 1) / per); }
 
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
-  }
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n < 1)
+    return 1;
   return n;
-}
-
-// Device word the tensor-core kernels set when an mbarrier wait gives up.
-int* tc_error_word() {
-  static int* p = nullptr;
-  if (!p && cudaMalloc(&p, sizeof(int)) == cudaSuccess) cudaMemset(p, 0, sizeof(int));
-  return p;
 }
 
 template <int KIN, int NOUT, int MODE>
 int launch_tc(Vol g, const void* in, const uint16_t* w, const float* bias, const float* zin, int silu, float* zout,
               uint16_t* aout, cudaStream_t s) {
   using S = TcShape<KIN, NOUT>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(conv_tc_kernel<KIN, NOUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
-        cudaSuccess)
-      return RMRTLB_ECUDA;
-    attr = true;
-  }
-  int* err = tc_error_word();
-  if (!err) return RMRTLB_ECUDA;
+  // the opt-in to more than 48 KB of shared memory holds per device: set it on every call
+  if (cudaFuncSetAttribute(conv_tc_kernel<KIN, NOUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) != cudaSuccess)
+    return RMRTLB_ECUDA;
   const long long tiles = (g.voxels() + 127) / 128;
   const long long cap = 3LL * sm_count();
   const unsigned grid = unsigned(tiles < cap ? tiles : cap);
-  conv_tc_kernel<KIN, NOUT, MODE><<<grid, kTcThreads, S::SMEM, s>>>(g, in, w, bias, zin, silu, zout, aout, err);
+  conv_tc_kernel<KIN, NOUT, MODE><<<grid, kTcThreads, S::SMEM, s>>>(g, in, w, bias, zin, silu, zout, aout);
   return status_of(cudaGetLastError());
 }
 
@@ -561,19 +550,14 @@ int chunks_of(Vol g) { return int((g.voxels() + kWeightChunk - 1) / kWeightChunk
 template <int CIN, int COUT>
 int wgrad_tc(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, float* scratch, cudaStream_t s) {
   using S = WgShape<CIN, COUT>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(conv_wgrad_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             S::SMEM) != cudaSuccess)
-      return RMRTLB_ECUDA;
-    attr = true;
-  }
-  int* err = tc_error_word();
-  if (!err) return RMRTLB_ECUDA;
+  // the opt-in to more than 48 KB of shared memory holds per device: set it on every call
+  if (cudaFuncSetAttribute(conv_wgrad_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
+      cudaSuccess)
+    return RMRTLB_ECUDA;
   const int chunks = chunks_of(g);
   float* part = scratch;
   float* bpart = scratch + size_t(chunks) * 27 * CIN * COUT;
-  conv_wgrad_tc_kernel<CIN, COUT><<<dim3(chunks, S::GROUPS), kTcThreads, S::SMEM, s>>>(g, x, dy, part, err);
+  conv_wgrad_tc_kernel<CIN, COUT><<<dim3(chunks, S::GROUPS), kTcThreads, S::SMEM, s>>>(g, x, dy, part);
   bias_grad_kernel<COUT><<<chunks, 32, 0, s>>>(g, dy, bpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return RMRTLB_ECUDA;
@@ -676,11 +660,10 @@ int rmrtlb_upsample_fields(int d, int h, int w, int c, const float* src, int D, 
 int rmrtlb_cnn_check(void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaStreamSynchronize(s) != cudaSuccess) return RMRTLB_ECUDA;
-  int* err = tc_error_word();
-  if (!err) return RMRTLB_ECUDA;
   int h = 0;
-  if (cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return RMRTLB_ECUDA;
-  if (h && cudaMemset(err, 0, sizeof(int)) != cudaSuccess) return RMRTLB_ECUDA;
+  if (cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int)) != cudaSuccess) return RMRTLB_ECUDA;
+  const int zero = 0;
+  if (h && cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)) != cudaSuccess) return RMRTLB_ECUDA;
   return h ? RMRTLB_ECUDA : RMRTLB_OK;
 }
 
