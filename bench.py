@@ -483,12 +483,17 @@ def run_reference(args):
     ny = int(max(8, min(256, 60.0 / max(args.steps, 1) / t_node / nx)))
     secs = _oracle_child(nx, ny, args.steps)     # one untimed warm-up step inside
     mlups = nx * ny * args.steps / secs / 1e6
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     line = {
-        "metric": "MLUPS", "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": 0, "steps": args.steps,
+        "metric": "MLUPS", "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": "rD2Q9 NSE Taylor-Green modes 4096x2048 dx=1 dy=0.6 FP32 storage",
-                   "lattice": "rD2Q9", "nx": 4096, "ny": 2048},
+                   "lattice": "rD2Q9", "nx": 4096, "ny": 2048, "storage": "f32", "basis": "raw",
+                   "check_every": CHECK_EVERY,
+                   "l2": "working set 604 MB > L2 (129 MB); no flush",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "device": "host cores (the oracle runs on the CPU; no GPU is used by this arm)",
         "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": f"each step: one FP64 oracle step on a {nx}x{ny} periodic band of the "
                                    f"4096x2048 workload, one BLAS thread"},
