@@ -106,10 +106,10 @@ enum rmrtlb_basis {
 };
 
 /* Population storage.  Every kind stores the deviation fbar_j - omega_j rho0;
- * F16 and BF16 store it times the power of two nearest 1/omega_j (exact to
- * apply and undo, keeps small-weight populations in the normal range) and
- * round to nearest even on every store.  F64 computes in FP64, the others
- * in FP32. */
+ * F16 stores it times the power of two nearest 1/omega_j (exact to apply
+ * and undo, keeps small-weight populations out of FP16's subnormals); BF16
+ * has FP32's exponent range and stores it unscaled; both round to nearest
+ * even on every store.  F64 computes in FP64, the others in FP32. */
 enum rmrtlb_storage {
     RMRTLB_ST_F64 = 0,
     RMRTLB_ST_F32 = 1,

@@ -9,7 +9,8 @@
 // zeroing them before the inverse transform keeps the corners empty.
 //
 // Storage holds the scaled deviation s_j = (fbar_j - omega_j rho0) * sc_j,
-// sc_j the power of two nearest 1/omega_j (exact to apply and to undo);
+// sc_j the power of two nearest 1/omega_j for FP16 storage (exact to apply
+// and to undo) and 1 for the others;
 // every moment below is a moment of delta_j = fbar_j - omega_j rho0, so the
 // rest state never enters the arithmetic (m(omega rho0) = m^eq(rho0, 0, 0)).
 #pragma once
@@ -540,10 +541,11 @@ __device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p, const V* bp
 template <int LAT>
 __device__ __forceinline__ constexpr int zi(int ez) { return Lat<LAT>::NZ == 3 ? ez + 1 : 0; }
 
-// Storage scaling: 16-bit populations are stored times a power of two near
-// 1/omega_j (for range); 32/64-bit ones unscaled.
+// Storage scaling: FP16 populations are stored times a power of two near
+// 1/omega_j (keeps small-weight deviations out of FP16's subnormal range);
+// BF16 has FP32's exponent range and, like 32/64-bit storage, is unscaled.
 template <typename ST>
-__device__ __forceinline__ constexpr bool scaled_storage() { return sizeof(ST) == 2; }
+__device__ __forceinline__ constexpr bool scaled_storage() { return std::is_same<ST, __half>::value; }
 
 // ------------------------------------------------------------------ kernels
 // One time step: pull gather from fin (post-collision of the previous step,

@@ -179,11 +179,12 @@ inline KParams<CT> to_kparams(const Consts& k) {
       p.q19h[g] = CT(k.cs2 * k.cs2 * c2[g] / ((c2[g] - k.cs2) * c2[al] * c2[be]));
     }
   }
-  const bool scaled = k.storage == RMRTLB_ST_F16 || k.storage == RMRTLB_ST_BF16;
+  const bool scaled = k.storage == RMRTLB_ST_F16;
   for (int j = 0; j < 27; ++j) {
     if (j < k.q) {
-      // 16-bit storage: power of two nearest 1/omega_j (exact to apply and
-      // undo); 32/64-bit storage is unscaled
+      // FP16 storage: power of two nearest 1/omega_j (exact to apply and
+      // undo, keeps deviations out of FP16's subnormals); BF16 (FP32's
+      // exponent range), FP32 and FP64 storage are unscaled
       const int e = scaled ? int(lround(-log2(k.w[j]))) : 0;
       p.sc[j] = CT(ldexp(1.0, e));
       p.sinv[j] = CT(ldexp(1.0, -e));
