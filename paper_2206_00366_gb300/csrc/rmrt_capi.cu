@@ -108,6 +108,7 @@ struct rmrtlb_solver {
   long long step;
   int check_every;
   int pairs;          // step kernel handles two nodes per thread (nx even)
+  int quads;          // four nodes per thread (16-bit storage on rD2Q9, nx % 4 == 0)
   bool has_prev;      // a periodic check wrote the residual snapshot
   long long slot_step[kSlots];
   bool slot_prev[kSlots];
@@ -271,6 +272,8 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
   s->kp64.hist_fresh = s->kp32.hist_fresh = 1;
   s->check_every = params->check_every;
   s->pairs = (nx % 2 == 0) && !axis_lattice(lattice) && !simple_ncde(eq_kind);
+  s->quads = s->pairs && nx % 4 == 0 && lattice == RMRTLB_D2Q9 &&
+             (storage == RMRTLB_ST_F16 || storage == RMRTLB_ST_BF16);
   *solver = s;
   return RMRTLB_OK;
 }
@@ -379,7 +382,13 @@ int rmrtlb_step(rmrtlb_t s, int n) {
   if (!s || n < 0) return RMRTLB_EINVAL;
   for (int i = 0; i < n; ++i) {
     LaunchArgs a = base_args(s, OP_STEP);
-    if (s->pairs) {
+    if (s->quads) {
+      const int quarter = s->k.nx / 4;
+      const int bx = block_x(quarter);
+      a.quads = 1;
+      a.block = dim3(bx, 1, 1);
+      a.grid = dim3((quarter + bx - 1) / bx, s->k.ny, s->k.nz);
+    } else if (s->pairs) {
       const int half = s->k.nx / 2;
       const int bx = block_x(half);
       a.pairs = 1;

@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <type_traits>
 #include <utility>
@@ -729,6 +730,124 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>:
       if constexpr (scaled_storage<ST>()) { va *= p.sc[j]; vb *= p.sc[j]; }
     }
     store_pair<ST, CT>(fout + j * N + own, va, vb);
+  });
+}
+
+
+// One time step, four x-adjacent nodes (x0 .. x0 + 3, x0 a multiple of 4)
+// per thread, for 16-bit storage on rD2Q9 (nx a multiple of 4): every
+// population is one aligned 8-byte load of four values, which doubles the
+// bytes in flight per thread against step_kernel_x2 (the 16-bit kernels are
+// limited by memory-level parallelism, not by arithmetic).  For e_x = +1 the
+// thread needs x0 - 1: the last value of the lane below (warp shuffle), lane 0
+// loading it; for e_x = -1 it needs x0 + 4 from the lane above, the last lane
+// of a warp or of a row loading it (periodic wrap).  The four nodes collide
+// as two packed FP32 pairs.
+template <typename ST>
+__device__ __forceinline__ void load_quad(const ST* p, float (&v)[4]) {
+  const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+  using H2 = typename Pair<ST>::T;
+  H2 a, b;
+  memcpy(&a, &w.x, 4);
+  memcpy(&b, &w.y, 4);
+  float2 fa, fb;
+  if constexpr (std::is_same<ST, __half>::value) {
+    fa = __half22float2(a);
+    fb = __half22float2(b);
+  } else {
+    fa = __bfloat1622float2(a);
+    fb = __bfloat1622float2(b);
+  }
+  v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+}
+template <typename ST>
+__device__ __forceinline__ void store_quad(ST* p, F2 a, F2 b) {
+  using H2 = typename Pair<ST>::T;
+  H2 ha, hb;
+  if constexpr (std::is_same<ST, __half>::value) {
+    ha = __floats2half2_rn(a.v.x, a.v.y);
+    hb = __floats2half2_rn(b.v.x, b.v.y);
+  } else {
+    ha = __floats2bfloat162_rn(a.v.x, a.v.y);
+    hb = __floats2bfloat162_rn(b.v.x, b.v.y);
+  }
+  uint2 w;
+  memcpy(&w.x, &ha, 4);
+  memcpy(&w.y, &hb, 4);
+  *reinterpret_cast<uint2*>(p) = w;
+}
+
+template <int LAT, typename ST, int BASIS, bool FORCED, bool NSE>
+__global__ void __launch_bounds__(128) step_kernel_x4(const ST* __restrict__ fin, ST* __restrict__ fout,
+                                                      const KParams<float> p) {
+  using L = Lat<LAT>;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int x0 = 4 * t;
+  const bool active = x0 < p.nx;
+  const int xc = active ? x0 : p.nx - 4;
+  const int lane = threadIdx.x & 31;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
+  const bool fix_lo = lane == 0;                       // needs x0 - 1 from memory
+  const bool fix_hi = lane == 31 || xc + 4 >= p.nx;    // needs x0 + 4 from memory
+  const int d_lo = (xc == 0 ? p.nx - 1 : xc - 1) - xc;
+  const int d_hi = (xc + 4 >= p.nx ? 0 : xc + 4) - xc;
+  const size_t N = p.N;
+  int roff[3][Lat<LAT>::NZ];
+#pragma unroll
+  for (int ey = -1; ey <= 1; ++ey)
+#pragma unroll
+    for (int ez = -1; ez <= 1; ++ez) {
+      if (Lat<LAT>::NZ == 1 && ez != 0) continue;
+      const int sy = Nbr::up(ey, ym, y, yp), sz = Nbr::up(ez, zm, z, zp);
+      roff[ey + 1][zi<LAT>(ez)] = (sz * p.ny + sy) * p.nx + xc;
+    }
+  Cube<LAT, F2> qa, qb;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < L::NZ; ++c) { qa.v[a][b][c] = F2(0.0f); qb.v[a][b][c] = F2(0.0f); }
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    const ST* src = fin + j * N + roff[ey + 1][zi<LAT>(ez)];
+    float v[4], o[4];
+    load_quad<ST>(src, v);
+    if constexpr (ex == 0) {
+      o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = v[3];
+    } else if constexpr (ex == 1) {
+      float prev = __shfl_up_sync(0xffffffffu, v[3], 1);
+      if (fix_lo) prev = load_st<ST, float>(src + d_lo);
+      o[0] = prev; o[1] = v[0]; o[2] = v[1]; o[3] = v[2];
+    } else {
+      float next = __shfl_down_sync(0xffffffffu, v[0], 1);
+      if (fix_hi) next = load_st<ST, float>(src + d_hi);
+      o[0] = v[1]; o[1] = v[2]; o[2] = v[3]; o[3] = next;
+    }
+    F2 a(o[0], o[1]), b(o[2], o[3]);
+    if constexpr (scaled_storage<ST>()) {
+      a = a * F2(p.sinv[j]);
+      b = b * F2(p.sinv[j]);
+    }
+    qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = a;
+    qb.v[ex + 1][ey + 1][zi<LAT>(ez)] = b;
+  });
+  collide<LAT, BASIS, FORCED, NSE>(qa, p);
+  collide<LAT, BASIS, FORCED, NSE>(qb, p);
+  if (!active) return;
+  const int own = (z * p.ny + y) * p.nx + x0;
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    F2 a = qa.v[ex + 1][ey + 1][zi<LAT>(ez)], b = qb.v[ex + 1][ey + 1][zi<LAT>(ez)];
+    if constexpr (scaled_storage<ST>()) {
+      a = a * F2(p.sc[j]);
+      b = b * F2(p.sc[j]);
+    }
+    store_quad<ST>(fout + j * N + own, a, b);
   });
 }
 

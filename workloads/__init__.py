@@ -117,16 +117,20 @@ def burgers_cole_hopf(nx, dx, U, diff, t, a=2.0, b=1.0, mode=1):
     return w / U
 
 
-def random_populations(q, shape, seed, level=1.0, amp=0.05):
+def random_populations(q, shape, seed, level=1.0, amp=0.05, base=None):
     """Random positive populations (q, nz, ny, nx) for parity tests.
 
-    Each direction gets a seeded base share of `level` and every value a
-    relative perturbation uniform in +-amp.  No equilibrium is implied: the
-    collision step is defined for any populations.
+    Each direction gets a seeded base share of `level` (or the q given
+    `base` values, e.g. a rest state) and every value a relative
+    perturbation uniform in +-amp.  No equilibrium is implied: the collision
+    step is defined for any populations.
     """
     rng = np.random.default_rng(seed)
-    base = rng.uniform(0.5, 1.5, size=q)
-    base *= level / base.sum()
+    if base is None:
+        base = rng.uniform(0.5, 1.5, size=q)
+        base *= level / base.sum()
+    else:
+        base = np.asarray(base, dtype=np.float64).reshape(q)
     noise = rng.uniform(-amp, amp, size=(q,) + tuple(shape))
     return base.reshape((q,) + (1,) * len(shape)) * (1.0 + noise)
 
