@@ -108,7 +108,7 @@ struct rmrtlb_solver {
   long long step;
   int check_every;
   int pairs;          // step kernel handles two nodes per thread (nx even)
-  int quads;          // four nodes per thread (16-bit storage on rD2Q9, nx % 4 == 0)
+  int quads;          // four nodes per thread (16-bit storage, nx % 4 == 0)
   bool has_prev;      // a periodic check wrote the residual snapshot
   long long slot_step[kSlots];
   bool slot_prev[kSlots];
@@ -272,7 +272,7 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
   s->kp64.hist_fresh = s->kp32.hist_fresh = 1;
   s->check_every = params->check_every;
   s->pairs = (nx % 2 == 0) && !axis_lattice(lattice) && !simple_ncde(eq_kind);
-  s->quads = s->pairs && nx % 4 == 0 && lattice == RMRTLB_D2Q9 &&
+  s->quads = s->pairs && nx % 4 == 0 &&
              (storage == RMRTLB_ST_F16 || storage == RMRTLB_ST_BF16);
   *solver = s;
   return RMRTLB_OK;

@@ -735,10 +735,11 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>:
 
 
 // One time step, four x-adjacent nodes (x0 .. x0 + 3, x0 a multiple of 4)
-// per thread, for 16-bit storage on rD2Q9 (nx a multiple of 4): every
-// population is one aligned 8-byte load of four values, which doubles the
-// bytes in flight per thread against step_kernel_x2 (the 16-bit kernels are
-// limited by memory-level parallelism, not by arithmetic).  For e_x = +1 the
+// per thread, for 16-bit storage (rD2Q9, rD3Q19, rD3Q27; nx a multiple of
+// 4): every population is one aligned 8-byte load of four values, which
+// doubles the bytes per load and halves the loads, shuffles and index
+// arithmetic per node against step_kernel_x2 (the 16-bit kernels were
+// limited by memory-level parallelism and issue, not by DRAM).  For e_x = +1 the
 // thread needs x0 - 1: the last value of the lane below (warp shuffle), lane 0
 // loading it; for e_x = -1 it needs x0 + 4 from the lane above, the last lane
 // of a warp or of a row loading it (periodic wrap).  The four nodes collide
@@ -778,7 +779,7 @@ __device__ __forceinline__ void store_quad(ST* p, F2 a, F2 b) {
 }
 
 template <int LAT, typename ST, int BASIS, bool FORCED, bool NSE>
-__global__ void __launch_bounds__(128) step_kernel_x4(const ST* __restrict__ fin, ST* __restrict__ fout,
+__global__ void __launch_bounds__(128, Tuning<LAT, 2, BASIS != 0>::X4_MIN_BLOCKS) step_kernel_x4(const ST* __restrict__ fin, ST* __restrict__ fout,
                                                       const KParams<float> p) {
   using L = Lat<LAT>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;

@@ -15,7 +15,7 @@ static void launch_basis(const LaunchArgs& a, const KParams<CT>& p, const ST* fi
     if (p.forced) step_kernel<LAT, ST, CT, BASIS, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
     else step_kernel<LAT, ST, CT, BASIS, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
     return;
-  } else if constexpr (LAT == LAT_D2Q9 && sizeof(ST) == 2) {
+  } else if constexpr (sizeof(ST) == 2) {
     if (a.quads) {
       if (p.forced) step_kernel_x4<LAT, ST, BASIS, true, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);
       else step_kernel_x4<LAT, ST, BASIS, false, NSE><<<a.grid, a.block, 0, a.stream>>>(fin, fout, p);

@@ -47,7 +47,7 @@ struct LaunchArgs {
   int storage;     // ST_*
   int central;     // basis of the relaxation, RMRTLB_BASIS_* (0 raw)
   int pairs;       // OP_STEP: two nodes per thread (nx even)
-  int quads;       // OP_STEP: four nodes per thread (16-bit storage on rD2Q9, nx % 4 == 0)
+  int quads;       // OP_STEP: four nodes per thread (16-bit storage, nx % 4 == 0)
   const void* fin;
   void* fout;
   const double* rho;       // OP_INIT_EQ

@@ -39,6 +39,30 @@
 #define RMRT_X2_MINB_D3Q27_W2_CENTRAL 5
 #endif
 
+// The same hint for the four-nodes-per-thread kernel (16-bit storage).  A
+// hint of 1 still changes the compiler's choice (it allows up to 255
+// registers; without a hint it keeps fewer).  Measured (MLUPS, best first):
+//   rD2Q9           9: 170,508   1: 168,989   none: 170,323
+//   rD3Q19 raw      1:  83,456   5:  81,669   none:  82,548
+//   rD3Q19 central  4:  67,137   1:  55,090   none:  65,967
+//   rD3Q27 raw      4:  58,009   1:  57,441   none:  57,624
+//   rD3Q27 central  3:  45,451   1:  41,471   none:  41,766
+#ifndef RMRT_X4_MINB_D2Q9
+#define RMRT_X4_MINB_D2Q9 9
+#endif
+#ifndef RMRT_X4_MINB_D3Q19
+#define RMRT_X4_MINB_D3Q19 1
+#endif
+#ifndef RMRT_X4_MINB_D3Q19_CENTRAL
+#define RMRT_X4_MINB_D3Q19_CENTRAL 4
+#endif
+#ifndef RMRT_X4_MINB_D3Q27
+#define RMRT_X4_MINB_D3Q27 4
+#endif
+#ifndef RMRT_X4_MINB_D3Q27_CENTRAL
+#define RMRT_X4_MINB_D3Q27_CENTRAL 3
+#endif
+
 namespace rmrt {
 // LAT: lattice; BYTES: size of one stored population; CENTRAL: basis.
 template <int LAT, int BYTES, bool CENTRAL>
@@ -50,5 +74,9 @@ struct Tuning {
                                : (CENTRAL ? RMRT_X2_MINB_D3Q19_W2_CENTRAL : RMRT_X2_MINB_D3Q19_W2))
                  : (BYTES == 4 ? RMRT_X2_MINB_D3Q27_W4
                                : (CENTRAL ? RMRT_X2_MINB_D3Q27_W2_CENTRAL : RMRT_X2_MINB_D3Q27_W2));
+  static constexpr int X4_MIN_BLOCKS =
+      LAT == 0 ? RMRT_X4_MINB_D2Q9
+      : LAT == 1 ? (CENTRAL ? RMRT_X4_MINB_D3Q19_CENTRAL : RMRT_X4_MINB_D3Q19)
+                 : (CENTRAL ? RMRT_X4_MINB_D3Q27_CENTRAL : RMRT_X4_MINB_D3Q27);
 };
 }  // namespace rmrt

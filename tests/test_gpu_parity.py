@@ -99,15 +99,21 @@ def test_random_populations(even, lattice, basis, kind, forced, storage):
         assert normwise(ug, uo) <= 10 * tol
 
 
-# 16-bit storage on rD2Q9: nx = 70 runs two nodes per thread; nx % 4 == 0
-# runs four nodes per thread (72 = 18 quads, a partly filled warp; 264 = 66
-# quads, two warps and a two-lane tail; 4 = one quad that wraps onto itself).
+# 16-bit storage: an even nx not divisible by 4 runs two nodes per thread;
+# nx % 4 == 0 runs four nodes per thread (rD2Q9: 72 = 18 quads, a partly
+# filled warp; 264 = 66 quads, two warps and a two-lane tail; 3-D: 16 = 4
+# quads per row; nx = 4 is one quad that wraps onto itself).
+SHAPES_16 = [("D2Q9", (70, 23, 1)), ("D2Q9", (72, 23, 1)), ("D2Q9", (264, 5, 1)), ("D2Q9", (4, 3, 1)),
+             ("D3Q19", (14, 11, 7)), ("D3Q19", (16, 11, 7)), ("D3Q19", (4, 3, 3)),
+             ("D3Q27", (14, 11, 7)), ("D3Q27", (16, 11, 7)), ("D3Q27", (4, 3, 3))]
+
+
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("forced", [False, True])
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("basis", ["raw", "central", "hermite", "central_hermite"])
-@pytest.mark.parametrize("shape", [(70, 23, 1), (72, 23, 1), (264, 5, 1), (4, 3, 1)])
-def test_random_populations_16bit_rd2q9(shape, basis, kind, forced, storage):
+@pytest.mark.parametrize("lattice,shape", SHAPES_16)
+def test_random_populations_16bit(lattice, shape, basis, kind, forced, storage):
     """Populations omega_j rho0 (1 + r), r uniform in +-0.05, six steps.
     Bounds derived from 16-bit storage: the initial store and each step
     round every stored deviation f_j - omega_j rho0 once, relative error at
@@ -117,12 +123,13 @@ def test_random_populations_16bit_rd2q9(shape, basis, kind, forced, storage):
     them times |c_j| <= max c, and dividing by rho adds |u| times the density
     error.  A wrong neighbour, lane or scale is an error of the size of the
     perturbation in some population, several times E."""
-    case = Case("D2Q9", shape, (1.0, 0.7, 0.55), kind=kind, basis=basis,
+    case = Case(lattice, shape, (1.0, 0.7, 0.55), kind=kind, basis=basis,
                 force=(2e-5, -1e-5, 1.5e-5) if forced else (0, 0, 0),
                 source=3e-6 if forced else 0.0)
     lat = case.lat()
-    rest = (lat.w * case.rho0).reshape(9, 1, 1, 1)             # omega_j rho0
-    pops = W.random_populations(9, case.field_shape, seed=17, amp=0.05, base=rest)
+    q = lat.q
+    rest = (lat.w * case.rho0).reshape(q, 1, 1, 1)             # omega_j rho0
+    pops = W.random_populations(q, case.field_shape, seed=17, amp=0.05, base=rest)
     steps = 6
     fo, ro, uo = oracle_run(case, steps, pops=pops, key="near-rest-pops-seed17")
     fg, rg, ug = gpu_run(case, storage, steps, pops=pops)
@@ -130,10 +137,10 @@ def test_random_populations_16bit_rd2q9(shape, basis, kind, forced, storage):
     D = max(np.abs(pops - rest).max(), np.abs(fo - rest).max())
     E = 2 * (steps + 1) * unit * D
     assert np.abs(fg - fo).max() <= E
-    assert np.abs(rg - ro).max() <= 9 * E
+    assert np.abs(rg - ro).max() <= q * E
     if kind.startswith("nse"):
         rmin = min(ro.min(), case.rho0)
-        assert np.abs(ug - uo).max() <= 9 * E * (lat.c.max() + np.abs(uo).max()) / rmin
+        assert np.abs(ug - uo).max() <= q * E * (lat.c.max() + np.abs(uo).max()) / rmin
 
 
 def test_set_get_roundtrip():
