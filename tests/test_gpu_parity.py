@@ -198,13 +198,17 @@ def test_taylor_green_3d(lattice, basis, storage):
 
 
 # ---------------------------------------------------------------- full-size, sampled
-def sampled_oracle(case, rho, u, nodes):
+def sampled_oracle(case, rho, u, nodes, with_dev=False):
     """One step of the oracle at sampled nodes from the equilibrium state
-    f^eq(rho, u): collide each upstream node x - e_j, take direction j."""
+    f^eq(rho, u): collide each upstream node x - e_j, take direction j.
+    with_dev: also the largest |f^eq_i - omega_i rho0| over those upstream
+    nodes (the initial deviation 16-bit storage holds)."""
     lat, m, S = case.oracle_setup()
     nz, ny, nx = rho.shape
     n = nodes.shape[0]
     out = np.empty((lat.q, n))
+    dev0 = 0.0
+    rest = (lat.w * case.rho0).reshape(lat.q, 1)
     for j in range(lat.q):
         ez = int(lat.e[j, 2]) if lat.d == 3 else 0
         z = (nodes[:, 0] - ez) % nz
@@ -214,7 +218,8 @@ def sampled_oracle(case, rho, u, nodes):
         uu = u[:, z, y, x].reshape(lat.d, 1, 1, n)
         f0 = R.init_equilibrium(lat, m, S, r, uu).reshape(lat.q, n)
         out[j] = R.collide(lat, m, S, f0)[j]
-    return out
+        dev0 = max(dev0, float(np.abs(f0 - rest).max()))
+    return (out, dev0) if with_dev else out
 
 
 @pytest.mark.parametrize("lattice,basis", [("D2Q9", "raw"), ("D3Q19", "raw"), ("D3Q19", "central"),
@@ -245,6 +250,42 @@ def test_full_size_one_step_sampled(lattice, basis):
     got = fg[:, idx[:, 0], idx[:, 1], idx[:, 2]].cpu().numpy()
     want = sampled_oracle(case, rho, u, nodes)
     assert normwise(got, want) <= 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("lattice,basis", [("D2Q9", "raw"), ("D3Q19", "raw"), ("D3Q19", "central"),
+                                           ("D3Q27", "raw"), ("D3Q27", "central")])
+def test_full_size_one_step_sampled_16bit(lattice, basis, storage):
+    """The 16-bit variants at full size in the launch configuration the bench
+    times (four nodes per thread): one step from seeded fields, 3000 sampled
+    nodes.  Bound from the storage: the initial store and the step each
+    round a deviation once (relative error <= u, 2^-11 FP16 / 2^-8 BF16);
+    E = 2 * 2u * D, D the largest deviation before or after the step."""
+    import torch
+    if lattice == "D2Q9":
+        shape, sp = (4096, 2048, 1), (1.0, 0.6, 1.0)
+        rho, u = W.taylor_green_2d_modes(4096, 2048, 1.0, 0.6, 1.0, 0.12, seed=2)
+    else:
+        shape, sp = (256, 256, 128), (1.0, 1.0, 0.5)
+        rho, u = W.random_fields((128, 256, 256), 3, seed=5, umax=0.02)
+    case = Case(lattice, shape, sp, basis=basis, nu=0.005, nu_bulk=0.01, s_free=1.1)
+    s = gpu_solver(case, storage)
+    s.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    s.step(1)
+    fg = torch.empty((s.q,) + rho.shape, dtype=torch.float64, device="cuda")
+    s.get_populations(fg)
+    rng = np.random.default_rng(13)
+    nz, ny, nx = rho.shape
+    nodes = np.stack([rng.integers(0, nz, 3000), rng.integers(0, ny, 3000), rng.integers(0, nx, 3000)], axis=1)
+    nodes[:4] = [[0, 0, 0], [nz - 1, ny - 1, nx - 1], [0, ny - 1, 0], [nz - 1, 0, nx - 1]]
+    idx = torch.from_numpy(nodes).cuda()
+    got = fg[:, idx[:, 0], idx[:, 1], idx[:, 2]].cpu().numpy()
+    want, dev0 = sampled_oracle(case, rho, u, nodes, with_dev=True)
+    lat = case.lat()
+    rest = (lat.w * case.rho0).reshape(lat.q, 1)
+    unit = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}[storage]
+    D = max(dev0, np.abs(want - rest).max())
+    assert np.abs(got - want).max() <= 4 * unit * D
 
 
 # ---------------------------------------------------------------- edge cases and API
