@@ -45,6 +45,8 @@ VARIANTS = [
     ("rD3Q27-central-f16", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f16", "central", "nse"),
     ("rD3Q27-hermite-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "hermite", "nse"),
     ("rD3Q27-central-hermite-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "central_hermite", "nse"),
+    ("rD2Q9-f64", "D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "f64", "raw", "nse"),
+    ("rD3Q27-raw-f64", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f64", "raw", "nse"),
 ]
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 ESIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
@@ -78,9 +80,9 @@ def hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(name: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+def profiled_entry(name: str):
+    """The committed ncu summary of one step workload, if it was taken on the
+    current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(path):
         return None
@@ -90,8 +92,34 @@ def profiled_traffic(name: str):
         return None
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    ent = d.get("workloads", {}).get(name)
+    return d.get("workloads", {}).get(name)
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    ent = profiled_entry(name)
     return ent.get("dram_bytes_per_launch") if ent else None
+
+
+# FP64 pipe of GB300: 1.25 TFLOP/s nominal = 625 G DFMA instructions/s; a
+# DADD or DMUL takes one pipe slot like a DFMA, so the FP64 step kernels are
+# measured in pipe instructions against 625 G/s.
+FP64_PIPE_GINST = 625.0
+
+
+def fp64_alu_roof(name: str, nodes: int, kernel_ms: float):
+    """ALU roofline of an FP64 step kernel from its ncu-counted DADD, DFMA
+    and DMUL per node (None without a current profile)."""
+    ent = profiled_entry(name)
+    if not ent or "fp64_inst_per_node" not in ent:
+        return None
+    rate = nodes / (kernel_ms * 1e-3)
+    ach = ent["fp64_inst_per_node"] * rate / 1e9
+    return {"bound": "alu", "unit": "G FP64 inst/s", "achieved": round(ach, 1), "peak": FP64_PIPE_GINST,
+            "frac": round(ach / FP64_PIPE_GINST, 4), "fp64_inst_per_node": ent["fp64_inst_per_node"],
+            "gflops": round(ent["fp64_flop_per_node"] * rate / 1e9, 1),
+            "peak_source": "nominal 1.25 TFLOP/s FP64 (DFMA) = 625 G pipe instructions/s"}
 
 
 class ClockSampler:
@@ -310,6 +338,8 @@ def run_ours(args):
                                   "kernel_ms": round(km, 5), "achieved_gbs": round(ach, 1),
                                   "frac_hbm": round(ach / peak, 4), "bytes_per_node": 2 * Q[lat] * ESIZE[st],
                                   "traffic": profiled_traffic(name)}
+                if st == "f64":
+                    variants[name]["alu"] = fp64_alu_roof(name, n, km)
                 del s
                 torch.cuda.empty_cache()
             except Exception as ex:  # report, do not hide
