@@ -463,9 +463,11 @@ def run_warmstart(args, re_seed=0):
 
 
 # ---------------------------------------------------------------- oracle timing
-def _oracle_worker(nx, ny, steps):
+def _oracle_worker(nx, ny, steps, sync=False):
     """Runs in a child process with one BLAS thread: oracle steps on an
-    nx x ny band of the workload; prints seconds."""
+    nx x ny band of the workload; prints seconds.  With sync, prints "ready"
+    after the set-up and one untimed step and waits for a line on stdin
+    before the timed steps (so that concurrent workers overlap)."""
     import oracle.rmrt as R
     import workloads as W
     lat = R.make_lattice("D2Q9", (1.0, 0.6))
@@ -474,30 +476,83 @@ def _oracle_worker(nx, ny, steps):
     rho, u = W.taylor_green_2d_modes(4096, 2048, 1.0, 0.6, 1.0, lat.cs2, seed=1)
     f = R.init_equilibrium(lat, m, S, rho[:, :ny, :nx].copy(), u[:, :, :ny, :nx].copy())
     f = R.step(lat, m, S, f, 1)
+    if sync:
+        print("ready", flush=True)
+        sys.stdin.readline()
     t0 = time.perf_counter()
     R.step(lat, m, S, f, steps)
-    print(json.dumps({"seconds": time.perf_counter() - t0}))
+    print(json.dumps({"seconds": time.perf_counter() - t0}), flush=True)
 
 
-def _oracle_child(nx, ny, steps):
+def _one_thread_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
+    return env
+
+
+def _oracle_child(nx, ny, steps):
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(nx), str(ny), str(steps)],
-                       capture_output=True, text=True, env=env, cwd=ROOT)
+                       capture_output=True, text=True, env=_one_thread_env(), cwd=ROOT)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_children(nx, ny, steps, procs):
+    """`procs` concurrent one-thread oracle processes, each stepping its own
+    nx x ny band `steps` times after a common start signal; returns the wall
+    seconds from the signal until the last one finished."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", str(nx), str(ny), str(steps), "sync"]
+    ps = [subprocess.Popen(cmd, stdin=subprocess.PIPE, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           env=_one_thread_env(), cwd=ROOT) for _ in range(procs)]
+    try:
+        for p in ps:
+            if p.stdout.readline().strip() != "ready":
+                raise RuntimeError(p.stderr.read()[-2000:])
+        t0 = time.perf_counter()
+        for p in ps:
+            p.stdin.write("go\n")
+            p.stdin.flush()
+        outs = [p.communicate() for p in ps]
+        wall = time.perf_counter() - t0
+    finally:
+        for p in ps:
+            if p.poll() is None:
+                p.kill()
+    for p, (out, err) in zip(ps, outs):
+        if p.returncode != 0:
+            raise RuntimeError(err[-2000:])
+    return wall
+
+
 def cpu_baseline(budget_s=20.0):
+    """The oracle on the host: one core, and every core (one process per
+    core, each on its own band of the workload)."""
     nx, ny = 1024, 512
     probe = _oracle_child(nx, ny, 1)
     steps = max(1, int(budget_s / max(probe, 1e-3)))
     secs = _oracle_child(nx, ny, steps)
-    return {"value": round(nx * ny * steps / secs / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} oracle steps on a {nx}x{ny} periodic band of the 4096x2048 workload "
-                      f"(FP64 numpy, one BLAS thread), {secs:.1f} s"}
+    single = {"value": round(nx * ny * steps / secs / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+              "sample": f"{steps} oracle steps on a {nx}x{ny} periodic band of the 4096x2048 workload "
+                        f"(FP64 numpy, one BLAS thread), {secs:.1f} s"}
+    procs = host_cores()
+    if procs <= 1:
+        return single
+    wall = _oracle_children(nx, ny, steps, procs)
+    return {"value": round(procs * nx * ny * steps / wall / 1e6, 4), "unit": "MLUPS", "cores": procs,
+            "kind": "oracle",
+            "sample": f"{procs} concurrent processes, one per host core, each {steps} oracle steps on its own "
+                      f"{nx}x{ny} periodic band of the 4096x2048 workload (FP64 numpy, one BLAS thread each), "
+                      f"{wall:.1f} s wall",
+            "single_core": single}
 
 
 def run_reference(args):
@@ -511,8 +566,10 @@ def run_reference(args):
     probe = _oracle_child(nx, 256, 1)
     t_node = probe / (nx * 256)
     ny = int(max(8, min(256, 60.0 / max(args.steps, 1) / t_node / nx)))
-    secs = _oracle_child(nx, ny, args.steps)     # one untimed warm-up step inside
-    mlups = nx * ny * args.steps / secs / 1e6
+    procs = host_cores()
+    # one process per host core on its own band; one untimed step inside each
+    secs = _oracle_children(nx, ny, args.steps, procs)
+    mlups = procs * nx * ny * args.steps / secs / 1e6
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     line = {
         "metric": "MLUPS", "value": round(mlups, 4), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -524,9 +581,10 @@ def run_reference(args):
                    "l2": "working set 604 MB > L2 (129 MB); no flush",
                    "parallelism": "replicas" if world > 1 else "single"},
         "device": "host cores (the oracle runs on the CPU; no GPU is used by this arm)",
-        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one FP64 oracle step on a {nx}x{ny} periodic band of the "
-                                   f"4096x2048 workload, one BLAS thread"},
+        "cpu_baseline": {"value": round(mlups, 4), "unit": "MLUPS", "cores": procs, "kind": "oracle",
+                         "sample": f"each step: one FP64 oracle step in each of {procs} concurrent processes "
+                                   f"(one per host core), each on its own {nx}x{ny} periodic band of the "
+                                   f"4096x2048 workload, one BLAS thread each"},
         "e2e": {"value": round(mlups, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -637,7 +695,8 @@ def run_only_train_step(args):
 
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--oracle-worker":
-        _oracle_worker(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]))
+        _oracle_worker(int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]),
+                       sync=len(sys.argv) > 5 and sys.argv[5] == "sync")
         return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)

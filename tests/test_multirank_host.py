@@ -63,3 +63,12 @@ def test_reference_arm_runs_on_rank_0_only():
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_concurrent_oracle_processes_start_together():
+    """The all-cores oracle timing: two one-thread oracle processes on their
+    own bands start their timed steps on one signal and both finish."""
+    import bench
+    wall = bench._oracle_children(64, 8, 2, 2)
+    assert 0.0 < wall < 120.0
+    assert bench.host_cores() >= 1
