@@ -406,7 +406,7 @@ def run_batched(args):
     ms = e0.elapsed_time(e1)
     res, conv, act, done = b.status()
     out["throughput"] = {"domains": len(doms), "nodes": nodes, "tile_width": width, "tile_rows": b.tile_rows,
-                         "steps": nsteps,
+                         "nodes_per_thread": b.nodes_per_thread, "steps": nsteps,
                          "mlups": round(nodes * nsteps / (ms * 1e-3) / 1e6, 1),
                          "achieved_gbs": round(72 * nodes * nsteps / (ms * 1e-3) / 1e9, 1),
                          "unstable_domains": int((act == -1).sum()),

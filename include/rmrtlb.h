@@ -291,11 +291,25 @@ int rmrtlb_batch_destroy(rmrtlb_batch_t batch);
 /* Every domain back at rest, active, step 0. */
 int rmrtlb_batch_reset(rmrtlb_batch_t batch);
 
-/* Autotuner: time `steps` steps with each tile shape — width 32, 64, 128
- * or 256 nodes (threads per block) times 1, 2 or 4 rows per block — keep
- * the fastest, then reset.  Writes the chosen width and rows (either
- * pointer may be NULL).  The batch starts with 128 x 1 tiles. */
-int rmrtlb_batch_tune(rmrtlb_batch_t batch, int steps, int* tile_width, int* tile_rows);
+/* Autotuner: time `steps` steps with each launch shape — tile width 32,
+ * 64, 128 or 256 nodes times 1, 2 or 4 rows per block, and for FP32
+ * storage nodes per thread 1 or 0 (automatic) — keep the fastest, then
+ * reset.  Nodes per thread: 1, a thread per node; 2 (FP32 only), two nodes
+ * per thread collided together in packed FP32 arithmetic; 0 (automatic,
+ * FP32 only), two while the domains being stepped hold at least twice as
+ * many nodes as the GPU has resident threads, else one (a thread per node
+ * finishes a step sooner when the batch, or what is left of it, is too
+ * small to fill the GPU).  Writes the chosen width, rows and nodes per
+ * thread (any pointer may be NULL).  The batch starts with 128 x 1 tiles
+ * and the automatic mode (FP32) or one node per thread (FP64). */
+int rmrtlb_batch_tune(rmrtlb_batch_t batch, int steps, int* tile_width, int* tile_rows,
+                      int* nodes_per_thread);
+
+/* Set the launch shape directly (the tuner's choices, e.g. from an earlier
+ * run): tile_width 32, 64, 128 or 256; tile_rows 1, 2 or 4;
+ * nodes_per_thread 1, or 2 or 0 with FP32 storage (see rmrtlb_batch_tune).
+ * The state is kept.  RMRTLB_EINVAL for any other value. */
+int rmrtlb_batch_set_launch(rmrtlb_batch_t batch, int tile_width, int tile_rows, int nodes_per_thread);
 
 /* Advance every active domain n steps (asynchronous). */
 int rmrtlb_batch_step(rmrtlb_batch_t batch, int n);

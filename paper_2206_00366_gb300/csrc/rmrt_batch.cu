@@ -173,6 +173,60 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const ST* __restrict__ 
   }
 }
 
+// FP32 storage: two nodes per thread, x0 + i and x0 + i + h (h = half the
+// tile width, rounded up), so that every load and store instruction of a
+// warp stays contiguous; the pair is collided as one F2 value in packed FP32
+// arithmetic (one instruction per operation for both nodes).  A thread
+// whose second node lies past the tile's width collides its first node
+// twice and stores it once.
+template <int LAT, int BASIS>
+__global__ void __launch_bounds__(128) batch_step_kernel_x2(const float* __restrict__ fin, float* __restrict__ fout,
+                                                            const BParams<float>* __restrict__ dom,
+                                                            const int4* __restrict__ tiles,
+                                                            const int* __restrict__ active) {
+  using L = Lat<LAT>;
+  const int4 t = tiles[blockIdx.x];  // (domain, row, x0, width)
+  if (active[t.x] != 1) return;      // retired: its last state stays in buffer A
+  __shared__ BParams<float> sp;
+  load_params(sp, dom, t.x);
+  const int w = tile_width(t), h = (w + 1) / 2;
+  const int i = int(threadIdx.x);
+  if (i >= h) return;
+  const bool has_b = i + h < w;
+  const float* base = fin + sp.off;
+  const int N = int(sp.k.N);
+  const int rows = tile_rows(t), xa = t.z + i, xb = has_b ? xa + h : xa;
+  RowYZ yz(t.y, sp.k.ny);
+  for (int r = 0; r < rows; ++r, yz.next(sp.k.ny)) {
+    const NodeXYZ na = node_at<LAT>(xa, yz.y, yz.z, sp);
+    const NodeXYZ nb = node_at<LAT>(xb, yz.y, yz.z, sp);
+    Cube<LAT, F2> q;
+    if constexpr (LAT == LAT_D3Q19) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) q.v[a][b][c] = F2(0.0f);
+    }
+    static_for<L::Q>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+      q.v[ex + 1][ey + 1][zi<LAT>(ez)] =
+          F2(gather<LAT, float, float, j>(base, na, sp), gather<LAT, float, float, j>(base, nb, sp));
+    });
+    collide<LAT, BASIS, false, true>(q, sp.k);
+    float* out = fout + sp.off;
+    static_for<L::Q>([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+      const F2 v = q.v[ex + 1][ey + 1][zi<LAT>(ez)];
+      out[j * N + na.own] = v.v.x;
+      if (has_b) out[j * N + nb.own] = v.v.y;
+    });
+  }
+}
+
 // Density and velocity of a node from its gathered populations.
 template <int LAT, typename ST, typename CT>
 __device__ __forceinline__ void node_fields(const ST* __restrict__ base, const NodeXYZ& n, const BParams<CT>& sp,
@@ -634,8 +688,11 @@ struct rmrtlb_batch {
   int storage;
   char* ws;
   cudaStream_t stream;
-  int width;                        // tile width (threads per block)
+  int width;                        // tile width (nodes)
   int rows;                         // rows per tile
+  int per_thread;                   // nodes per thread: 1, 2 (FP32, packed) or 0 (automatic, FP32)
+  size_t live_nodes;                // nodes of the domains in the tile list
+  size_t fill_nodes;                // twice the GPU's resident threads
   size_t ntiles;
   int check_every;
   double tol;
@@ -656,10 +713,12 @@ template <typename T> T* at(rmrtlb_batch* b, size_t off) { return reinterpret_ca
 cudaError_t build_tiles(rmrtlb_batch* b, int width, int rows, const std::vector<int>* act = nullptr) {
   std::vector<int4> t;
   std::vector<int> tb(b->dom.size() + 1, 0);
+  size_t live = 0;
   for (size_t d = 0; d < b->dom.size(); ++d) {
     tb[d] = int(t.size());
     if (act && (*act)[d] != 1) continue;
     const auto& D = b->dom[d];
+    live += nodes_of(D);
     const int nr = int(rows_of(D));
     for (int r = 0; r < nr; r += rows)
       for (int x0 = 0; x0 < D.nx; x0 += width) {
@@ -670,6 +729,7 @@ cudaError_t build_tiles(rmrtlb_batch* b, int width, int rows, const std::vector<
   }
   tb[b->dom.size()] = int(t.size());
   b->ntiles = t.size();
+  b->live_nodes = live;
   b->width = width;
   b->rows = rows;
   b->tile_begin_host = tb;
@@ -688,6 +748,14 @@ void drop_graph(rmrtlb_batch* b) {
   b->graph_ok = false;
 }
 
+// Two nodes per thread (packed FP32) when asked for, or, in the automatic
+// mode, while the domains being stepped hold at least twice as many nodes
+// as the GPU has resident threads; below that a thread per node finishes a
+// step sooner (the tail of a batch run, small batches).
+bool pairs(const rmrtlb_batch* b) {
+  return b->per_thread == 2 || (b->per_thread == 0 && b->live_nodes >= b->fill_nodes);
+}
+
 // Kernel launches, one functor per kernel; dispatch() picks the template
 // instance for the batch's lattice, basis and storage.
 struct StepF {
@@ -697,8 +765,18 @@ struct StepF {
     if (b->ntiles == 0) return cudaSuccess;
     const ST* fin = at<ST>(b, b->cur == 0 ? b->L.fA : b->L.fB);
     ST* fout = at<ST>(b, b->cur == 0 ? b->L.fB : b->L.fA);
-    batch_step_kernel<LAT, BASIS, ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
-        fin, fout, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active));
+    if constexpr (std::is_same<ST, float>::value) {
+      if (pairs(b)) {
+        batch_step_kernel_x2<LAT, BASIS><<<unsigned(b->ntiles), (b->width + 1) / 2, 0, b->stream>>>(
+            fin, fout, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active));
+      } else {
+        batch_step_kernel<LAT, BASIS, ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
+            fin, fout, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active));
+      }
+    } else {
+      batch_step_kernel<LAT, BASIS, ST, CT><<<unsigned(b->ntiles), b->width, 0, b->stream>>>(
+          fin, fout, at<BParams<CT>>(b, b->L.dom), at<int4>(b, b->L.tiles), at<int>(b, b->L.active));
+    }
     return cudaGetLastError();
   }
 };
@@ -967,6 +1045,14 @@ int rmrtlb_batch_create(rmrtlb_batch_t* out, int lattice, int basis, int ndomain
     e = cudaMemcpyAsync(b->ws + b->L.cold, cold.data(), cold.size() * sizeof(BCold), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   b->rows = 1;
+  b->per_thread = storage == RMRTLB_ST_F32 ? 0 : 1;
+  {
+    int dev = 0, sms = 0, tps = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&tps, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    b->fill_nodes = 2 * size_t(sms) * size_t(tps);
+  }
   if (e == cudaSuccess) e = build_tiles(b, 128, 1);
   if (e == cudaSuccess) e = reset_state(b);
   if (e != cudaSuccess) { delete b; return RMRTLB_ECUDA; }
@@ -1062,31 +1148,52 @@ int rmrtlb_batch_status(rmrtlb_batch_t b, double* residual, long long* steps_to_
   return RMRTLB_OK;
 }
 
-int rmrtlb_batch_tune(rmrtlb_batch_t b, int steps, int* width_out, int* rows_out) {
+int rmrtlb_batch_tune(rmrtlb_batch_t b, int steps, int* width_out, int* rows_out, int* per_thread_out) {
   if (!b || steps < 1) return RMRTLB_EINVAL;
   float best = 1e30f;
-  int best_w = b->width, best_r = b->rows;
+  int best_w = b->width, best_r = b->rows, best_p = b->per_thread;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RMRTLB_ECUDA;
-  for (int r : kRows)
-    for (int w : kWidths) {
-      if (build_tiles(b, w, r) != cudaSuccess) return RMRTLB_ECUDA;
-      for (int i = 0; i < 2; ++i) { do_step(b); b->cur ^= 1; }
-      cudaEventRecord(e0, b->stream);
-      for (int i = 0; i < steps; ++i) { do_step(b); b->cur ^= 1; }
-      cudaEventRecord(e1, b->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) return RMRTLB_ECUDA;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; best_w = w; best_r = r; }
-    }
+  // FP32: one node per thread, or the automatic mode (two while the batch fills the GPU)
+  const int modes[2] = {1, 0};
+  const int nmodes = b->storage == RMRTLB_ST_F32 ? 2 : 1;
+  for (int mi = 0; mi < nmodes; ++mi)
+    for (int r : kRows)
+      for (int w : kWidths) {
+        const int p = modes[mi];
+        b->per_thread = p;
+        if (build_tiles(b, w, r) != cudaSuccess) return RMRTLB_ECUDA;
+        for (int i = 0; i < 2; ++i) { do_step(b); b->cur ^= 1; }
+        cudaEventRecord(e0, b->stream);
+        for (int i = 0; i < steps; ++i) { do_step(b); b->cur ^= 1; }
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return RMRTLB_ECUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_w = w; best_r = r; best_p = p; }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   drop_graph(b);
+  b->per_thread = best_p;
   if (build_tiles(b, best_w, best_r) != cudaSuccess || reset_state(b) != cudaSuccess) return RMRTLB_ECUDA;
   if (width_out) *width_out = best_w;
   if (rows_out) *rows_out = best_r;
+  if (per_thread_out) *per_thread_out = best_p;
   return RMRTLB_OK;
+}
+
+int rmrtlb_batch_set_launch(rmrtlb_batch_t b, int tile_width, int tile_rows, int nodes_per_thread) {
+  if (!b) return RMRTLB_EINVAL;
+  bool w_ok = false, r_ok = false;
+  for (int w : kWidths) w_ok = w_ok || w == tile_width;
+  for (int r : kRows) r_ok = r_ok || r == tile_rows;
+  const bool p_ok = nodes_per_thread == 1 ||
+                    ((nodes_per_thread == 2 || nodes_per_thread == 0) && b->storage == RMRTLB_ST_F32);
+  if (!w_ok || !r_ok || !p_ok) return RMRTLB_EINVAL;
+  drop_graph(b);
+  b->per_thread = nodes_per_thread;
+  return build_tiles(b, tile_width, tile_rows) == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA;
 }
 
 int rmrtlb_batch_set_populations(rmrtlb_batch_t b, int domain, const double* f) {

@@ -134,7 +134,8 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_batch_init_fields": (i, [_vp, i, _vp, _vp, i]),
         "rmrtlb_batch_destroy": (i, [_vp]),
         "rmrtlb_batch_reset": (i, [_vp]),
-        "rmrtlb_batch_tune": (i, [_vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "rmrtlb_batch_tune": (i, [_vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "rmrtlb_batch_set_launch": (i, [_vp, i, i, i]),
         "rmrtlb_batch_step": (i, [_vp, i]),
         "rmrtlb_batch_status": (i, [_vp, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong),
                                     ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]),
@@ -156,7 +157,7 @@ def exported_symbols() -> list:
             "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
             "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_stress", "rmrtlb_population_totals_noalloc",
             "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
-            "rmrtlb_batch_tune", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
+            "rmrtlb_batch_tune", "rmrtlb_batch_set_launch", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
             "rmrtlb_batch_get_populations", "rmrtlb_batch_fields", "rmrtlb_batch_run", "rmrtlb_batch_init_fields",
             "rmrtlb_conv3d_forward", "rmrtlb_conv3d_backward_data", "rmrtlb_conv3d_backward_weight_scratch",
             "rmrtlb_conv3d_backward_weight", "rmrtlb_mse", "rmrtlb_adam", "rmrtlb_cavity_features",
@@ -293,9 +294,14 @@ def rmrtlb_batch_reset(h):
 
 
 def rmrtlb_batch_tune(h, steps: int):
-    w, r = ctypes.c_int(), ctypes.c_int()
-    _check(lib().rmrtlb_batch_tune(h, steps, ctypes.byref(w), ctypes.byref(r)), "rmrtlb_batch_tune")
-    return w.value, r.value
+    w, r, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().rmrtlb_batch_tune(h, steps, ctypes.byref(w), ctypes.byref(r), ctypes.byref(p)),
+           "rmrtlb_batch_tune")
+    return w.value, r.value, p.value
+
+
+def rmrtlb_batch_set_launch(h, tile_width: int, tile_rows: int, nodes_per_thread: int):
+    _check(lib().rmrtlb_batch_set_launch(h, tile_width, tile_rows, nodes_per_thread), "rmrtlb_batch_set_launch")
 
 
 def rmrtlb_batch_step(h, n: int):
@@ -490,6 +496,8 @@ class Batch:
         torch.cuda.synchronize()
         self.h = rmrtlb_batch_create(self.lattice, self.basis, self.domains, self.storage, rho0, check_every, tol,
                                      self.workspace.data_ptr(), nbytes, sp)
+        self.tile_rows = 1
+        self.nodes_per_thread = 0 if self.storage == STORAGE_NAMES["f32"] else 1   # 0: automatic
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -505,10 +513,16 @@ class Batch:
         rmrtlb_batch_reset(self.h)
 
     def tune(self, steps=20):
-        """Autotune the tile shape; returns the width (threads per block),
-        the rows per tile are kept in self.tile_rows."""
-        w, self.tile_rows = rmrtlb_batch_tune(self.h, steps)
+        """Autotune the launch shape; returns the tile width (nodes); the
+        rows per tile and the nodes per thread are kept in self.tile_rows
+        and self.nodes_per_thread."""
+        w, self.tile_rows, self.nodes_per_thread = rmrtlb_batch_tune(self.h, steps)
         return w
+
+    def set_launch(self, tile_width, tile_rows, nodes_per_thread):
+        """Set the launch shape directly (see tune); the state is kept."""
+        rmrtlb_batch_set_launch(self.h, tile_width, tile_rows, nodes_per_thread)
+        self.tile_rows, self.nodes_per_thread = tile_rows, nodes_per_thread
 
     def step(self, n=1):
         rmrtlb_batch_step(self.h, n)

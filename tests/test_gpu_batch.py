@@ -40,11 +40,16 @@ DOMAINS = [
 ]
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("storage,tol,per_thread", [("f64", 1e-12, 1), ("f32", 1e-5, 1), ("f32", 1e-5, 2)])
 @pytest.mark.parametrize("graphs", [False, True])
-def test_batch_matches_oracle(storage, tol, graphs):
+@pytest.mark.parametrize("width,rows", [(128, 1), (32, 4)])
+def test_batch_matches_oracle(storage, tol, per_thread, graphs, width, rows):
+    """Every launch shape: one or two nodes per thread (the pair's second
+    node x0 + i + h; odd widths leave a thread with one node), tiles of
+    32 x 4 and 128 x 1."""
     from paper_2206_00366_gb300.rmrtlb import Batch
     b = Batch(DOMAINS, storage=storage, check_every=1000, tol=1e-9, use_graphs=graphs)
+    b.set_launch(width, rows, per_thread)
     f0 = [W.random_populations(9, (1, d["ny"], d["nx"]), seed=20 + k) for k, d in enumerate(DOMAINS)]
     for k in range(len(DOMAINS)):
         b.set_populations(k, f0[k])
@@ -58,6 +63,19 @@ def test_batch_matches_oracle(storage, tol, graphs):
         assert normwise(fg, fo) <= tol
         assert normwise(rg, ro) <= tol
         assert normwise(ug, uo) <= 10 * tol
+
+
+def test_batch_set_launch_rejects_bad_shapes():
+    from paper_2206_00366_gb300.rmrtlb import Batch, RmrtlbError
+    b64 = Batch(DOMAINS[:2], storage="f64")
+    with pytest.raises(RmrtlbError):
+        b64.set_launch(128, 1, 2)          # two nodes per thread is FP32 only
+    with pytest.raises(RmrtlbError):
+        b64.set_launch(128, 1, 0)
+    b = Batch(DOMAINS[:2], storage="f32")
+    for bad in [(48, 1, 1), (128, 3, 1), (128, 1, 4), (128, 1, -1)]:
+        with pytest.raises(RmrtlbError):
+            b.set_launch(*bad)
 
 
 def test_batch_graph_equals_direct():
@@ -116,6 +134,7 @@ def test_batch_tune_picks_a_width_and_resets():
     b.step(10)
     w = b.tune(5)
     assert w in (32, 64, 128, 256)
+    assert b.tile_rows in (1, 2, 4) and b.nodes_per_thread in (0, 1)
     res, conv, act, done = b.status()
     assert done == 0 and act.all()
     z = b.get_populations(0)
@@ -160,13 +179,15 @@ def oracle_domain3(lattice, basis, d, steps, f0, rho0=1.0):
 
 @pytest.mark.parametrize("lattice", ["D3Q19", "D3Q27"])
 @pytest.mark.parametrize("basis", ["raw", "central", "hermite", "central_hermite"])
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-5)])
-def test_batch3d_matches_oracle(lattice, basis, storage, tol):
+@pytest.mark.parametrize("storage,tol,per_thread", [("f64", 1e-12, 1), ("f32", 1e-5, 1), ("f32", 1e-5, 2)])
+def test_batch3d_matches_oracle(lattice, basis, storage, tol, per_thread):
     """3-D cavities (walls on every face, lid on the top z face moving +x):
-    populations after 12 steps from random populations, domain by domain."""
+    populations after 12 steps from random populations, domain by domain,
+    with one or two nodes per thread."""
     from paper_2206_00366_gb300.rmrtlb import Batch
     q = 19 if lattice == "D3Q19" else 27
     b = Batch(DOMAINS3, storage=storage, check_every=1000, tol=1e-9, lattice=lattice, basis=basis)
+    b.set_launch(64, 2, per_thread)
     f0 = [W.random_populations(q, (d["nz"], d["ny"], d["nx"]), seed=40 + k) for k, d in enumerate(DOMAINS3)]
     for k, d in enumerate(DOMAINS3):        # created at rest: fbar = omega rho0
         lat = R.make_lattice(lattice, (d["dx"], d["dy"], d["dz"]))
