@@ -58,6 +58,8 @@ extern "C" {
                                   the last check step */
 #define RMRTLB_ETOOBIG   (-5)  /* input larger than a fixed-size internal
                                   buffer allows */
+#define RMRTLB_ETIMEOUT  (-6)  /* a bounded device-side wait gave up: the
+                                  kernel skipped its outputs and returned */
 
 /* --------------------------------------------------------------- choices */
 /* Lattices of Sec. III.  rD2Q5 and rD3Q7 (Remark I: rest and axis

@@ -17,7 +17,8 @@
  * aligned, unless stated otherwise.  Calls are asynchronous on `stream`
  * (a cudaStream_t, NULL for the legacy stream) and return RMRTLB_OK,
  * RMRTLB_EINVAL (bad size, unsupported channel pair, misaligned or NULL
- * pointer) or RMRTLB_ECUDA (launch failure).  Sizes: n d h w < 2^31. */
+ * pointer) or RMRTLB_ECUDA (launch failure); a give-up of a bounded wait
+ * inside a kernel is reported by rmrtlb_cnn_check (RMRTLB_ETIMEOUT).  Sizes: n d h w < 2^31. */
 #ifndef RMRTLB_CNN_H
 #define RMRTLB_CNN_H
 
@@ -91,11 +92,19 @@ int rmrtlb_cavity_features(int n, int d, int h, int w, const double* re, uint16_
 int rmrtlb_upsample_fields(int d, int h, int w, int c, const float* src, int D, int H, int W,
                            const double* scale, const double* offset, double* dst, void* stream);
 
-/* Synchronises `stream` and returns RMRTLB_ECUDA if any tensor-core
+/* Synchronises `stream` and returns RMRTLB_ETIMEOUT if any tensor-core
  * convolution since the last call gave up waiting for its MMAs (a bounded
- * wait; the kernel then skips its outputs) or if the stream reports an
- * error, else RMRTLB_OK.  Clears the condition. */
+ * wait; the kernel then skips its outputs and returns), RMRTLB_ECUDA if the
+ * stream reports an error, else RMRTLB_OK.  Clears the condition. */
 int rmrtlb_cnn_check(void* stream);
+
+/* Self-test of that bounded wait (no counterpart in the paper): one thread
+ * initialises an mbarrier that nothing arrives on and waits for it with the
+ * same polling routine the convolutions use, giving up after `polls` polls
+ * (1 <= polls <= 2^20, else RMRTLB_EINVAL); the give-up is recorded exactly
+ * as a convolution's, so the next rmrtlb_cnn_check returns
+ * RMRTLB_ETIMEOUT, and the context stays usable. */
+int rmrtlb_cnn_wait_selftest(unsigned polls, void* stream);
 
 /* Training targets of one cavity from its fields: for each of n nodes,
  * out[4 i + 0] = (rho[i] - rho0) * rho_scale, out[4 i + 1 + a] =

@@ -223,6 +223,7 @@ const char* rmrtlb_strerror(int status) {
     case RMRTLB_ECUDA: return "CUDA runtime error";
     case RMRTLB_EUNSTABLE: return "unstable state (NaN/Inf, density <= 0 or |u| >= c_s)";
     case RMRTLB_ETOOBIG: return "input larger than the fixed internal buffer allows";
+    case RMRTLB_ETIMEOUT: return "a bounded device-side wait gave up";
     default: return "unknown status";
   }
 }

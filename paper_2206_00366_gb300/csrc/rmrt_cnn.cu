@@ -567,6 +567,18 @@ int wgrad_tc(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, fl
   return status_of(cudaGetLastError());
 }
 
+// An mbarrier that nothing arrives on, waited for with the convolutions'
+// bounded polling: the wait gives up after `polls` polls and the give-up
+// is recorded in the same error word.
+__global__ void wait_selftest_kernel(uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!tc::mbar_wait(&bar, 0, polls)) atomicExch(&g_tc_error, 1);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -664,7 +676,13 @@ int rmrtlb_cnn_check(void* stream) {
   if (cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int)) != cudaSuccess) return RMRTLB_ECUDA;
   const int zero = 0;
   if (h && cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)) != cudaSuccess) return RMRTLB_ECUDA;
-  return h ? RMRTLB_ECUDA : RMRTLB_OK;
+  return h ? RMRTLB_ETIMEOUT : RMRTLB_OK;
+}
+
+int rmrtlb_cnn_wait_selftest(unsigned polls, void* stream) {
+  if (polls < 1 || polls > (1u << 20)) return RMRTLB_EINVAL;
+  wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(polls);
+  return status_of(cudaGetLastError());
 }
 
 int rmrtlb_pack_fields(long long n, int d, const double* rho, const double* u, double rho0, double rho_scale,

@@ -25,7 +25,7 @@ EQ_NSE, EQ_NSE_HELUO, EQ_NCDE_LINEAR, EQ_NCDE_QUAD = 0, 1, 2, 3
 EQ_NCDE_SIMPLE_LINEAR, EQ_NCDE_SIMPLE_QUAD = 4, 5
 BASIS_RAW, BASIS_CENTRAL, BASIS_HERMITE, BASIS_CENTRAL_HERMITE = 0, 1, 2, 3
 ST_F64, ST_F32, ST_F16, ST_BF16 = 0, 1, 2, 3
-OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETOOBIG = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETOOBIG, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 NOALLOC_MAX_NODES = 67108864
 
 LATTICE_NAMES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27, "D2Q5": D2Q5, "D3Q7": D3Q7}
@@ -131,6 +131,7 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_upsample_fields": (i, [i, i, i, i, _vp, i, i, i, ctypes.POINTER(d), ctypes.POINTER(d), _vp, _vp]),
         "rmrtlb_pack_fields": (i, [ctypes.c_longlong, i, _vp, _vp, d, d, d, _vp, _vp]),
         "rmrtlb_cnn_check": (i, [_vp]),
+        "rmrtlb_cnn_wait_selftest": (i, [ctypes.c_uint, _vp]),
         "rmrtlb_batch_init_fields": (i, [_vp, i, _vp, _vp, i]),
         "rmrtlb_batch_destroy": (i, [_vp]),
         "rmrtlb_batch_reset": (i, [_vp]),
@@ -161,7 +162,7 @@ def exported_symbols() -> list:
             "rmrtlb_batch_get_populations", "rmrtlb_batch_fields", "rmrtlb_batch_run", "rmrtlb_batch_init_fields",
             "rmrtlb_conv3d_forward", "rmrtlb_conv3d_backward_data", "rmrtlb_conv3d_backward_weight_scratch",
             "rmrtlb_conv3d_backward_weight", "rmrtlb_mse", "rmrtlb_adam", "rmrtlb_cavity_features",
-            "rmrtlb_upsample_fields", "rmrtlb_pack_fields", "rmrtlb_cnn_check"]
+            "rmrtlb_upsample_fields", "rmrtlb_pack_fields", "rmrtlb_cnn_check", "rmrtlb_cnn_wait_selftest"]
 
 
 def _check(status: int, where: str):
@@ -374,6 +375,10 @@ def rmrtlb_upsample_fields(d, h, w, c, src, D, H, W, scale, offset, dst, stream=
 
 def rmrtlb_cnn_check(stream=0):
     _check(lib().rmrtlb_cnn_check(stream), "rmrtlb_cnn_check")
+
+
+def rmrtlb_cnn_wait_selftest(polls, stream=0):
+    _check(lib().rmrtlb_cnn_wait_selftest(polls, stream), "rmrtlb_cnn_wait_selftest")
 
 
 def rmrtlb_pack_fields(n, d, rho, u, rho0, rho_scale, u_scale, out, stream=0):

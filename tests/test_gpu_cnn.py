@@ -63,6 +63,34 @@ def test_conv_forward(cin, cout, silu):
     assert np.abs(host(a) - ao).max() <= 2.0 ** -7 * np.abs(ao).max()
 
 
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """Failure detection without a GPU fault: an mbarrier that nothing
+    arrives on, waited for with the convolutions' bounded polling, gives up
+    after 1000 polls; rmrtlb_cnn_check reports RMRTLB_ETIMEOUT once, and the
+    context stays usable (a convolution afterwards matches the oracle)."""
+    import torch
+    from paper_2206_00366_gb300 import rmrtlb as B
+    B.rmrtlb_cnn_check()
+    B.rmrtlb_cnn_wait_selftest(1000)
+    with pytest.raises(B.RmrtlbError) as e:
+        B.rmrtlb_cnn_check()
+    assert e.value.status == B.ETIMEOUT
+    B.rmrtlb_cnn_check()                     # the condition was cleared
+    with pytest.raises(B.RmrtlbError) as e:
+        B.rmrtlb_cnn_wait_selftest(0)
+    assert e.value.status == B.EINVAL
+    n, d, h, w = SHAPE
+    rng = np.random.default_rng(5)
+    xg, x = bf16(rng.normal(size=(n, d, h, w, 32)))
+    wg, wv = bf16(rng.normal(scale=0.2, size=(27, 32, 32)))
+    b = np.zeros(32, dtype=np.float32)
+    z = torch.empty((n, d, h, w, 32), dtype=torch.float32, device="cuda")
+    bt = dev(b, torch.float32)
+    B.rmrtlb_conv3d_forward(n, d, h, w, 32, 32, xg.data_ptr(), wg.data_ptr(), bt.data_ptr(), 0, z.data_ptr(), 0)
+    B.rmrtlb_cnn_check()
+    assert normwise(host(z), C.conv3d(x, wv, b.astype(np.float64))) <= 1e-5
+
+
 @pytest.mark.parametrize("cin,cout", [(32, 32), (32, 4)])
 @pytest.mark.parametrize("with_z", [True, False])
 def test_conv_backward_data(cin, cout, with_z):
