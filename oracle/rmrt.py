@@ -31,6 +31,12 @@ explicit REDF); nothing uses closed-form equilibrium moments.  The one place
 where the paper is garbled or silent, the reading taken is stated in the
 docstring of the function concerned.
 
+Parity unpinned: the auxiliary distribution G (M_2G of Eq. M2GComput a for
+the forced NSE, M_1G of Eq. 4-11 for the NCDE with a source), computed in
+``equilibrium_and_sources``.  It carries no mass or momentum, so the
+invariant pins do not see it, and no closed-form flow in the tests isolates
+it; it is the printed formula evaluated as written.
+
 Array conventions: a population field is an array of shape (q, nz, ny, nx)
 (2-D lattices use nz = 1), x fastest; a node list is an array of shape (q, n).
 Lattice units: dt is explicit, c_alpha = dx_alpha / dt.
@@ -494,6 +500,10 @@ def equilibrium_and_sources(lat: Lattice, m: Model, S: np.ndarray, rho, u, dBdt=
       M_1G = (I - S_1/2) B' S (Eq. 4-11, first case).
     Simplified NCDE (Eq. 4-16): f^eq = g^eq(phi, B, 0), F = omega S,
       G = g^eq(0, (I - S_1/2) dB/dt, 0), dB/dt given per node (n, d).
+
+    Parity unpinned for G of the forced NSE and of the NCDE with a source
+    (see the module header); the simplified NCDE's G is pinned by the
+    planted omission of dB/dt.
     """
     d, n, cs2 = lat.d, rho.size, lat.cs2
     I = np.eye(d)
