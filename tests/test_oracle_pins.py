@@ -291,6 +291,57 @@ def test_reduces_to_lallemand_luo_mrt():
     np.testing.assert_allclose(got, want, atol=2e-15)
 
 
+def test_forced_step_reduces_to_guo_forced_mrt():
+    """Standard D2Q9 (c_s^2 = 1/3), body force, no source: through third
+    order every raw moment after one oracle collision equals the textbook
+    Lallemand-Luo MRT step with Guo's forcing (Guo, Zheng & Shi, Phys. Rev.
+    E 65, 046308 (2002), in moment space: m* = m - Sbar (m - m^eq) +
+    dt (I - Sbar/2) M F~, F~_i = w_i [(e_i - u)/c_s^2 + (e_i.u) e_i/c_s^4].F,
+    u = (j + dt F/2)/rho).  The second-order moments carry the force only
+    through the auxiliary distribution G (M_2G of Eq. M2GComput a), so a
+    dropped G, a wrong (I - S_2/2) factor or a transposed u F term fails
+    here.  Only the fourth-order moment xxyy, which does not enter the NSE,
+    is built differently by the two schemes."""
+    lat = R.make_lattice("D2Q9", (1, 1), 1.0, 1.0 / 3.0)
+    MLL = np.array([
+        [1, 1, 1, 1, 1, 1, 1, 1, 1],
+        [-4, -1, -1, -1, -1, 2, 2, 2, 2],
+        [4, -2, -2, -2, -2, 1, 1, 1, 1],
+        [0, 1, 0, -1, 0, 1, -1, -1, 1],
+        [0, -2, 0, 2, 0, 1, -1, -1, 1],
+        [0, 0, 1, 0, -1, 1, 1, -1, -1],
+        [0, 0, -2, 0, 2, 1, 1, -1, -1],
+        [0, 1, -1, 1, -1, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 1, -1, 1, -1]], dtype=float)
+    Sbar = np.diag([0.9, 1.2, 1.4, 0.9, 1.15, 0.9, 1.15, 1.8, 1.8])
+    f = W.random_populations(9, (50,), seed=6)
+    F = np.array([2e-3, -1.5e-3])
+    cs2 = 1.0 / 3.0
+    ex, ey = lat.e[:, 0].astype(float), lat.e[:, 1].astype(float)
+    rho = f.sum(0)
+    ux = (ex @ f + 0.5 * F[0]) / rho
+    uy = (ey @ f + 0.5 * F[1]) / rho
+    u2 = ux ** 2 + uy ** 2
+    meq = np.array([rho, -2 * rho + 3 * rho * u2, rho - 3 * rho * u2, rho * ux, -rho * ux, rho * uy, -rho * uy,
+                    rho * (ux ** 2 - uy ** 2), rho * ux * uy])
+    eu = ex[:, None] * ux[None] + ey[:, None] * uy[None]
+    eF = ex * F[0] + ey * F[1]
+    uF = ux * F[0] + uy * F[1]
+    Ft = lat.w[:, None] * ((eF[:, None] - uF[None]) / cs2 + eu * eF[:, None] / cs2 ** 2)
+    mll = MLL @ f
+    want = np.linalg.solve(MLL, mll - Sbar @ (mll - meq) + (np.eye(9) - 0.5 * Sbar) @ (MLL @ Ft))
+    N = MLL @ np.linalg.inv(R.moment_matrix(lat))
+    S = np.linalg.solve(N, Sbar @ N)
+    got = R.collide(lat, R.Model(force=(F[0], F[1], 0.0)), S, f)
+    M = R.moment_matrix(lat)
+    low = [k for k, a in enumerate(R.monomials("D2Q9")) if sum(a) <= 3]
+    np.testing.assert_allclose((M @ got)[low], (M @ want)[low], atol=2e-15)
+    # what G adds to the second-order moments, u F + F u, is ten orders of
+    # magnitude above the tolerance (the pin has teeth)
+    assert min(np.abs(2 * ux * F[0]).max(), np.abs(2 * uy * F[1]).max(),
+               np.abs(ux * F[1] + uy * F[0]).max()) > 1e-5
+
+
 # ---------------------------------------------------------------- invariants
 @pytest.mark.parametrize("name", R.LATTICES)
 @pytest.mark.parametrize("basis", [R.RAW, R.CENTRAL, R.HERMITE, R.CENTRAL_HERMITE])
