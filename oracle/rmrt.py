@@ -31,13 +31,12 @@ explicit REDF); nothing uses closed-form equilibrium moments.  The one place
 where the paper is garbled or silent, the reading taken is stated in the
 docstring of the function concerned.
 
-Parity unpinned: two parts of the auxiliary distribution G, computed in
-``equilibrium_and_sources`` — the source part c_s^2 Sbar I of M_2G (Eq.
-M2GComput a) of the NSE, and M_1G of Eq. (4-11) of the NCDE with a source.
-G carries no mass or momentum, so the invariant pins do not see it, and no
-closed-form flow in the tests isolates those parts; they are the printed
-formulas evaluated as written.  (The force part u F + F u of M_2G is pinned:
-a forced step reduces to the textbook Guo-forced MRT step.)
+Pins of the auxiliary distribution G (computed in
+``equilibrium_and_sources``), which carries no mass or momentum and so
+escapes the invariant pins: its force part u F + F u (Eq. M2GComput a) by
+the reduction of a forced step to the textbook Guo-forced MRT step; its
+source part c_s^2 Sbar I and the NCDE's M_1G (Eq. 4-11) by steady sourced
+flows with closed forms that a planted omission of G misses.
 
 Array conventions: a population field is an array of shape (q, nz, ny, nx)
 (2-D lattices use nz = 1), x fastest; a node list is an array of shape (q, n).
@@ -503,10 +502,9 @@ def equilibrium_and_sources(lat: Lattice, m: Model, S: np.ndarray, rho, u, dBdt=
     Simplified NCDE (Eq. 4-16): f^eq = g^eq(phi, B, 0), F = omega S,
       G = g^eq(0, (I - S_1/2) dB/dt, 0), dB/dt given per node (n, d).
 
-    Parity unpinned for the source part of M_2G and for M_1G of the NCDE
-    with a source (see the module header); the force part of M_2G is pinned
-    by the Guo-forced MRT reduction, the simplified NCDE's G by the planted
-    omission of dB/dt.
+    G is pinned by the Guo-forced MRT reduction (force part of M_2G), by
+    steady sourced flows (source part of M_2G, M_1G of the NCDE) and, for
+    the simplified NCDE, by the planted omission of dB/dt.
     """
     d, n, cs2 = lat.d, rho.size, lat.cs2
     I = np.eye(d)

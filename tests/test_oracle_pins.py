@@ -1050,6 +1050,79 @@ def test_simple_ncde_needs_the_dBdt_term():
     assert e < 0.02 and e < 0.4 * e_no, (e, e_no)
 
 
+# ---------------------------------------------------------------- the auxiliary distribution G with a source
+def _collide_without_G(lat, m, S, fl):
+    """A planted mistake: the oracle's raw-basis collision with G dropped."""
+    rho, u = R.macroscopic(lat, m, fl)
+    feq, _, F = R.equilibrium_and_sources(lat, m, S, rho, u)
+    M, I = R.moment_matrix(lat), np.eye(lat.q)
+    mb, meq, mF = M @ fl, M @ feq, M @ F
+    return np.linalg.solve(M, mb - S @ (mb - meq) + lat.dt * (I - 0.5 * S) @ mF)
+
+
+def _steady_sourced(model, S, lat, nx, ny, steps, with_G):
+    f = R.init_equilibrium(lat, model, S, np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx)))
+    for _ in range(steps):
+        fl = f.reshape(lat.q, -1)
+        fs = R.collide(lat, model, S, fl) if with_G else _collide_without_G(lat, model, S, fl)
+        f = R.stream(lat, fs.reshape(f.shape))
+    return R.fields(lat, model, f)
+
+
+@pytest.mark.parametrize("kind,S0,bound", [(R.NCDE_LINEAR, 1e-3, 2e-3), (R.NCDE_QUAD, 1e-4, 3e-3)])
+def test_sourced_ncde_steady_state_needs_G(kind, S0, bound):
+    """phi_t + u phi_x = D phi_xx + S0 sin(kx) on the rectangular rD2Q9
+    lattice (dx = 1, dy = 0.7), periodic, u = 0.2 along x: the steady state
+    is phi = 1 + A sin(kx) + B cos(kx), A = S0 D / (u^2 + D^2 k^2),
+    B = -u A / (D k) (for the quadratic kind B = u phi^2/2 at small
+    amplitude, where the same linear solution holds to O(A)).  The oracle
+    reaches it within `bound`; dropping G = g^eq(0, M_1G, 0) of Eq. (4-11),
+    M_1G = (I - S_1/2) B' S, makes the error many times larger."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.7), 1.0)
+    nx, ny, u, D = 32, 2, 0.2, 0.05
+    tau = D / (lat.cs2 * lat.dt) + 0.5
+    rr = R.Rates(1.0, np.full(2, 1 / tau), np.full(2, 1.1), np.full(2, 1.1), np.full((2, 2), 1.1), 1.1)
+    S = R.relaxation_matrix(lat, rr)
+    x = np.arange(nx, dtype=float)
+    k = 2 * np.pi / nx
+    src = np.broadcast_to(S0 * np.sin(k * x), (ny, nx)).reshape(-1).copy()
+    model = R.Model(kind, adv=(u, 0.0, 0.0), source=src)
+    A = S0 * D / (u * u + D * D * k * k)
+    exact = 1.0 + A * np.sin(k * x) - u * A / (D * k) * np.cos(k * x)
+    err = []
+    for with_G in (True, False):
+        phi = _steady_sourced(model, S, lat, nx, ny, 4000, with_G)[0][0, 0]
+        err.append(np.abs(phi - exact).max() / np.abs(exact - 1.0).max())
+    assert err[0] < bound and err[0] < 0.2 * err[1], err
+
+
+def test_nse_mass_source_steady_state_needs_G():
+    """NSE with a mass source Sbar = S0 sin(kx) on rD2Q9 (dx = 1, dy = 0.7),
+    periodic, small S0: continuity gives u = -S0 cos(kx) / (k rho0) and the
+    normal viscous stress, with the longitudinal viscosity nu_L = 2 nu
+    (1 - 1/d) + nu_b of the sound-attenuation pin, balances the pressure:
+    rho = rho0 + nu_L S0 sin(kx) / c_s^2.  The oracle matches both within
+    1 %; dropping G (its M_2G = (I - S_2/2) c_s^2 Sbar I here, Eq.
+    M2GComput a) leaves u unchanged but makes the density error about 20 %."""
+    lat = R.make_lattice("D2Q9", (1.0, 0.7), 1.0)
+    nx, ny, nu, nub, S0 = 32, 2, 0.05, 0.05, 1e-5
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, nub, 1.1))
+    x = np.arange(nx, dtype=float)
+    k = 2 * np.pi / nx
+    src = np.broadcast_to(S0 * np.sin(k * x), (ny, nx)).reshape(-1).copy()
+    model = R.Model(R.NSE, source=src)
+    nuL = 2 * (1 - 1 / 2) * nu + nub
+    rho_ex = 1.0 + nuL * S0 * np.sin(k * x) / lat.cs2
+    u_ex = -S0 * np.cos(k * x) / k
+    res = []
+    for with_G in (True, False):
+        rho, u = _steady_sourced(model, S, lat, nx, ny, 4000, with_G)
+        res.append((np.abs(rho[0, 0] - rho_ex).max() / np.abs(rho_ex - 1).max(),
+                    np.abs(u[0, 0, 0] - u_ex).max() / np.abs(u_ex).max()))
+    (er, eu), (er_no, _) = res
+    assert er < 1e-2 and eu < 1e-2 and er < 0.1 * er_no, res
+
+
 # ---------------------------------------------------------------- brute force in exact arithmetic
 def _exact_step(name, c, cs2, nu, nub, sfree, shape, seed):
     """One unforced NSE collide-and-stream step in sympy rationals, written
