@@ -6,6 +6,7 @@
 // GEMMs on the tensor cores (tcgen05, rmrt_cnn_tc.cuh).  The weight gradient
 // reduces over voxels in a fixed order (per-chunk partials, then a
 // fixed-order sum), so results are deterministic.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -241,6 +242,282 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(taddr, 32);
+}
+
+// ------------------------------------------------------------------ forward, fed by the tensor-memory accelerator
+// Output tiles are boxes of BW x BH voxels of one (image, z) plane, BW * BH
+// = 128 = the MMA's M.  For each of the 27 taps the tensor-memory
+// accelerator copies the box shifted by the tap from the channels-last
+// input straight into shared memory.  32 channels: one copy of 128 rows x
+// 64 bytes with the 64-byte swizzle, which is the MMA's K-major 64-byte
+// swizzled layout (8-row atoms of 512 bytes; the second K step of 16
+// channels starts 32 bytes into the row).  8 channels: one copy of 128 rows
+// x 16 bytes, the canonical no-swizzle K-major layout (8 x 16-byte core
+// matrices stacked along M, SBO = 128 bytes), K 8..15 read from a zero
+// block (LBO = its distance).  The copy engine moves a box row by row, so
+// wide rows (one 64-byte row per voxel rather than four 16-byte ones) keep
+// it off the critical path.  Out-of-range
+// coordinates read as zero, which is the convolution's zero padding, so no
+// thread gathers anything.  Warp roles (192 threads): warp 4 lane 0 issues
+// the copies into a ring of STAGES buffers of GROUP taps each, warp 5 lane 0
+// issues the MMAs (a buffer is free again once its MMAs complete: one
+// tcgen05.commit per buffer, since a commit per tap costs more than the tap),
+// and warps 0-3 read the accumulator (one tensor-memory lane per thread)
+// while the next tile accumulates into the second of two accumulators.
+// Every wait is bounded; a give-up raises the block's abort flag, the copy
+// warp waits for its copies still in flight and the MMA warp for its last
+// MMAs, and the kernel records the condition for rmrtlb_cnn_check.
+// Buffers in the copy ring and taps per buffer (a divisor of 27: the MMAs of
+// one buffer are committed once, and a commit is not free); overridable with
+// -D to compare alternatives.  Measured on GB300 (4 x 32 x 64 x 64 voxels,
+// microseconds for 8->32 / 32->32 / 32->4): 1 tap x 6 buffers 150 / 185 /
+// 167; 3 x 2: 124 / 141 / 97; 3 x 3: 123 / 128 / 95; 9 x 2: 123 / 126 / 72.
+#ifndef RMRT_TMA_STAGES_K8
+#define RMRT_TMA_STAGES_K8 2
+#endif
+#ifndef RMRT_TMA_STAGES_K32
+#define RMRT_TMA_STAGES_K32 2
+#endif
+#ifndef RMRT_TMA_GROUP_K8
+#define RMRT_TMA_GROUP_K8 9
+#endif
+#ifndef RMRT_TMA_GROUP_K32
+#define RMRT_TMA_GROUP_K32 9
+#endif
+template <int KIN, int NOUT>
+struct TmaShape {
+  static constexpr int KP = KIN < 16 ? 16 : KIN;      // K per tap, padded to the MMA's 16
+  static constexpr int NP = NOUT < 16 ? 16 : NOUT;
+  static constexpr int KC = KP / 8;                   // 16-byte chunks of K
+  // 32 channels: one copy per tap of 128 rows x 64 bytes, 64-byte swizzle;
+  // 8 channels: one copy of 128 rows x 16 bytes (no swizzle) plus a zero block for K 8..15
+  static constexpr bool SW64 = KIN == 32;
+  static constexpr int LOADED = SW64 ? 1 : KIN / 8;   // copies per tap
+  static constexpr int CHUNK = SW64 ? 128 * 64 : 128 * 16;
+  static constexpr int TAP = LOADED * CHUNK;          // bytes of one tap's A tile
+  static constexpr int GROUP = KIN == 8 ? RMRT_TMA_GROUP_K8 : RMRT_TMA_GROUP_K32;   // taps per buffer
+  static constexpr int STAGE = GROUP * TAP;
+  static constexpr int STAGES = KIN == 8 ? RMRT_TMA_STAGES_K8 : RMRT_TMA_STAGES_K32;
+  static_assert(27 % GROUP == 0, "taps per buffer must divide 27");
+  static constexpr int B_TAP = NP * KP * 2;
+  static constexpr int OFF_B = STAGES * STAGE;
+  static constexpr int OFF_ZERO = OFF_B + 27 * B_TAP;
+  static constexpr int ZERO = (!SW64 && LOADED < KC) ? CHUNK : 0;
+  static constexpr int OFF_BAR = OFF_ZERO + ZERO;
+  static constexpr int NBAR = 2 * STAGES + 4;
+  static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16 + 1024;   // + room to align the base to 1024
+};
+constexpr int kTmaThreads = 192;
+constexpr uint32_t kTmaWaitLimit = 1u << 22;   // polls before a role of the copy-fed kernel gives up
+
+// Bounded wait that also gives up as soon as another role raised `abort`.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (uint32_t i = 0; i < kTmaWaitLimit; i += 64) {
+    if (tc::mbar_wait(bar, parity, 64)) return true;
+    if (*abort) return false;
+  }
+  return false;
+}
+
+struct TileAt {
+  int n, z, y0, x0;
+};
+__device__ __forceinline__ TileAt tile_at(long long tile, const Vol& g, int bw, int bh, int tx_n, int ty_n) {
+  TileAt t;
+  t.x0 = int(tile % tx_n) * bw;
+  long long r = tile / tx_n;
+  t.y0 = int(r % ty_n) * bh;
+  r /= ty_n;
+  t.z = int(r % g.d);
+  t.n = int(r / g.d);
+  return t;
+}
+
+template <int KIN, int NOUT>
+__global__ void __launch_bounds__(kTmaThreads) conv_tma_kernel(const __grid_constant__ CUtensorMap tmap, Vol g,
+                                                               int bw, int bh, const uint16_t* __restrict__ wt,
+                                                               const float* __restrict__ bias, int apply_silu,
+                                                               float* __restrict__ zout, uint16_t* __restrict__ aout) {
+  using S = TmaShape<KIN, NOUT>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t* As = smem;
+  uint8_t* Bs = smem + S::OFF_B;
+  uint8_t* Zs = smem + S::OFF_ZERO;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
+  uint64_t* empty = full + S::STAGES;
+  uint64_t* accf = empty + S::STAGES;    // accumulator a written (the MMAs of a tile complete)
+  uint64_t* acce = accf + 2;             // accumulator a read out by the four epilogue warps
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 2);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // weights of every tap, B_t[n][k] K-major in 8 x 16-byte core matrices; the zero block
+  for (int i = tid; i < 27 * S::NP * S::KP; i += kTmaThreads) {
+    const int t = i / (S::NP * S::KP), rem = i % (S::NP * S::KP), n = rem / S::KP, k = rem % S::KP;
+    const uint16_t val = (n < NOUT && k < KIN) ? wt[(size_t(t) * KIN + k) * NOUT + n] : uint16_t(0);
+    *reinterpret_cast<uint16_t*>(Bs + t * S::B_TAP + ((n >> 3) * S::KC + (k >> 3)) * 128 + (n & 7) * 16 +
+                                 (k & 7) * 2) = val;
+  }
+  for (int i = tid; i < S::ZERO / 16; i += kTmaThreads) reinterpret_cast<uint4*>(Zs)[i] = make_uint4(0, 0, 0, 0);
+  if (warp == 5) tc::tmem_alloc(tslot, 64);
+  if (tid == 0) {
+    for (int k = 0; k < S::STAGES; ++k) {
+      tc::mbar_init(&full[k], 1);
+      tc::mbar_init(&empty[k], 1);
+    }
+    tc::mbar_init(&accf[0], 1);
+    tc::mbar_init(&accf[1], 1);
+    tc::mbar_init(&acce[0], 4);
+    tc::mbar_init(&acce[1], 4);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = *tslot;
+  const int tx_n = (g.w + bw - 1) / bw, ty_n = (g.h + bh - 1) / bh;
+  const long long tiles = (long long)g.n * g.d * ty_n * tx_n;
+
+  if (warp == 4) {
+    if (lane == 0) {                       // copies
+      uint32_t it = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const TileAt p = tile_at(tile, g, bw, bh, tx_n, ty_n);
+        for (int t0 = 0; t0 < 27; t0 += S::GROUP) {
+          const int st = int(it % S::STAGES);
+          const uint32_t round = it / S::STAGES;
+          if (round > 0 && !mbar_wait_or_abort(&empty[st], (round - 1) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_expect_tx(&full[st], S::STAGE);
+#pragma unroll
+          for (int g2 = 0; g2 < S::GROUP; ++g2) {
+            const int t = t0 + g2, dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+#pragma unroll
+            for (int c = 0; c < S::LOADED; ++c)
+              tc::tma_load_5d(As + st * S::STAGE + g2 * S::TAP + c * S::CHUNK, &tmap, &full[st],
+                              (S::SW64 ? 32 : 8) * c, p.x0 + dx, p.y0 + dy, p.z + dz, p.n);
+          }
+          ++it;
+        }
+      }
+      if (!ok) {
+        *abort = 1;
+        atomicExch(&g_tc_error, 1);
+      }
+      // no copy may still be writing shared memory when the block exits
+      for (uint32_t k = it > uint32_t(S::STAGES) ? it - S::STAGES : 0; k < it; ++k)
+        tc::mbar_wait(&full[k % S::STAGES], (k / S::STAGES) & 1, kTmaWaitLimit);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {                       // MMAs
+      const uint32_t idesc = tc::idesc_bf16(S::NP);
+      uint32_t it = 0, j = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++j) {
+        const uint32_t a = j & 1;
+        if (j >= 2 && !mbar_wait_or_abort(&acce[a], ((j >> 1) - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        for (int t0 = 0; t0 < 27; t0 += S::GROUP) {
+          const int st = int(it % S::STAGES);
+          if (!mbar_wait_or_abort(&full[st], (it / S::STAGES) & 1, abort)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+#pragma unroll
+          for (int g2 = 0; g2 < S::GROUP; ++g2) {
+            const int t = t0 + g2;
+            const uint32_t abase = tc::smem_u32(As + st * S::STAGE + g2 * S::TAP);
+#pragma unroll
+            for (int kk = 0; kk < S::KP / 16; ++kk) {
+              uint64_t ad;
+              if constexpr (S::SW64) {
+                ad = tc::smem_desc_sw64(abase + 32 * kk, 512);
+              } else {
+                const uint32_t a0 = abase + 2 * kk * S::CHUNK;
+                const uint32_t lbo = S::ZERO ? tc::smem_u32(Zs) - a0 : uint32_t(S::CHUNK);
+                ad = tc::smem_desc(a0, lbo, 128);
+              }
+              const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + t * S::B_TAP) + kk * 256, 128, S::KC * 128);
+              tc::mma_bf16(taddr + a * 32, ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          tc::mma_commit(&empty[st]);      // the buffer is free once these MMAs have read it
+          ++it;
+        }
+        if (ok) tc::mma_commit(&accf[a]);
+      }
+      if (!ok) {
+        *abort = 1;
+        atomicExch(&g_tc_error, 1);
+      }
+      // the last MMAs must have completed before the accumulators are released
+      if (it > 0) tc::mbar_wait(&empty[(it - 1) % S::STAGES], ((it - 1) / S::STAGES) & 1, kTmaWaitLimit);
+    }
+  } else {                                 // epilogue: warps 0-3, thread = row = tensor-memory lane
+    uint32_t j = 0;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++j) {
+      const uint32_t a = j & 1;
+      int ok = 1;
+      if (lane == 0) ok = int(mbar_wait_or_abort(&accf[a], (j >> 1) & 1, abort));
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) {
+          *abort = 1;
+          atomicExch(&g_tc_error, 1);
+        }
+        break;
+      }
+      tc::fence_after();
+      float acc[32];
+      const uint32_t ta = taddr + (uint32_t(warp * 32) << 16) + a * 32;
+      tc::tmem_ld16(ta, *reinterpret_cast<float(*)[16]>(acc));
+      if constexpr (S::NP == 32) tc::tmem_ld16(ta + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[a]);
+      const TileAt p = tile_at(tile, g, bw, bh, tx_n, ty_n);
+      const int y = p.y0 + tid / bw, x = p.x0 + tid % bw;
+      if (y < g.h && x < g.w) {
+        const long long v = (((long long)p.n * g.d + p.z) * g.h + y) * g.w + x;
+#pragma unroll
+        for (int n = 0; n < NOUT; ++n) acc[n] += bias[n];
+        if (zout) {
+          float4* zo = reinterpret_cast<float4*>(zout + v * NOUT);
+#pragma unroll
+          for (int q = 0; q < NOUT / 4; ++q)
+            zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+        if (aout) {
+          uint32_t* ao = reinterpret_cast<uint32_t*>(aout + v * NOUT);
+#pragma unroll
+          for (int q = 0; q < NOUT / 2; ++q) {
+            float p0 = acc[2 * q], p1 = acc[2 * q + 1];
+            if (apply_silu) {
+              p0 *= sigm(p0);
+              p1 *= sigm(p1);
+            }
+            ao[q] = uint32_t(f2bf(p0)) | (uint32_t(f2bf(p1)) << 16);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc::fence_after();
+    tc::tmem_dealloc(taddr, 64);
+  }
 }
 
 // ------------------------------------------------------------------ backward weight
@@ -545,6 +822,86 @@ int launch_tc(Vol g, const void* in, const uint16_t* w, const float* bias, const
   return status_of(cudaGetLastError());
 }
 
+// cuTensorMapEncodeTiled of the driver, found through the runtime (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Output box of the copy-fed kernel: BW x BH = 128 voxels, BW a power of
+// two, BW <= w and BH <= h, the one covering the plane with the fewest
+// padded voxels; false when the plane is too small for any (the gathering
+// kernel then runs).
+bool pick_box(const Vol& g, int& bw, int& bh) {
+  bool found = false;
+  long long best = 0;
+  for (int b = 128; b >= 8; b >>= 1) {
+    const int c = 128 / b;
+    if (b > g.w || c > g.h) continue;
+    const long long cover = (long long)((g.w + b - 1) / b) * b * ((g.h + c - 1) / c) * c;
+    if (!found || cover < best) {
+      found = true;
+      best = cover;
+      bw = b;
+      bh = c;
+    }
+  }
+  return found;
+}
+
+template <int KIN, int NOUT>
+int launch_tma(Vol g, const uint16_t* x, const uint16_t* w, const float* bias, int silu, float* z, uint16_t* a,
+               cudaStream_t s) {
+  using S = TmaShape<KIN, NOUT>;
+  int bw = 0, bh = 0;
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc || !pick_box(g, bw, bh)) return launch_tc<KIN, NOUT, 0>(g, x, w, bias, nullptr, silu, z, a, s);
+  // channels-last BF16 input as a 5-D tensor (c, x, y, z, image); boxes of all 32 channels (64-byte
+  // swizzle) or of the 8 channels x BW x BH
+  CUtensorMap tm;
+  const cuuint64_t dims[5] = {cuuint64_t(KIN), cuuint64_t(g.w), cuuint64_t(g.h), cuuint64_t(g.d), cuuint64_t(g.n)};
+  const cuuint64_t row = cuuint64_t(KIN) * 2;
+  const cuuint64_t strides[4] = {row, row * cuuint64_t(g.w), row * cuuint64_t(g.w) * g.h,
+                                 row * cuuint64_t(g.w) * g.h * g.d};
+  const cuuint32_t box[5] = {S::SW64 ? 32u : 8u, cuuint32_t(bw), cuuint32_t(bh), 1, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t*>(x), dims, strides, box, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, S::SW64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return RMRTLB_ECUDA;
+  // the opt-in to more than 48 KB of shared memory holds per device: set it on every call
+  if (cudaFuncSetAttribute(conv_tma_kernel<KIN, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
+      cudaSuccess)
+    return RMRTLB_ECUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<KIN, NOUT>, kTmaThreads, S::SMEM) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const long long tiles = (long long)g.n * g.d * ((g.h + bh - 1) / bh) * ((g.w + bw - 1) / bw);
+  const long long cap = (long long)per_sm * sm_count();
+  const unsigned grid = unsigned(tiles < cap ? tiles : cap);
+  conv_tma_kernel<KIN, NOUT><<<grid, kTmaThreads, S::SMEM, s>>>(tm, g, bw, bh, w, bias, silu, z, a);
+  return status_of(cudaGetLastError());
+}
+
 int chunks_of(Vol g) { return int((g.voxels() + kWeightChunk - 1) / kWeightChunk); }
 
 template <int CIN, int COUT>
@@ -589,9 +946,9 @@ int rmrtlb_conv3d_forward(int n, int d, int h, int w, int cin, int cout, const u
   if ((z && !aligned16(z)) || (a && (reinterpret_cast<size_t>(a) & 7))) return RMRTLB_EINVAL;
   const Vol g{n, d, h, w};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cin == 8 && cout == 32) return launch_tc<8, 32, 0>(g, x, weight, bias, nullptr, apply_silu, z, a, s);
-  if (cin == 32 && cout == 32) return launch_tc<32, 32, 0>(g, x, weight, bias, nullptr, apply_silu, z, a, s);
-  if (cin == 32 && cout == 4) return launch_tc<32, 4, 0>(g, x, weight, bias, nullptr, apply_silu, z, a, s);
+  if (cin == 8 && cout == 32) return launch_tma<8, 32>(g, x, weight, bias, apply_silu, z, a, s);
+  if (cin == 32 && cout == 32) return launch_tma<32, 32>(g, x, weight, bias, apply_silu, z, a, s);
+  if (cin == 32 && cout == 4) return launch_tma<32, 4>(g, x, weight, bias, apply_silu, z, a, s);
   return RMRTLB_EINVAL;
 }
 

@@ -38,6 +38,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return d;
 }
 
+// The same for a K-major operand stored with the 64-byte swizzle (rows of
+// 64 bytes, 8-row atoms of 512 bytes, as the tensor-memory accelerator's
+// 64-byte swizzle writes them): SBO = the stride between 8-row atoms, LBO
+// unused (one K step of 16 elements lies within a row), layout type 4.  A K
+// step inside the row advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((addr & 0x3FFFF) >> 4);
+  d |= uint64_t(1) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
+  d |= uint64_t(1) << 46;
+  d |= uint64_t(4) << 61;
+  return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
 // K-major (or, with mn_major, both MN-major), M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n, bool mn_major = false) {
@@ -92,6 +107,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+// Tensor-memory accelerator: arm `bar` for `bytes` of incoming copies (one
+// arrival), then a 5-D tiled copy of the box at coordinates c0..c4 (c0
+// innermost; out-of-range elements read as zero) into shared memory, whose
+// completion is counted on `bar`.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(void* dst, const void* tmap, uint64_t* bar, int c0, int c1, int c2, int c3,
+                                            int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // 32 lanes x 32b, 16 or 32 consecutive columns: thread i of the warp gets

@@ -63,6 +63,34 @@ def test_conv_forward(cin, cout, silu):
     assert np.abs(host(a) - ao).max() <= 2.0 ** -7 * np.abs(ao).max()
 
 
+# Planes large enough for the copy-fed kernel (boxes of 16 x 8, 64 x 2,
+# 8 x 16 and 128 x 1 voxels; ragged in x, in y and in both).
+TMA_SHAPES = [(2, 3, 9, 20), (1, 2, 16, 64), (1, 1, 130, 8), (1, 2, 3, 200)]
+
+
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("cin,cout", PAIRS)
+@pytest.mark.parametrize("silu", [True, False])
+def test_conv_forward_copy_fed(shape, cin, cout, silu):
+    import torch
+    from paper_2206_00366_gb300 import rmrtlb as B
+    n, d, h, w = shape
+    rng = np.random.default_rng(cin + 3 * cout + h)
+    xg, x = bf16(rng.normal(size=(n, d, h, w, cin)))
+    wg, wv = bf16(rng.normal(scale=0.2, size=(27, cin, cout)))
+    b = rng.normal(size=cout).astype(np.float32)
+    z = torch.empty((n, d, h, w, cout), dtype=torch.float32, device="cuda")
+    a = torch.empty((n, d, h, w, cout), dtype=torch.bfloat16, device="cuda")
+    bt = dev(b, torch.float32)
+    B.rmrtlb_conv3d_forward(n, d, h, w, cin, cout, xg.data_ptr(), wg.data_ptr(), bt.data_ptr(),
+                            silu, z.data_ptr(), a.data_ptr())
+    B.rmrtlb_cnn_check()
+    zo = C.conv3d(x, wv, b.astype(np.float64))
+    assert normwise(host(z), zo) <= 1e-5
+    ao = C.silu(zo) if silu else zo
+    assert np.abs(host(a) - ao).max() <= 2.0 ** -7 * np.abs(ao).max()
+
+
 def test_bounded_wait_gives_up_and_reports_timeout():
     """Failure detection without a GPU fault: an mbarrier that nothing
     arrives on, waited for with the convolutions' bounded polling, gives up
