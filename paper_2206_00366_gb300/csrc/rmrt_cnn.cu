@@ -70,7 +70,13 @@ struct TcShape {
   static constexpr int NP = NOUT < 16 ? 16 : NOUT;   // N padded to 16 (M = 128 needs N % 16 == 0)
   static constexpr int KC = KP / 8;                  // core matrices along K
   static constexpr int B_TAP = NP * KP * 2;          // bytes of one tap's weights
-  static constexpr int A_BUF = 128 * KP * 2;         // bytes of one A buffer
+  // taps per A buffer (one commit per buffer): three for rows of up to 8
+  // channels; one for 32-channel rows, whose gather (FP32 rows of 128 bytes
+  // in the input gradient) is the bound and wants the occupancy instead
+  // (measured, 32 -> 32 input gradient: 608 us with one, 819 us with three)
+  static constexpr int GROUP = KIN >= 32 ? 1 : 3;
+  static constexpr int A_TAP = 128 * KP * 2;         // bytes of one tap's A tile
+  static constexpr int A_BUF = GROUP * A_TAP;        // bytes of one A buffer
   static constexpr int SMEM = 27 * B_TAP + 2 * A_BUF + 64;
 };
 
@@ -118,7 +124,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
 
   const long long V = g.voxels();
   const long long tiles = (V + 127) / 128;
-  uint32_t T = 0;   // taps issued by this CTA (selects the A buffer and the barrier phase)
+  uint32_t T = 0;   // tap groups issued by this CTA (selects the A buffer and the barrier phase)
   bool ok = true;
   // raw neighbour row of one tap: BF16 (MODE 0) or FP32 (MODE 1) values
   using Raw = typename std::conditional<MODE == 0, uint4, float4>::type;
@@ -145,49 +151,62 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
     const long long v = tile * 128 + tid;
     const bool valid = v < V;
     const VoxCoord c = coord_of(valid ? v : 0, g);
-    Raw raw[NRAW1];
-    bool present;
-    load_row(c, valid, 0, raw, present);   // tap 0; tap t + 1 is loaded while tap t is issued
-    for (int t = 0; t < 27; ++t, ++T) {
+    Raw raw[S::GROUP][NRAW1];
+    bool present[S::GROUP];
+    // the rows of group 0; the rows of group k + 1 are loaded while group k is issued
+#pragma unroll
+    for (int gg = 0; gg < S::GROUP; ++gg) load_row(c, valid, gg, raw[gg], present[gg]);
+    for (int t0 = 0; t0 < 27; t0 += S::GROUP, ++T) {
       const int b = int(T & 1);
-      // buffer b is free once the MMAs of tap T - 2 have completed
+      // buffer b is free once the MMAs of group T - 2 have completed
       if (tid == 0) s_ok = T < 2 ? 1 : int(tc::mbar_wait(&bar[b], ((T - 2) >> 1) & 1, kWaitLimit));
       __syncthreads();
       if (!s_ok) { ok = false; break; }
-      uint4 row[S::KC];
-#pragma unroll
-      for (int q = 0; q < S::KC; ++q) row[q] = make_uint4(0, 0, 0, 0);
-      if (present) {
-        if constexpr (MODE == 0) {
-#pragma unroll
-          for (int q = 0; q < NRAW; ++q) row[q] = raw[q];
-        } else {
-          uint32_t pk[S::KP / 2];
-#pragma unroll
-          for (int q = 0; q < S::KP / 2; ++q) pk[q] = 0;
-#pragma unroll
-          for (int q = 0; q < NRAW; ++q) {
-            pk[2 * q] = uint32_t(f2bf(raw[q].x)) | (uint32_t(f2bf(raw[q].y)) << 16);
-            pk[2 * q + 1] = uint32_t(f2bf(raw[q].z)) | (uint32_t(f2bf(raw[q].w)) << 16);
-          }
-#pragma unroll
-          for (int q = 0; q < S::KC; ++q) row[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-        }
-      }
       uint8_t* Ab = As + b * S::A_BUF;
 #pragma unroll
-      for (int q = 0; q < S::KC; ++q)
-        *reinterpret_cast<uint4*>(Ab + ((tid >> 3) * S::KC + q) * 128 + (tid & 7) * 16) = row[q];
-      if (t + 1 < 27) load_row(c, valid, t + 1, raw, present);
+      for (int gg = 0; gg < S::GROUP; ++gg) {
+        uint4 row[S::KC];
+#pragma unroll
+        for (int q = 0; q < S::KC; ++q) row[q] = make_uint4(0, 0, 0, 0);
+        if (present[gg]) {
+          if constexpr (MODE == 0) {
+#pragma unroll
+            for (int q = 0; q < NRAW; ++q) row[q] = raw[gg][q];
+          } else {
+            uint32_t pk[S::KP / 2];
+#pragma unroll
+            for (int q = 0; q < S::KP / 2; ++q) pk[q] = 0;
+#pragma unroll
+            for (int q = 0; q < NRAW; ++q) {
+              pk[2 * q] = uint32_t(f2bf(raw[gg][q].x)) | (uint32_t(f2bf(raw[gg][q].y)) << 16);
+              pk[2 * q + 1] = uint32_t(f2bf(raw[gg][q].z)) | (uint32_t(f2bf(raw[gg][q].w)) << 16);
+            }
+#pragma unroll
+            for (int q = 0; q < S::KC; ++q)
+              row[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < S::KC; ++q)
+          *reinterpret_cast<uint4*>(Ab + gg * S::A_TAP + ((tid >> 3) * S::KC + q) * 128 + (tid & 7) * 16) = row[q];
+      }
+      if (t0 + S::GROUP < 27) {
+#pragma unroll
+        for (int gg = 0; gg < S::GROUP; ++gg) load_row(c, valid, t0 + S::GROUP + gg, raw[gg], present[gg]);
+      }
       tc::fence_async_smem();
       __syncthreads();
       if (tid == 0) {
         tc::fence_after();
 #pragma unroll
-        for (int kk = 0; kk < S::KP / 16; ++kk) {
-          const uint64_t ad = tc::smem_desc(tc::smem_u32(Ab) + kk * 256, 128, S::KC * 128);
-          const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + t * S::B_TAP) + kk * 256, 128, S::KC * 128);
-          tc::mma_bf16(taddr, ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+        for (int gg = 0; gg < S::GROUP; ++gg) {
+          const int t = t0 + gg;
+#pragma unroll
+          for (int kk = 0; kk < S::KP / 16; ++kk) {
+            const uint64_t ad = tc::smem_desc(tc::smem_u32(Ab + gg * S::A_TAP) + kk * 256, 128, S::KC * 128);
+            const uint64_t bd = tc::smem_desc(tc::smem_u32(Bs + t * S::B_TAP) + kk * 256, 128, S::KC * 128);
+            tc::mma_bf16(taddr, ad, bd, idesc, (t > 0 || kk > 0) ? 1u : 0u);
+          }
         }
         tc::mma_commit(&bar[b]);
       }

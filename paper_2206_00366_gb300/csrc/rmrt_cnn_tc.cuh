@@ -1,14 +1,17 @@
 // Implicit-GEMM 3 x 3 x 3 convolution on the fifth-generation tensor cores
 // (tcgen05.mma, kind::f16, BF16 operands, FP32 accumulator in tensor memory).
 //
-// One CTA of 128 threads owns one tensor-memory accumulator of 128 lanes x
-// NP columns and walks output tiles of 128 consecutive voxels (grid-stride).
-// For each of the 27 taps the threads gather their voxel's neighbour row
-// (K channels, BF16; zero outside the volume) into shared memory in the
-// canonical no-swizzle K-major layout (8 x 16-byte core matrices), one
-// thread issues the MMAs of that tap (K = 16 per instruction) and commits
-// them to an mbarrier; two A buffers alternate, so the gather of tap t + 1
-// overlaps the MMAs of tap t.  All 27 weight slices stay in shared memory.
+// Gathering kernel (the input gradient, and the forward pass on planes too
+// small for the copy-fed kernel): one CTA of 128 threads owns one
+// tensor-memory accumulator of 128 lanes x NP columns and walks output tiles
+// of 128 consecutive voxels (grid-stride).  For each group of taps (three
+// for narrow rows, one for 32-channel rows) the threads gather their voxel's
+// neighbour rows (K channels, BF16; zero outside the volume) into shared
+// memory in the canonical no-swizzle K-major layout (8 x 16-byte core
+// matrices), one thread issues the MMAs of the group (K = 16 per
+// instruction) and commits them to an mbarrier once; two A buffers
+// alternate, so the gather of group k + 1 overlaps the MMAs of group k.  All
+// 27 weight slices stay in shared memory.
 // The epilogue reads the accumulator with tcgen05.ld (one lane, i.e. one
 // voxel, per thread).
 //
