@@ -41,14 +41,23 @@ int rmrtlb_conv3d_forward(int n, int d, int h, int w, int cin, int cout,
                           const uint16_t* x, const uint16_t* weight, const float* bias,
                           int apply_silu, float* z, uint16_t* a, void* stream);
 
+/* Bytes of device scratch rmrtlb_conv3d_backward_data can use (host only):
+ * a BF16 copy of dy when cout = 32 and the plane holds a 128-voxel box (the
+ * copy-fed kernel then runs), else 0. */
+size_t rmrtlb_conv3d_backward_data_scratch(int n, int d, int h, int w, int cin, int cout);
+
 /* Gradient with respect to the input, channel pairs (32, 32), (32, 4):
  * dx[v, ci] = sum_t sum_co dy[v - tap_t, co] w[t, ci, co], multiplied by
  * silu'(z_in[v, ci]) when z_in (the FP32 pre-activation that produced x)
  * is not NULL; the same tensor-core implicit GEMM with dy rounded to BF16
- * (nearest even) on the way in.  dy, z_in, dx FP32. */
+ * (nearest even).  dy, z_in, dx FP32.  With `scratch` (device, 16-byte
+ * aligned, at least rmrtlb_conv3d_backward_data_scratch bytes) dy is first
+ * rounded into it and the kernel is fed by the tensor-memory accelerator;
+ * with NULL (or a short scratch) the threads gather and round dy
+ * themselves.  Both give the same result. */
 int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout,
                                 const float* dy, const uint16_t* weight, const float* z_in,
-                                float* dx, void* stream);
+                                float* dx, void* scratch, size_t scratch_bytes, void* stream);
 
 /* Bytes of device scratch rmrtlb_conv3d_backward_weight needs (host only). */
 size_t rmrtlb_conv3d_backward_weight_scratch(int n, int d, int h, int w, int cin, int cout);

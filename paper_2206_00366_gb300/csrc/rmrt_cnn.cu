@@ -352,10 +352,15 @@ __device__ __forceinline__ TileAt tile_at(long long tile, const Vol& g, int bw, 
   return t;
 }
 
-template <int KIN, int NOUT>
+// MODE 0: forward (in: BF16 x; out: z = acc + bias in FP32 and a = silu(z)
+// or z in BF16).  MODE 1: input gradient of a layer with cin = NOUT, cout =
+// KIN (in: dy rounded to BF16 beforehand; taps mirrored, weights read as
+// w[t, n, k]; out: dx = acc * silu'(zin) or acc, FP32).
+template <int KIN, int NOUT, int MODE>
 __global__ void __launch_bounds__(kTmaThreads) conv_tma_kernel(const __grid_constant__ CUtensorMap tmap, Vol g,
                                                                int bw, int bh, const uint16_t* __restrict__ wt,
                                                                const float* __restrict__ bias, int apply_silu,
+                                                               const float* __restrict__ zin,
                                                                float* __restrict__ zout, uint16_t* __restrict__ aout) {
   using S = TmaShape<KIN, NOUT>;
   extern __shared__ uint8_t smem_raw[];
@@ -374,7 +379,9 @@ __global__ void __launch_bounds__(kTmaThreads) conv_tma_kernel(const __grid_cons
   // weights of every tap, B_t[n][k] K-major in 8 x 16-byte core matrices; the zero block
   for (int i = tid; i < 27 * S::NP * S::KP; i += kTmaThreads) {
     const int t = i / (S::NP * S::KP), rem = i % (S::NP * S::KP), n = rem / S::KP, k = rem % S::KP;
-    const uint16_t val = (n < NOUT && k < KIN) ? wt[(size_t(t) * KIN + k) * NOUT + n] : uint16_t(0);
+    uint16_t val = 0;
+    if (n < NOUT && k < KIN)
+      val = MODE == 0 ? wt[(size_t(t) * KIN + k) * NOUT + n] : wt[(size_t(t) * NOUT + n) * KIN + k];
     *reinterpret_cast<uint16_t*>(Bs + t * S::B_TAP + ((n >> 3) * S::KC + (k >> 3)) * 128 + (n & 7) * 16 +
                                  (k & 7) * 2) = val;
   }
@@ -416,7 +423,8 @@ __global__ void __launch_bounds__(kTmaThreads) conv_tma_kernel(const __grid_cons
           tc::mbar_expect_tx(&full[st], S::STAGE);
 #pragma unroll
           for (int g2 = 0; g2 < S::GROUP; ++g2) {
-            const int t = t0 + g2, dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+            const int t = t0 + g2, sg = MODE == 0 ? 1 : -1;   // the input gradient reads v - tap
+            const int dz = sg * (t / 9 - 1), dy = sg * ((t / 3) % 3 - 1), dx = sg * (t % 3 - 1);
 #pragma unroll
             for (int c = 0; c < S::LOADED; ++c)
               tc::tma_load_5d(As + st * S::STAGE + g2 * S::TAP + c * S::CHUNK, &tmap, &full[st],
@@ -506,7 +514,21 @@ __global__ void __launch_bounds__(kTmaThreads) conv_tma_kernel(const __grid_cons
       if (lane == 0) tc::mbar_arrive(&acce[a]);
       const TileAt p = tile_at(tile, g, bw, bh, tx_n, ty_n);
       const int y = p.y0 + tid / bw, x = p.x0 + tid % bw;
-      if (y < g.h && x < g.w) {
+      if (MODE == 1 && y < g.h && x < g.w) {
+        const long long v = (((long long)p.n * g.d + p.z) * g.h + y) * g.w + x;
+        if (zin) {
+          const float* zr = zin + v * NOUT;
+#pragma unroll
+          for (int n = 0; n < NOUT; ++n) {
+            const float zz = zr[n], sgm = sigm(zz);
+            acc[n] *= sgm * (1.0f + zz * (1.0f - sgm));
+          }
+        }
+        float4* dxo = reinterpret_cast<float4*>(zout + v * NOUT);
+#pragma unroll
+        for (int q = 0; q < NOUT / 4; ++q)
+          dxo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+      } else if (MODE == 0 && y < g.h && x < g.w) {
         const long long v = (((long long)p.n * g.d + p.z) * g.h + y) * g.w + x;
 #pragma unroll
         for (int n = 0; n < NOUT; ++n) acc[n] += bias[n];
@@ -883,33 +905,35 @@ bool pick_box(const Vol& g, int& bw, int& bh) {
   return found;
 }
 
-template <int KIN, int NOUT>
-int launch_tma(Vol g, const uint16_t* x, const uint16_t* w, const float* bias, int silu, float* z, uint16_t* a,
-               cudaStream_t s) {
-  using S = TmaShape<KIN, NOUT>;
-  int bw = 0, bh = 0;
+// Tensor map of a channels-last BF16 tensor (c, x, y, z, image) for boxes
+// of all 32 channels (64-byte swizzle) or of 8 channels, BW x BH voxels.
+template <int KIN>
+bool make_tmap(CUtensorMap* tm, const Vol& g, const uint16_t* x, int bw, int bh) {
   const EncodeTiledFn enc = encode_tiled();
-  if (!enc || !pick_box(g, bw, bh)) return launch_tc<KIN, NOUT, 0>(g, x, w, bias, nullptr, silu, z, a, s);
-  // channels-last BF16 input as a 5-D tensor (c, x, y, z, image); boxes of all 32 channels (64-byte
-  // swizzle) or of the 8 channels x BW x BH
-  CUtensorMap tm;
+  if (!enc) return false;
+  constexpr bool sw64 = TmaShape<KIN, 32>::SW64;
   const cuuint64_t dims[5] = {cuuint64_t(KIN), cuuint64_t(g.w), cuuint64_t(g.h), cuuint64_t(g.d), cuuint64_t(g.n)};
   const cuuint64_t row = cuuint64_t(KIN) * 2;
   const cuuint64_t strides[4] = {row, row * cuuint64_t(g.w), row * cuuint64_t(g.w) * g.h,
                                  row * cuuint64_t(g.w) * g.h * g.d};
-  const cuuint32_t box[5] = {S::SW64 ? 32u : 8u, cuuint32_t(bw), cuuint32_t(bh), 1, 1};
+  const cuuint32_t box[5] = {sw64 ? 32u : 8u, cuuint32_t(bw), cuuint32_t(bh), 1, 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t*>(x), dims, strides, box, es,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, S::SW64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
-          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return RMRTLB_ECUDA;
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<uint16_t*>(x), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int KIN, int NOUT, int MODE>
+int run_tma(const CUtensorMap& tm, Vol g, int bw, int bh, const uint16_t* w, const float* bias, int silu,
+            const float* zin, float* z, uint16_t* a, cudaStream_t s) {
+  using S = TmaShape<KIN, NOUT>;
   // the opt-in to more than 48 KB of shared memory holds per device: set it on every call
-  if (cudaFuncSetAttribute(conv_tma_kernel<KIN, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
+  if (cudaFuncSetAttribute(conv_tma_kernel<KIN, NOUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
       cudaSuccess)
     return RMRTLB_ECUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<KIN, NOUT>, kTmaThreads, S::SMEM) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<KIN, NOUT, MODE>, kTmaThreads,
+                                                    S::SMEM) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
@@ -917,8 +941,36 @@ int launch_tma(Vol g, const uint16_t* x, const uint16_t* w, const float* bias, i
   const long long tiles = (long long)g.n * g.d * ((g.h + bh - 1) / bh) * ((g.w + bw - 1) / bw);
   const long long cap = (long long)per_sm * sm_count();
   const unsigned grid = unsigned(tiles < cap ? tiles : cap);
-  conv_tma_kernel<KIN, NOUT><<<grid, kTmaThreads, S::SMEM, s>>>(tm, g, bw, bh, w, bias, silu, z, a);
+  conv_tma_kernel<KIN, NOUT, MODE><<<grid, kTmaThreads, S::SMEM, s>>>(tm, g, bw, bh, w, bias, silu, zin, z, a);
   return status_of(cudaGetLastError());
+}
+
+template <int KIN, int NOUT>
+int launch_tma(Vol g, const uint16_t* x, const uint16_t* w, const float* bias, int silu, float* z, uint16_t* a,
+               cudaStream_t s) {
+  int bw = 0, bh = 0;
+  CUtensorMap tm;
+  if (!pick_box(g, bw, bh) || !make_tmap<KIN>(&tm, g, x, bw, bh))
+    return launch_tc<KIN, NOUT, 0>(g, x, w, bias, nullptr, silu, z, a, s);
+  return run_tma<KIN, NOUT, 0>(tm, g, bw, bh, w, bias, silu, nullptr, z, a, s);
+}
+
+// FP32 -> BF16 (nearest even), count a multiple of 4.
+__global__ void to_bf16_kernel(long long count4, const float4* __restrict__ in, uint2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count4;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = in[i];
+    out[i] = make_uint2(uint32_t(f2bf(v.x)) | (uint32_t(f2bf(v.y)) << 16),
+                        uint32_t(f2bf(v.z)) | (uint32_t(f2bf(v.w)) << 16));
+  }
+}
+
+// Scratch of the copy-fed input gradient: a BF16 copy of dy (32 channels,
+// planes that hold a 128-voxel box), else none.
+size_t bwd_data_scratch(const Vol& g, int cout) {
+  int bw = 0, bh = 0;
+  if (cout != 32 || !pick_box(g, bw, bh)) return 0;
+  return size_t(g.voxels()) * 32 * 2;
 }
 
 int chunks_of(Vol g) { return int((g.voxels() + kWeightChunk - 1) / kWeightChunk); }
@@ -971,12 +1023,32 @@ int rmrtlb_conv3d_forward(int n, int d, int h, int w, int cin, int cout, const u
   return RMRTLB_EINVAL;
 }
 
+size_t rmrtlb_conv3d_backward_data_scratch(int n, int d, int h, int w, int cin, int cout) {
+  if (!vol_ok(n, d, h, w) || cin != 32) return 0;
+  return bwd_data_scratch(Vol{n, d, h, w}, cout);
+}
+
 int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout, const float* dy,
-                                const uint16_t* weight, const float* z_in, float* dx, void* stream) {
+                                const uint16_t* weight, const float* z_in, float* dx, void* scratch,
+                                size_t scratch_bytes, void* stream) {
   if (!vol_ok(n, d, h, w) || !aligned16(dy) || !weight || !aligned16(dx)) return RMRTLB_EINVAL;
   const Vol g{n, d, h, w};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cin == 32 && cout == 32) return launch_tc<32, 32, 1>(g, dy, weight, nullptr, z_in, 0, dx, nullptr, s);
+  if (cin == 32 && cout == 32) {
+    const size_t need = bwd_data_scratch(g, cout);
+    int bw = 0, bh = 0;
+    CUtensorMap tm;
+    uint16_t* dy16 = static_cast<uint16_t*>(scratch);
+    if (need && scratch && aligned16(scratch) && scratch_bytes >= need && pick_box(g, bw, bh) &&
+        make_tmap<32>(&tm, g, dy16, bw, bh)) {
+      const long long count4 = g.voxels() * 32 / 4;
+      const unsigned grid = blocks_for(count4, 256) < 8192u ? blocks_for(count4, 256) : 8192u;
+      to_bf16_kernel<<<grid, 256, 0, s>>>(count4, reinterpret_cast<const float4*>(dy), reinterpret_cast<uint2*>(dy16));
+      if (cudaGetLastError() != cudaSuccess) return RMRTLB_ECUDA;
+      return run_tma<32, 32, 1>(tm, g, bw, bh, weight, nullptr, 0, z_in, dx, nullptr, s);
+    }
+    return launch_tc<32, 32, 1>(g, dy, weight, nullptr, z_in, 0, dx, nullptr, s);
+  }
   if (cin == 32 && cout == 4) return launch_tc<4, 32, 1>(g, dy, weight, nullptr, z_in, 0, dx, nullptr, s);
   return RMRTLB_EINVAL;
 }

@@ -121,7 +121,8 @@ def lib() -> ctypes.CDLL:
                                     sz, _vp]),
         "rmrtlb_batch_run": (i, [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
         "rmrtlb_conv3d_forward": (i, [i, i, i, i, i, i, _vp, _vp, _vp, i, _vp, _vp, _vp]),
-        "rmrtlb_conv3d_backward_data": (i, [i, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp]),
+        "rmrtlb_conv3d_backward_data": (i, [i, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+        "rmrtlb_conv3d_backward_data_scratch": (ctypes.c_size_t, [i, i, i, i, i, i]),
         "rmrtlb_conv3d_backward_weight_scratch": (sz, [i, i, i, i, i, i]),
         "rmrtlb_conv3d_backward_weight": (i, [i, i, i, i, i, i, _vp, _vp, _vp, _vp, _vp, sz, _vp]),
         "rmrtlb_mse": (i, [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -160,7 +161,8 @@ def exported_symbols() -> list:
             "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
             "rmrtlb_batch_tune", "rmrtlb_batch_set_launch", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
             "rmrtlb_batch_get_populations", "rmrtlb_batch_fields", "rmrtlb_batch_run", "rmrtlb_batch_init_fields",
-            "rmrtlb_conv3d_forward", "rmrtlb_conv3d_backward_data", "rmrtlb_conv3d_backward_weight_scratch",
+            "rmrtlb_conv3d_forward", "rmrtlb_conv3d_backward_data", "rmrtlb_conv3d_backward_data_scratch",
+            "rmrtlb_conv3d_backward_weight_scratch",
             "rmrtlb_conv3d_backward_weight", "rmrtlb_mse", "rmrtlb_adam", "rmrtlb_cavity_features",
             "rmrtlb_upsample_fields", "rmrtlb_pack_fields", "rmrtlb_cnn_check", "rmrtlb_cnn_wait_selftest"]
 
@@ -340,9 +342,14 @@ def rmrtlb_conv3d_forward(n, d, h, w, cin, cout, x, weight, bias, apply_silu, z,
            "rmrtlb_conv3d_forward")
 
 
-def rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dy, weight, z_in, dx, stream=0):
-    _check(lib().rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dy, weight, z_in, dx, stream),
-           "rmrtlb_conv3d_backward_data")
+def rmrtlb_conv3d_backward_data_scratch(n, d, h, w, cin, cout) -> int:
+    return int(lib().rmrtlb_conv3d_backward_data_scratch(n, d, h, w, cin, cout))
+
+
+def rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dy, weight, z_in, dx, scratch=None, scratch_bytes=0,
+                                stream=0):
+    _check(lib().rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dy, weight, z_in, dx, scratch, scratch_bytes,
+                                             stream), "rmrtlb_conv3d_backward_data")
 
 
 def rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, cout) -> int:

@@ -143,6 +143,9 @@ class Net:
         self.g = [torch.empty(V * 32, dtype=torch.float32, device=dev) for _ in range(2)]
         sb = max(B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, CH[k], CH[k + 1]) for k in range(4))
         self.scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+        # BF16 copy of dy for the copy-fed input gradient (0 bytes where it does not apply)
+        sd = max(B.rmrtlb_conv3d_backward_data_scratch(n, d, h, w, CH[k], CH[k + 1]) for k in range(1, 4))
+        self.scratch_dy = torch.empty(max(sd, 16), dtype=torch.uint8, device=dev)
         self.re = torch.empty(n, dtype=torch.float64, device=dev)
         self._shape = (n,) + tuple(shape)
 
@@ -180,7 +183,8 @@ class Net:
             if k > 0:
                 nxt = self.g[k % 2]
                 B.rmrtlb_conv3d_backward_data(n, d, h, w, CH[k], CH[k + 1], _ptr(g), self.w16(k),
-                                              _ptr(self.z[k - 1]), _ptr(nxt))
+                                              _ptr(self.z[k - 1]), _ptr(nxt), _ptr(self.scratch_dy),
+                                              self.scratch_dy.numel())
                 g = nxt
         self.step_count += 1
         B.rmrtlb_adam(self.master.numel(), _ptr(self.master), _ptr(self.bf16), _ptr(self.grad), _ptr(self.m),

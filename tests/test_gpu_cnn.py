@@ -39,6 +39,9 @@ def host(t):
 
 PAIRS = [(8, 32), (32, 32), (32, 4)]
 SHAPE = (2, 5, 6, 13)   # 780 voxels: several 128-voxel blocks and a ragged tail
+# Planes large enough for the copy-fed kernels (boxes of 16 x 8, 64 x 2,
+# 8 x 16 and 128 x 1 voxels; ragged in x, in y and in both).
+TMA_SHAPES = [(2, 3, 9, 20), (1, 2, 16, 64), (1, 1, 130, 8), (1, 2, 3, 200)]
 
 
 @pytest.mark.parametrize("cin,cout", PAIRS)
@@ -61,11 +64,6 @@ def test_conv_forward(cin, cout, silu):
     assert normwise(host(z), zo) <= 1e-5
     ao = C.silu(zo) if silu else zo
     assert np.abs(host(a) - ao).max() <= 2.0 ** -7 * np.abs(ao).max()
-
-
-# Planes large enough for the copy-fed kernel (boxes of 16 x 8, 64 x 2,
-# 8 x 16 and 128 x 1 voxels; ragged in x, in y and in both).
-TMA_SHAPES = [(2, 3, 9, 20), (1, 2, 16, 64), (1, 1, 130, 8), (1, 2, 3, 200)]
 
 
 @pytest.mark.parametrize("shape", TMA_SHAPES)
@@ -121,19 +119,28 @@ def test_bounded_wait_gives_up_and_reports_timeout():
 
 @pytest.mark.parametrize("cin,cout", [(32, 32), (32, 4)])
 @pytest.mark.parametrize("with_z", [True, False])
-def test_conv_backward_data(cin, cout, with_z):
+@pytest.mark.parametrize("shape,use_scratch", [(SHAPE, False), (SHAPE, True)] + [(s, True) for s in TMA_SHAPES]
+                         + [(TMA_SHAPES[0], False)])
+def test_conv_backward_data(cin, cout, with_z, shape, use_scratch):
+    """Thread-gathering kernel (no scratch, or a plane too small for a box)
+    and, with a scratch for the BF16 copy of dy and cout = 32, the copy-fed
+    kernel with mirrored taps."""
     import torch
     from paper_2206_00366_gb300 import rmrtlb as B
-    n, d, h, w = SHAPE
-    rng = np.random.default_rng(7 + cout)
+    n, d, h, w = shape
+    rng = np.random.default_rng(7 + cout + h)
     dy = rng.normal(size=(n, d, h, w, cout)).astype(np.float32)
     zin = rng.normal(size=(n, d, h, w, cin)).astype(np.float32)
     wg, wv = bf16(rng.normal(scale=0.2, size=(27, cin, cout)))
     dx = torch.empty((n, d, h, w, cin), dtype=torch.float32, device="cuda")
     zt = dev(zin, torch.float32)
     dyt = dev(dy, torch.float32)
+    sb = B.rmrtlb_conv3d_backward_data_scratch(n, d, h, w, cin, cout) if use_scratch else 0
+    assert (sb > 0) == (use_scratch and cout == 32 and shape != SHAPE)
+    sc = torch.empty(max(sb, 16), dtype=torch.uint8, device="cuda")
     B.rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dyt.data_ptr(), wg.data_ptr(),
-                                  zt.data_ptr() if with_z else None, dx.data_ptr())
+                                  zt.data_ptr() if with_z else None, dx.data_ptr(),
+                                  sc.data_ptr() if use_scratch else None, sb)
     B.rmrtlb_cnn_check()
     dyb = torch.tensor(dy).to(torch.bfloat16).to(torch.float64).numpy()   # the tensor cores take BF16
     ref = C.conv3d_backward_data(dyb, wv)

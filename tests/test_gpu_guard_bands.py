@@ -148,6 +148,25 @@ def test_convolution_writes_stay_in_their_outputs(cin, cout):
         B.rmrtlb_conv3d_backward_data(n, d, h, w, cin, cout, dy.data_ptr(), wt.data_ptr(), 0, dx_p)
         B.rmrtlb_cnn_check()
         assert_bands(dx_t, v * cin * 4)
+    # the copy-fed kernels (a plane that holds 16 x 8 boxes), output and dy scratch guarded
+    n2, d2, h2, w2 = 1, 3, 9, 20
+    v2 = n2 * d2 * h2 * w2
+    x2 = torch.tensor(rng.normal(size=(v2, cin)), dtype=torch.bfloat16, device="cuda")
+    z2_t, z2_p = guarded(v2 * cout * 4)
+    a2_t, a2_p = guarded(v2 * cout * 2)
+    B.rmrtlb_conv3d_forward(n2, d2, h2, w2, cin, cout, x2.data_ptr(), wt.data_ptr(), bias.data_ptr(), 1, z2_p, a2_p)
+    B.rmrtlb_cnn_check()
+    assert_bands(z2_t, v2 * cout * 4)
+    assert_bands(a2_t, v2 * cout * 2)
+    if cin == 32:
+        dy2 = torch.tensor(rng.normal(size=(v2, cout)), dtype=torch.float32, device="cuda")
+        sd = B.rmrtlb_conv3d_backward_data_scratch(n2, d2, h2, w2, cin, cout)
+        sd_t, sd_p = guarded(max(sd, 16))
+        dx2_t, dx2_p = guarded(v2 * cin * 4)
+        B.rmrtlb_conv3d_backward_data(n2, d2, h2, w2, cin, cout, dy2.data_ptr(), wt.data_ptr(), 0, dx2_p, sd_p, sd)
+        B.rmrtlb_cnn_check()
+        assert_bands(sd_t, max(sd, 16))
+        assert_bands(dx2_t, v2 * cin * 4)
     dy = torch.tensor(rng.normal(size=(v, cout)), dtype=torch.float32, device="cuda")
     sb = B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, cout)
     sc_t, sc_p = guarded(sb)
