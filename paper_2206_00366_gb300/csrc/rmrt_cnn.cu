@@ -27,7 +27,6 @@ struct Vol {
   __host__ __device__ long long voxels() const { return (long long)n * d * h * w; }
 };
 
-__device__ __forceinline__ float bf2f(uint16_t b) { return __uint_as_float(uint32_t(b) << 16); }
 __device__ __forceinline__ uint16_t f2bf(float f) {
   const __nv_bfloat16 h = __float2bfloat16_rn(f);
   return *reinterpret_cast<const uint16_t*>(&h);
