@@ -127,6 +127,29 @@ def test_batch_converges_and_retires():
     assert u[0, 0, -1, :].mean() > 0
 
 
+def test_batch_bench_workload_parity_on_every_domain():
+    """The 512 seeded cavities the bench times (37.5 M nodes), in the launch
+    shape the tuner picks for them (CUDA graphs, automatic node pairing):
+    every domain starts from seeded random populations near rest and
+    matches the oracle stepping it alone after two steps, and keeps its
+    mass (walls and a tangential lid conserve it)."""
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    doms = W.cavity_domains(512, seed=4)
+    b = Batch(doms, storage="f32", check_every=1000000, tol=1e-9)
+    b.tune(2)
+    f0 = []
+    for k, d in enumerate(doms):
+        lat = R.make_lattice("D2Q9", (d["dx"], d["dy"]))
+        f0.append(W.random_populations(9, (1, d["ny"], d["nx"]), seed=100 + k, amp=0.02, base=lat.w.reshape(9)))
+        b.set_populations(k, f0[k])
+    b.step(2)
+    for k, d in enumerate(doms):
+        fg = b.get_populations(k)
+        fo, _ = oracle_domain(d, 2, f0[k])
+        assert normwise(fg, fo) <= 1e-5, k
+        assert abs(fg.sum() / f0[k].sum() - 1.0) <= 1e-6, k
+
+
 def test_batch_tune_picks_a_width_and_resets():
     from paper_2206_00366_gb300.rmrtlb import Batch
     doms = W.cavity_domains(20, seed=4, size=(20, 80))
