@@ -5,9 +5,8 @@ the oracle legs of ``bench.py`` may import it; it shares nothing with the
 CUDA library.
 
 The paper has no learned component: its RMRT-LB step is the solver whose
-steady states the network learns to predict, and the solver stays the judge
-of every warm-started run (the run is accepted only when its own residual
-converges).  Everything here is a plain textbook definition, written out
+steady states the network learns to predict, and a warm-started run is
+accepted only when the solver's own residual converges.  Everything here is a plain textbook definition, written out
 loop by loop over the 27 taps with numpy matrix products over channels:
 
 * 3-D cross-correlation with a 3 x 3 x 3 kernel and zero padding ("same"
