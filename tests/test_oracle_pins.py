@@ -1050,6 +1050,22 @@ def test_simple_ncde_needs_the_dBdt_term():
     assert e < 0.02 and e < 0.4 * e_no, (e, e_no)
 
 
+@pytest.mark.parametrize("name", ["D2Q9", "D3Q19", "D3Q27"])
+def test_sampled_step_equals_the_full_step(name):
+    """collide_stream_at (the oracle at selected nodes, for full-size
+    checks) equals one full periodic step at every node of a small field."""
+    dx = (1.0, 0.7, 0.55)
+    lat = R.make_lattice(name, dx[: 2 if name == "D2Q9" else 3])
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, 0.03, 0.05, 1.1))
+    m = R.Model(R.NSE, force=(1e-4, -2e-4, 1e-4), source=2e-5)
+    shape = (1, 5, 6) if name == "D2Q9" else (3, 4, 5)
+    f = W.random_populations(lat.q, shape, seed=9)
+    full = R.step(lat, m, S, f, 1)
+    nodes = np.array([(z, y, x) for z in range(shape[0]) for y in range(shape[1]) for x in range(shape[2])])
+    got = R.collide_stream_at(lat, m, S, f, nodes)
+    np.testing.assert_allclose(got, full.reshape(lat.q, -1), rtol=0, atol=1e-15)
+
+
 # ---------------------------------------------------------------- the auxiliary distribution G with a source
 def _collide_without_G(lat, m, S, fl):
     """A planted mistake: the oracle's raw-basis collision with G dropped."""
