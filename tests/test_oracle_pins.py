@@ -658,6 +658,152 @@ def test_sound_wave_speed_and_bulk_attenuation():
     assert abs(2 * half / period - 1) < 0.02
 
 
+# ---------------------------------------------------------------- 3-D S_2 block and bulk viscosity
+SPACING_3D = (1.0, 0.8, 0.5)
+
+
+def shear_wave_rate_3d(lat, S, shape, kidx, pol, steps=300):
+    """Decay rate / k^2 of a plane shear wave u = pol A sin(k . x) on a
+    periodic (nx, ny, nz) box, k_a = 2 pi kidx_a / (n_a dx_a); pol is
+    perpendicular to k (a divergence-free wave)."""
+    nx, ny, nz = shape
+    X, Y, Z = W.grid((nz, ny, nx), lat.dx)
+    k = np.array([2 * np.pi * kidx[a] / (shape[a] * lat.dx[a]) for a in range(3)])
+    pol = np.asarray(pol, dtype=np.float64)
+    assert abs(pol @ k) < 1e-12
+    ph = k[0] * X + k[1] * Y + k[2] * Z
+    amp = 1e-3
+    u = np.stack([pol[a] * amp * np.sin(ph) for a in range(3)])
+    m = R.Model()
+    f = R.init_equilibrium(lat, m, S, np.ones((nz, ny, nx)), u)
+    basis = np.sin(ph)
+
+    def amp_of(f):
+        uu = R.fields(lat, m, f)[1]
+        return mode_amp(sum(pol[a] * uu[a] for a in range(3)), basis)
+    f = R.step(lat, m, S, f, 100)
+    a0 = amp_of(f)
+    f = R.step(lat, m, S, f, steps)
+    a1 = amp_of(f)
+    return -np.log(a1 / a0) / steps / (k @ k)
+
+
+def xz_diagonal_wave():
+    """A shear wave along the physical diagonal of the xz plane (24 nodes at
+    dx = 1 and 48 at dz = 0.5 per wavelength; the second-order truncation
+    error of the decay rate is then about 0.6%), polarised in that plane:
+    its stress has normal components on x and z, so it runs through the
+    dense S_2 block."""
+    k = np.array([2 * np.pi / 24, 0.0, 2 * np.pi / 24])
+    return (24, 2, 48), (1, 0, 1), (-k[2] / np.hypot(k[0], k[2]), 0.0, k[0] / np.hypot(k[0], k[2]))
+
+
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q27"])
+def test_shear_wave_isotropy_3d(name):
+    """rD3Q19 and rD3Q27 with dx = 1, dy = 0.8, dz = 0.5: shear waves along z
+    (x-polarised), along the xz diagonal (polarised in the xz plane and
+    along y) all decay at the one nu of Eq. (4-31) within 1%."""
+    lat = R.make_lattice(name, SPACING_3D)
+    nu = 0.01
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, 0.03, 1.1))
+    shape, kidx, pol = xz_diagonal_wave()
+    for shp, kk, pp in [((2, 2, 48), (0, 0, 1), (1.0, 0.0, 0.0)), (shape, kidx, pol), (shape, kidx, (0.0, 1.0, 0.0))]:
+        assert abs(shear_wave_rate_3d(lat, S, shp, kk, pp) / nu - 1) < 0.01, (shp, pp)
+
+
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q27"])
+def test_shear_wave_3d_detects_single_rate_s2(name):
+    """Planted mistake: normal stresses relaxed at the off-diagonal rate (one
+    viscous rate for every second moment) leave the z-axis wave untouched
+    but make the xz-diagonal wave decay at a wrong rate."""
+    lat = R.make_lattice(name, SPACING_3D)
+    nu = 0.01
+    r = R.rates_from_viscosity(lat, nu, 0.03, 1.1)
+    r.s_shear = np.full(3, r.s_off[0, 1])
+    r.s_bulk = np.full(3, r.s_off[0, 1])
+    S = R.relaxation_matrix(lat, r)
+    shape, kidx, pol = xz_diagonal_wave()
+    assert abs(shear_wave_rate_3d(lat, S, shape, kidx, pol) / nu - 1) > 0.2
+
+
+def sound_wave_3d(lat, S, axis, n=64, periods=4):
+    """Energy decay rate / k^2 and period / (2 pi / (c_s k)) of a plane sound
+    wave along one axis of a 3-D box (two nodes on the other axes)."""
+    shape = [2, 2, 2]
+    shape[axis] = n
+    nx, ny, nz = shape
+    X = W.grid((nz, ny, nx), lat.dx)[axis]
+    k = 2 * np.pi / (n * lat.dx[axis])
+    amp = 1e-4
+    u = np.zeros((3, nz, ny, nx))
+    u[axis] = amp * np.sin(k * X)
+    m = R.Model()
+    f = R.init_equilibrium(lat, m, S, np.ones((nz, ny, nx)), u)
+    period = 2 * np.pi / (np.sqrt(lat.cs2) * k)
+    nsteps = int(round(periods * period))
+    E, A = [], []
+    for _ in range(nsteps + 1):
+        rho, uu = R.fields(lat, m, f)
+        a = mode_amp(uu[axis], np.sin(k * X))
+        b = mode_amp(rho - 1, np.cos(k * X))
+        E.append(a * a + lat.cs2 * b * b)
+        A.append(a)
+        f = R.step(lat, m, S, f, 1)
+    slope = np.polyfit(np.arange(nsteps + 1), np.log(E), 1)[0]
+    A = np.array(A)
+    zc = np.where(np.diff(np.sign(A)) != 0)[0]
+    return -slope / (k * k), 2 * np.mean(np.diff(zc)) / period
+
+
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q27"])
+def test_sound_wave_3d_bulk_attenuation(name):
+    """Plane sound waves along x and along z (dz = 0.5) propagate at c_s and
+    their energy decays at k^2 [2 nu (1 - 1/d) + nu_b] with d = 3 (Eqs.
+    4-24-3, 4-31b): pins nu_b and the z-axis entries of the S_2 block."""
+    lat = R.make_lattice(name, SPACING_3D)
+    nu, nub = 0.01, 0.04
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, nub, 1.1))
+    nuL = 2 * nu * (1 - 1 / 3) + nub
+    for axis in (0, 2):
+        g, per = sound_wave_3d(lat, S, axis)
+        assert abs(g / nuL - 1) < 0.015, axis
+        assert abs(per - 1) < 0.01, axis
+
+
+def _s2_block_with(d_in_rank_one=None, z_axis_c2_from=None):
+    """A copy of the oracle's S_2 block with one planted change: the rank-one
+    term divided by `d_in_rank_one` instead of d, or a_z built with the
+    (c^2 - c_s^2) of another axis."""
+    def block(lat, r):
+        c2 = lat.c * lat.c - lat.cs2
+        a = (1.0 / r.s_bulk - 1.0 / r.s_shear) * c2
+        if z_axis_c2_from is not None:
+            a = a.copy()
+            a[2] = (1.0 / r.s_bulk[2] - 1.0 / r.s_shear[2]) * c2[z_axis_c2_from]
+        d = lat.d if d_in_rank_one is None else d_in_rank_one
+        return np.linalg.inv(np.diag(1.0 / r.s_shear) + np.outer(a, 1.0 / c2) / d)
+    return block
+
+
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q27"])
+def test_3d_pins_detect_planted_s2_mistakes(name, monkeypatch):
+    """The 3-D pins see a wrong 1/d in Eq. (4-27-1) (the sound attenuation is
+    30% off) and a z-axis a_z built with c_x (the z sound wave decays several
+    times too fast and the xz-diagonal shear wave more than 2% off, beyond
+    the 1% of the isotropy pin)."""
+    lat = R.make_lattice(name, SPACING_3D)
+    nu, nub = 0.01, 0.04
+    nuL = 2 * nu * (1 - 1 / 3) + nub
+    monkeypatch.setattr(R, "s2_diag_block", _s2_block_with(d_in_rank_one=2))
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, nub, 1.1))
+    assert abs(sound_wave_3d(lat, S, 0)[0] / nuL - 1) > 0.2
+    monkeypatch.setattr(R, "s2_diag_block", _s2_block_with(z_axis_c2_from=0))
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, nu, nub, 1.1))
+    assert abs(sound_wave_3d(lat, S, 2)[0] / nuL - 1) > 0.5
+    shape, kidx, pol = xz_diagonal_wave()
+    assert abs(shear_wave_rate_3d(lat, S, shape, kidx, pol) / nu - 1) > 0.015
+
+
 def test_poiseuille_profile():
     """Force-driven channel between resting walls (y axis, half-way
     bounce-back): the steady profile is u = F/(2 rho nu) (y+dy/2)(H-y-dy/2)
