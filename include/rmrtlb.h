@@ -108,15 +108,29 @@ enum rmrtlb_basis {
 };
 
 /* Population storage.  Every kind stores the deviation fbar_j - omega_j rho0;
- * F16 stores it times the power of two nearest 1/omega_j (exact to apply
- * and undo, keeps small-weight populations out of FP16's subnormals); BF16
- * has FP32's exponent range and stores it unscaled; both round to nearest
- * even on every store.  F64 computes in FP64, the others in FP32. */
+ * F64 computes in FP64, the others in FP32.
+ *   F16:   IEEE binary16 of the deviation times the power of two nearest
+ *          1/omega_j (exact to apply and undo, keeps small-weight
+ *          populations out of FP16's subnormals).
+ *   BF16:  bfloat16 of the deviation, unscaled (FP32's exponent range).
+ *   E3M12: a 16-bit float with a sign, 3 exponent bits and 12 mantissa
+ *          bits, with subnormals, of the deviation times the same power of
+ *          two as F16, in a range R set by rmrtlb_params.storage_range (a
+ *          power of two, default 2 for the NSE and 8 for the NCDE): 4x
+ *          FP16's resolution for scaled magnitudes in [R/128, R), a fixed
+ *          spacing of R * 2^-19 below.  Magnitudes that round beyond R
+ *          saturate; the check then reports RMRTLB_EUNSTABLE with flag 8.
+ * The 16-bit kinds round stochastically in rmrtlb_step (the rounding
+ * error has mean zero and is not repeated from step to step; the random
+ * bits come from a counter-based generator of the step index and the node,
+ * so runs are reproducible) and to nearest even when populations are set
+ * or initialised. */
 enum rmrtlb_storage {
     RMRTLB_ST_F64 = 0,
     RMRTLB_ST_F32 = 1,
     RMRTLB_ST_F16 = 2,
-    RMRTLB_ST_BF16 = 3
+    RMRTLB_ST_BF16 = 3,
+    RMRTLB_ST_E3M12 = 4
 };
 
 /* ------------------------------------------------------------ parameters */
@@ -143,6 +157,16 @@ typedef struct {
     int check_every;     /* rmrtlb_step runs the FP64 check (mass, momentum,
                             residual, stability flags) every check_every
                             steps; 0 disables it */
+    double storage_range;/* E3M12 storage: the scaled deviation
+                            (fbar_j - omega_j rho0) * 2^round(-log2 omega_j)
+                            is stored in a range that ends at the power of two
+                            at or above storage_range (values that round
+                            beyond it saturate and the check reports flag 8);
+                            the format's resolution scales with the range.
+                            <= 0 selects 2 for the NSE kinds (flows up to a
+                            Mach number of about 0.3) and 8 for the NCDE
+                            kinds (phi - rho0 of order 1).  Ignored by the
+                            other storages. */
 } rmrtlb_params;
 
 typedef struct rmrtlb_solver* rmrtlb_t;   /* opaque, library-owned */
@@ -232,7 +256,8 @@ int rmrtlb_stress(rmrtlb_t solver, double* stress, double* strain_rate);
  *   out[4] kinetic energy sum rho |u|^2 / 2    out[5] residual
  *          ||u - u_prev||_2 / ||u||_2 against the previous check (-1 if
  *          there was none)                     out[6] step counter
- *   out[7] flags: 1 NaN/Inf, 2 density <= 0, 4 |u| >= c_s.
+ *   out[7] flags: 1 NaN/Inf, 2 density <= 0, 4 |u| >= c_s, 8 an E3M12
+ *          population saturated (scaled magnitude 8 or more).
  * Returns RMRTLB_EUNSTABLE when a flag is set (out is still filled). */
 int rmrtlb_stats(rmrtlb_t solver, double out[8]);
 
@@ -362,18 +387,34 @@ int rmrtlb_batch_fields(rmrtlb_batch_t batch, int domain, double* rho, double* u
  *   out[0] = sum_x sum_j f_j            out[1..3] = sum_x sum_j c_j f_j
  *   out[4] = sum_x |sum_j c_j f_j|^2 / (2 sum_j f_j)
  * for populations f given as q FP64 planes in rmrtlb_lattice_info order
- * (device memory, e.g. filled by rmrtlb_get_populations); for an unforced
- * NSE state these are the mass, momentum and kinetic energy that
- * rmrtlb_stats reports.  out may be host or device memory (host: the call
- * synchronises the stream).  No solver and no workspace are needed: the
- * reduction scratch is a fixed array of (4096 * 8 + 8) doubles inside the
- * library, present on every GPU that loads it until the process exits.  At
- * most RMRTLB_NOALLOC_MAX_NODES nodes (nx*ny*nz) are accepted; larger grids
- * return RMRTLB_ETOOBIG.  The first call on a device looks the array up on
- * that device; make that first call before any stream capture.  All calls
- * share the array: calls whose kernels overlap on the GPU (unordered
- * streams) race and may return wrong totals; calls on one stream are
- * ordered.  Calls no cudaMalloc or cudaFree. */
+ * (device memory of the current device, e.g. filled by
+ * rmrtlb_get_populations).  Only RMRTLB_D2Q9, RMRTLB_D3Q19 and RMRTLB_D3Q27
+ * are accepted; the axis-only lattices return RMRTLB_EINVAL.  f must hold
+ * full populations (not deviations from a rest state); a node whose mass
+ * sum_j f_j is exactly zero adds nothing to out[4].  For an unforced NSE
+ * state these are the mass, momentum and kinetic energy that rmrtlb_stats
+ * reports.
+ *   out: host memory -> the totals are copied back and the call
+ *        synchronises the stream before it returns; such a call cannot be
+ *        captured into a CUDA graph, and during an active capture of the
+ *        stream it returns RMRTLB_EINVAL without enqueueing anything.
+ *        Device or managed memory of the current device -> the call is
+ *        asynchronous: out is written in stream order, so synchronise the
+ *        stream before reading a managed out on the host.
+ * f or a device out on another GPU than the current one -> RMRTLB_EINVAL.
+ * No solver and no workspace are needed: the reduction scratch is a fixed
+ * array of (4096 * 8 + 8) doubles inside the library, present on every GPU
+ * that loads it until the process exits.  At most RMRTLB_NOALLOC_MAX_NODES
+ * nodes (nx*ny*nz) are accepted; larger grids return RMRTLB_ETOOBIG.  The
+ * first call on a device looks the array up on that device and keeps its
+ * address for the rest of the process; make that first call before any
+ * stream capture, and do not call this entry point again on a device after
+ * cudaDeviceReset (the kept address belonged to the destroyed context).  A
+ * CUDA error left pending by earlier, unrelated work is returned as
+ * RMRTLB_ECUDA before anything is launched, and is left pending for its
+ * owner.  All calls share the array: calls whose kernels overlap on the GPU
+ * (unordered streams) race and may return wrong totals; calls on one stream
+ * are ordered.  Calls no cudaMalloc or cudaFree. */
 #define RMRTLB_NOALLOC_MAX_NODES 67108864LL
 int rmrtlb_population_totals_noalloc(int lattice, int nx, int ny, int nz,
                                      double dx, double dy, double dz, double dt,

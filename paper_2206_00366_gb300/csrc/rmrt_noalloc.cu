@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(NA_THREADS) totals_kernel(const double* __rest
     });
     acc[0] += m0;
     acc[1] += m1[0]; acc[2] += m1[1]; acc[3] += m1[2];
-    acc[4] += 0.5 * (m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2]) / m0;
+    if (m0 != 0.0) acc[4] += 0.5 * (m1[0] * m1[0] + m1[1] * m1[1] + m1[2] * m1[2]) / m0;
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k)
@@ -120,13 +120,21 @@ cudaError_t scratch_on_current_device(double** out) {
   return cudaSuccess;
 }
 
-bool device_accessible(const void* p) {
+enum Where { HOST_MEMORY, THIS_DEVICE, OTHER_DEVICE };
+
+// Where a pointer lives relative to the current device dev: device memory
+// of dev and managed memory (the kernels reach both from dev) are
+// THIS_DEVICE, device memory of another GPU is OTHER_DEVICE, pageable and
+// pinned host memory are HOST_MEMORY.
+Where where_is(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+    cudaGetLastError();   // the query's own error: unregistered host memory on old runtimes
+    return HOST_MEMORY;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return THIS_DEVICE;
+  if (at.type == cudaMemoryTypeDevice) return at.device == dev ? THIS_DEVICE : OTHER_DEVICE;
+  return HOST_MEMORY;
 }
 
 }  // namespace
@@ -140,10 +148,22 @@ extern "C" int rmrtlb_population_totals_noalloc(int lattice, int nx, int ny, int
   if (!(dt > 0) || !(dx > 0) || !(dy > 0) || (lattice != RMRTLB_D2Q9 && !(dz > 0))) return RMRTLB_EINVAL;
   const long long N = (long long)nx * ny * nz;
   if (N > NA_MAX_NODES) return RMRTLB_ETOOBIG;
-  if (!device_accessible(f)) return RMRTLB_EINVAL;
+  // an error left pending by earlier work is not ours: report it, keep it
+  if (cudaPeekAtLastError() != cudaSuccess) return RMRTLB_ECUDA;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RMRTLB_ECUDA;
+  if (where_is(f, dev) != THIS_DEVICE) return RMRTLB_EINVAL;
+  const Where out_at = where_is(out, dev);
+  if (out_at == OTHER_DEVICE) return RMRTLB_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (out_at == HOST_MEMORY) {
+    // a host out needs a copy and a synchronisation, neither of which a capture may hold
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return RMRTLB_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return RMRTLB_EINVAL;
+  }
   double* scratch = nullptr;
   if (scratch_on_current_device(&scratch) != cudaSuccess) return RMRTLB_ECUDA;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nblk = int((N + NA_NODES_PER_BLOCK - 1) / NA_NODES_PER_BLOCK);
   const double cx = dx / dt, cy = dy / dt, cz = lattice == RMRTLB_D2Q9 ? 0.0 : dz / dt;
   switch (lattice) {
@@ -152,7 +172,7 @@ extern "C" int rmrtlb_population_totals_noalloc(int lattice, int nx, int ny, int
     default: totals_kernel<LAT_D3Q27><<<nblk, NA_THREADS, 0, s>>>(f, size_t(N), cx, cy, cz, scratch); break;
   }
   if (cudaGetLastError() != cudaSuccess) return RMRTLB_ECUDA;
-  const bool out_dev = device_accessible(out);
+  const bool out_dev = out_at == THIS_DEVICE;
   double* result = out_dev ? out : scratch + size_t(NA_MAX_BLOCKS) * 8;
   totals_finalize<<<1, NA_THREADS, 0, s>>>(scratch, nblk, result);
   if (cudaGetLastError() != cudaSuccess) return RMRTLB_ECUDA;
