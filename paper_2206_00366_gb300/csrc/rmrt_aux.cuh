@@ -114,7 +114,11 @@ __global__ void __launch_bounds__(CHECK_THREADS) check_kernel(
       const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
       const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
       const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
-      const CT dj = load_st<ST, CT>(fin + j * N + idx) * p.sinv[j];
+      const CT raw = load_st<ST, CT>(fin + j * N + idx);
+      if constexpr (std::is_same<ST, E3M12>::value) {
+        if ((__float_as_uint(raw) & 0x7FFFFFFFu) >= E3M12_MAX_W) flag |= 8;   // saturated code
+      }
+      const CT dj = raw * p.sinv[j];
       s0 += dj;
       if (ex) s1[0] += CT(ex) * dj;
       if (ey) s1[1] += CT(ey) * dj;

@@ -137,12 +137,12 @@ LaunchArgs base_args(rmrtlb_solver* s, Op op) {
 
 cudaError_t launch(rmrtlb_solver* s, const LaunchArgs& a) {
   using Fn = cudaError_t (*)(const LaunchArgs&);
-  static const Fn table[5][4] = {
-      {launch_d2q9_f64, launch_d2q9_f32, launch_d2q9_f16, launch_d2q9_bf16},
-      {launch_d3q19_f64, launch_d3q19_f32, launch_d3q19_f16, launch_d3q19_bf16},
-      {launch_d3q27_f64, launch_d3q27_f32, launch_d3q27_f16, launch_d3q27_bf16},
-      {launch_d2q5_f64, launch_d2q5_f32, launch_d2q5_f16, launch_d2q5_bf16},
-      {launch_d3q7_f64, launch_d3q7_f32, launch_d3q7_f16, launch_d3q7_bf16}};
+  static const Fn table[5][5] = {
+      {launch_d2q9_f64, launch_d2q9_f32, launch_d2q9_f16, launch_d2q9_bf16, launch_d2q9_e3m12},
+      {launch_d3q19_f64, launch_d3q19_f32, launch_d3q19_f16, launch_d3q19_bf16, launch_d3q19_e3m12},
+      {launch_d3q27_f64, launch_d3q27_f32, launch_d3q27_f16, launch_d3q27_bf16, launch_d3q27_e3m12},
+      {launch_d2q5_f64, launch_d2q5_f32, launch_d2q5_f16, launch_d2q5_bf16, launch_d2q5_e3m12},
+      {launch_d3q7_f64, launch_d3q7_f32, launch_d3q7_f16, launch_d3q7_bf16, launch_d3q7_e3m12}};
   return table[s->k.lat][s->k.storage](a);
 }
 
@@ -238,7 +238,7 @@ int rmrtlb_lattice_info(int lattice, int* q, int* d, int* e) {
 }
 
 int rmrtlb_workspace_bytes(int lattice, int nx, int ny, int nz, int storage, size_t* bytes) {
-  if (!bytes || !valid_dims(lattice, nx, ny, nz) || storage < 0 || storage > 3) return RMRTLB_EINVAL;
+  if (!bytes || !valid_dims(lattice, nx, ny, nz) || storage < 0 || storage > 4) return RMRTLB_EINVAL;
   *bytes = make_layout(lattice, nx, ny, nz, storage).total;
   return RMRTLB_OK;
 }
@@ -248,7 +248,7 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
                   size_t workspace_bytes, void* stream) {
   if (!solver || !params || !valid_dims(lattice, nx, ny, nz)) return RMRTLB_EINVAL;
   *solver = nullptr;
-  if (eq_kind < 0 || eq_kind > 5 || basis < 0 || basis > 3 || storage < 0 || storage > 3) return RMRTLB_EINVAL;
+  if (eq_kind < 0 || eq_kind > 5 || basis < 0 || basis > 3 || storage < 0 || storage > 4) return RMRTLB_EINVAL;
   if (!(dt > 0) || !(dx > 0) || !(dy > 0) || (lattice_d(lattice) == 3 && !(dz > 0))) return RMRTLB_EINVAL;
   if (!workspace || (reinterpret_cast<size_t>(workspace) % kAlign) != 0) return RMRTLB_EINVAL;
   const Layout L = make_layout(lattice, nx, ny, nz, storage);
@@ -274,7 +274,7 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
   s->check_every = params->check_every;
   s->pairs = (nx % 2 == 0) && !axis_lattice(lattice) && !simple_ncde(eq_kind);
   s->quads = s->pairs && nx % 4 == 0 &&
-             (storage == RMRTLB_ST_F16 || storage == RMRTLB_ST_BF16);
+             (storage == RMRTLB_ST_F16 || storage == RMRTLB_ST_BF16 || storage == RMRTLB_ST_E3M12);
   *solver = s;
   return RMRTLB_OK;
 }
@@ -398,6 +398,9 @@ int rmrtlb_step(rmrtlb_t s, int n) {
     }
     a.fin = pop_ptr(s, s->cur);
     a.fout = pop_ptr(s, 1 - s->cur);
+    // seed of the stochastic rounding of 16-bit stores: a function of the
+    // step index only, so a run is reproducible
+    s->kp32.seed = unsigned((unsigned long long)s->step * 0x9E3779B97F4A7C15ull >> 32);
     if (launch(s, a) != cudaSuccess) return RMRTLB_ECUDA;   // the parameters are copied at launch
     s->kp64.hist_fresh = s->kp32.hist_fresh = 0;
     s->cur = 1 - s->cur;

@@ -9,8 +9,9 @@
 // zeroing them before the inverse transform keeps the corners empty.
 //
 // Storage holds the scaled deviation s_j = (fbar_j - omega_j rho0) * sc_j,
-// sc_j the power of two nearest 1/omega_j for FP16 storage (exact to apply
-// and to undo) and 1 for the others;
+// sc_j the power of two nearest 1/omega_j for FP16 and E3M12 storage (exact
+// to apply and to undo; for E3M12 also times 2^(bias - 127), see E3M12
+// below) and 1 for the others;
 // every moment below is a moment of delta_j = fbar_j - omega_j rho0, so the
 // rest state never enters the arithmetic (m(omega rho0) = m^eq(rho0, 0, 0)).
 #pragma once
@@ -76,6 +77,69 @@ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 // ------------------------------------------------------------------ storage
+// E3M12: a 16-bit float with a sign bit, 3 exponent bits (bias 5) and 12
+// mantissa bits, with subnormals: 4x the resolution of FP16 for magnitudes
+// of the scaled deviation in [2^-4, 8), FP16's absolute resolution 2^-16
+// below, and saturation at 8 - 2^-10 (counted by the check kernel).  A
+// value x is held in FP32 as w = x * 2^(5 - 127) (the factor is folded into
+// the storage scale sc_j, its inverse into sinv_j), which places the E3M12
+// code of x, normal or subnormal, in bits 11..25 of w: decoding is a shift,
+// encoding a rounding at bit 11 and a shift.  The FP32 arithmetic that meets
+// w is compiled without flush-to-zero, so subnormal w are exact.
+struct E3M12 {
+  unsigned short b;
+};
+constexpr int E3M12_BIAS = 5;
+constexpr unsigned E3M12_MAX_W = 0x03FFF800u;    // FP32 bits of the largest code's w
+
+__device__ __forceinline__ float e3m12_decode(unsigned code) {
+  return __uint_as_float(((code & 0x7FFFu) << 11) | ((code & 0x8000u) << 16));
+}
+// Two codes of one 32-bit word (low half first) to FP32.
+__device__ __forceinline__ float2 e3m12_decode2(unsigned w) {
+  return make_float2(__uint_as_float(((w & 0x7FFFu) << 11) | ((w & 0x8000u) << 16)),
+                     __uint_as_float(((w >> 5) & 0x03FFF800u) | (w & 0x80000000u)));
+}
+// |w| bits plus the rounding increment, saturated at the largest code, as a
+// code magnitude in bits 11..25.
+__device__ __forceinline__ unsigned e3m12_mag(unsigned u, unsigned add) {
+  return min((u & 0x7FFFFFFFu) + add, 0x03FFFFFFu);
+}
+// Round to nearest, ties to even.
+__device__ __forceinline__ unsigned e3m12_encode_rn(float w) {
+  const unsigned u = __float_as_uint(w);
+  const unsigned a = e3m12_mag(u, 0x3FFu + ((u >> 11) & 1u));
+  return (a >> 11) | ((u >> 16) & 0x8000u);
+}
+// Stochastic rounding of two values into one word (x low half, y high
+// half): r supplies 11 random bits per value (bits 0..10 and 16..26); adding
+// them below bit 11 and truncating rounds up with probability equal to the
+// discarded fraction of a unit in the last place.
+__device__ __forceinline__ unsigned e3m12_encode2_sr(float x, float y, unsigned r) {
+  const unsigned ux = __float_as_uint(x), uy = __float_as_uint(y);
+  const unsigned ax = e3m12_mag(ux, r & 0x7FFu), ay = e3m12_mag(uy, (r >> 16) & 0x7FFu);
+  return (ax >> 11) | ((ux >> 16) & 0x8000u) | ((ay << 5) & 0x7FFF0000u) | (uy & 0x80000000u);
+}
+
+// Random bits for stochastic rounding: a 32-bit linear congruential state per
+// thread, seeded from the step's seed and the thread's first node, each
+// output xor-folded with its upper half (the upper bits of the state have the
+// long periods).  The rounding only needs bits that are uniform and
+// unrelated to the values rounded; the sequence is reproducible for a given
+// step and grid.
+struct SrBits {
+  unsigned s;
+  __device__ __forceinline__ explicit SrBits(unsigned seed, unsigned node) {
+    unsigned x = seed ^ (node * 0x9E3779B1u);
+    x ^= x >> 16; x *= 0x7FEB352Du; x ^= x >> 15; x *= 0x846CA68Bu; x ^= x >> 16;
+    s = x;
+  }
+  __device__ __forceinline__ unsigned next() {
+    s = s * 747796405u + 2891336453u;
+    return s ^ (s >> 16);
+  }
+};
+
 template <typename ST, typename CT> __device__ __forceinline__ CT load_st(const ST* p) {
   return static_cast<CT>(__ldg(p));
 }
@@ -85,6 +149,9 @@ template <> __device__ __forceinline__ float load_st<__half, float>(const __half
 template <> __device__ __forceinline__ float load_st<__nv_bfloat16, float>(const __nv_bfloat16* p) {
   return __bfloat162float(__ldg(p));
 }
+template <> __device__ __forceinline__ float load_st<E3M12, float>(const E3M12* p) {
+  return e3m12_decode(__ldg(reinterpret_cast<const unsigned short*>(p)));
+}
 template <typename ST, typename CT> __device__ __forceinline__ void store_st(ST* p, CT v) {
   *p = static_cast<ST>(v);
 }
@@ -93,6 +160,9 @@ template <> __device__ __forceinline__ void store_st<__half, float>(__half* p, f
 }
 template <> __device__ __forceinline__ void store_st<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
   *p = __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ void store_st<E3M12, float>(E3M12* p, float v) {
+  p->b = (unsigned short)e3m12_encode_rn(v);
 }
 
 // ------------------------------------------------------------------ node geometry
@@ -542,11 +612,53 @@ __device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p, const V* bp
 template <int LAT>
 __device__ __forceinline__ constexpr int zi(int ez) { return Lat<LAT>::NZ == 3 ? ez + 1 : 0; }
 
-// Storage scaling: FP16 populations are stored times a power of two near
-// 1/omega_j (keeps small-weight deviations out of FP16's subnormal range);
-// BF16 has FP32's exponent range and, like 32/64-bit storage, is unscaled.
+// Storage scaling: FP16 and E3M12 populations are stored times a power of
+// two near 1/omega_j (keeps small-weight deviations out of the subnormal
+// range; E3M12 also carries its 2^(bias - 127) in the factor); BF16 has
+// FP32's exponent range and, like 32/64-bit storage, is unscaled.
 template <typename ST>
-__device__ __forceinline__ constexpr bool scaled_storage() { return std::is_same<ST, __half>::value; }
+__device__ __forceinline__ constexpr bool scaled_storage() {
+  return std::is_same<ST, __half>::value || std::is_same<ST, E3M12>::value;
+}
+template <typename ST>
+__device__ __forceinline__ constexpr bool storage16() {
+  return std::is_same<ST, __half>::value || std::is_same<ST, __nv_bfloat16>::value || std::is_same<ST, E3M12>::value;
+}
+
+// Two FP32 values to one word of two 16-bit codes (lo in the low half) with
+// stochastic rounding: the discarded part of each value is compared with
+// random bits, so the rounding error has mean zero and no correlation from
+// one step to the next (round-to-nearest repeats the same error while a
+// slowly varying population changes by less than a unit in the last place
+// per step, and that error then grows with the step count).  FP16 and BF16
+// use the conversion instruction with a random-bits operand (the low 16
+// bits of r round lo, the high 16 bits round hi); E3M12 adds the random bits
+// below its last place and truncates.
+template <typename ST>
+__device__ __forceinline__ unsigned sr_pack2(float lo, float hi, unsigned r) {
+  if constexpr (std::is_same<ST, E3M12>::value) {
+    return e3m12_encode2_sr(lo, hi, r);
+  } else {
+    unsigned d;
+    if constexpr (std::is_same<ST, __half>::value)
+      asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    else
+      asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
+  }
+}
+
+// The stores of the step kernels: 16-bit storage rounds stochastically,
+// FP32 and FP64 store the value.
+template <typename ST, typename CT>
+__device__ __forceinline__ void store_step(ST* p, CT v, SrBits& rng) {
+  if constexpr (storage16<ST>()) {
+    const unsigned w = sr_pack2<ST>(float(v), 0.0f, rng.next());
+    *reinterpret_cast<unsigned short*>(p) = (unsigned short)(w & 0xFFFFu);
+  } else {
+    store_st<ST, CT>(p, v);
+  }
+}
 
 // ------------------------------------------------------------------ kernels
 // One time step: pull gather from fin (post-collision of the previous step,
@@ -593,12 +705,13 @@ __global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, S
   } else {
     collide<LAT, BASIS, FORCED, NSE>(q, p);
   }
+  SrBits rng(p.seed, unsigned(own));
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
     CT v = q.v[ex + 1][ey + 1][zi<LAT>(ez)];
     if constexpr (scaled_storage<ST>()) v *= p.sc[j];
-    store_st<ST, CT>(fout + j * N + own, v);
+    store_step<ST, CT>(fout + j * N + own, v, rng);
   });
 }
 
@@ -608,6 +721,7 @@ template <> struct Pair<double> { using T = double2; };
 template <> struct Pair<float> { using T = float2; };
 template <> struct Pair<__half> { using T = __half2; };
 template <> struct Pair<__nv_bfloat16> { using T = __nv_bfloat162; };
+template <> struct Pair<E3M12> { using T = unsigned; };
 
 template <typename ST, typename CT>
 __device__ __forceinline__ void load_pair(const ST* p, CT& lo, CT& hi) {
@@ -622,6 +736,11 @@ __device__ __forceinline__ void load_pair<__half, float>(const __half* p, float&
 template <>
 __device__ __forceinline__ void load_pair<__nv_bfloat16, float>(const __nv_bfloat16* p, float& lo, float& hi) {
   const float2 v = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+  lo = v.x; hi = v.y;
+}
+template <>
+__device__ __forceinline__ void load_pair<E3M12, float>(const E3M12* p, float& lo, float& hi) {
+  const float2 v = e3m12_decode2(__ldg(reinterpret_cast<const unsigned*>(p)));
   lo = v.x; hi = v.y;
 }
 template <typename ST, typename CT>
@@ -716,6 +835,7 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>:
   if constexpr (!PACKED) collide<LAT, BASIS, FORCED, NSE>(qb, p);
   if (!active) return;
   const int own = (z * p.ny + y) * p.nx + x0;
+  SrBits rng(p.seed, unsigned(own));
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
@@ -729,7 +849,10 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>:
       vb = qb.v[ex + 1][ey + 1][zi<LAT>(ez)];
       if constexpr (scaled_storage<ST>()) { va *= p.sc[j]; vb *= p.sc[j]; }
     }
-    store_pair<ST, CT>(fout + j * N + own, va, vb);
+    if constexpr (storage16<ST>())
+      *reinterpret_cast<unsigned*>(fout + j * N + own) = sr_pack2<ST>(float(va), float(vb), rng.next());
+    else
+      store_pair<ST, CT>(fout + j * N + own, va, vb);
   });
 }
 
@@ -755,6 +878,9 @@ __device__ __forceinline__ void load_quad(const ST* p, float (&v)[4]) {
   if constexpr (std::is_same<ST, __half>::value) {
     fa = __half22float2(a);
     fb = __half22float2(b);
+  } else if constexpr (std::is_same<ST, E3M12>::value) {
+    fa = e3m12_decode2(w.x);
+    fb = e3m12_decode2(w.y);
   } else {
     fa = __bfloat1622float2(a);
     fb = __bfloat1622float2(b);
@@ -762,19 +888,10 @@ __device__ __forceinline__ void load_quad(const ST* p, float (&v)[4]) {
   v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
 }
 template <typename ST>
-__device__ __forceinline__ void store_quad(ST* p, F2 a, F2 b) {
-  using H2 = typename Pair<ST>::T;
-  H2 ha, hb;
-  if constexpr (std::is_same<ST, __half>::value) {
-    ha = __floats2half2_rn(a.v.x, a.v.y);
-    hb = __floats2half2_rn(b.v.x, b.v.y);
-  } else {
-    ha = __floats2bfloat162_rn(a.v.x, a.v.y);
-    hb = __floats2bfloat162_rn(b.v.x, b.v.y);
-  }
+__device__ __forceinline__ void store_quad(ST* p, F2 a, F2 b, SrBits& rng) {
   uint2 w;
-  memcpy(&w.x, &ha, 4);
-  memcpy(&w.y, &hb, 4);
+  w.x = sr_pack2<ST>(a.v.x, a.v.y, rng.next());
+  w.y = sr_pack2<ST>(b.v.x, b.v.y, rng.next());
   *reinterpret_cast<uint2*>(p) = w;
 }
 
@@ -840,6 +957,7 @@ __global__ void __launch_bounds__(128, Tuning<LAT, 2, BASIS != 0>::X4_MIN_BLOCKS
   collide<LAT, BASIS, FORCED, NSE>(qb, p);
   if (!active) return;
   const int own = (z * p.ny + y) * p.nx + x0;
+  SrBits rng(p.seed, unsigned(own));
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
@@ -848,7 +966,7 @@ __global__ void __launch_bounds__(128, Tuning<LAT, 2, BASIS != 0>::X4_MIN_BLOCKS
       a = a * F2(p.sc[j]);
       b = b * F2(p.sc[j]);
     }
-    store_quad<ST>(fout + j * N + own, a, b);
+    store_quad<ST>(fout + j * N + own, a, b, rng);
   });
 }
 

@@ -28,7 +28,7 @@ inline bool axis_lattice(int lat) { return lat == RMRTLB_D2Q5 || lat == RMRTLB_D
 inline bool simple_ncde(int kind) {
   return kind == RMRTLB_EQ_NCDE_SIMPLE_LINEAR || kind == RMRTLB_EQ_NCDE_SIMPLE_QUAD;
 }
-inline size_t storage_size(int st) { return st == RMRTLB_ST_F64 ? 8 : (st == RMRTLB_ST_F32 ? 4 : 2); }
+inline size_t storage_size(int st) { return st == RMRTLB_ST_F64 ? 8 : (st == RMRTLB_ST_F32 ? 4 : 2); }  // 16-bit: F16, BF16, E3M12
 
 inline void lattice_dir(int lat, int j, int e[3]) {
   if (lat == RMRTLB_D2Q9 || lat == RMRTLB_D2Q5) {   // rD2Q5: the first 5 of rD2Q9
@@ -48,6 +48,7 @@ struct Consts {
   double s0, s1[3], s2[3][3], soff[3], sfree;
   double ss[3], sb[3];                 // NSE: s_s and s_b of Eq. (4-31) per axis
   double force[3], adv[3];
+  int st_shift;                        // E3M12: stored value = scaled deviation * 2^st_shift (range 8 * 2^-shift)
 };
 
 inline bool rate_ok(double s) { return s > 0.0 && s < 2.0 && isfinite(s); }
@@ -179,15 +180,20 @@ inline KParams<CT> to_kparams(const Consts& k) {
       p.q19h[g] = CT(k.cs2 * k.cs2 * c2[g] / ((c2[g] - k.cs2) * c2[al] * c2[be]));
     }
   }
-  const bool scaled = k.storage == RMRTLB_ST_F16;
+  const bool scaled = k.storage == RMRTLB_ST_F16 || k.storage == RMRTLB_ST_E3M12;
+  // E3M12 values x (the scaled deviation times 2^st_shift, so that the
+  // chosen range maps onto the format's [0, 8)) are carried in FP32 as
+  // x * 2^(bias - 127), their code in bits 11..25 of that number: both
+  // factors are part of the scale
+  const int e3 = k.storage == RMRTLB_ST_E3M12 ? k.st_shift + 5 - 127 : 0;
   for (int j = 0; j < 27; ++j) {
     if (j < k.q) {
-      // FP16 storage: power of two nearest 1/omega_j (exact to apply and
-      // undo, keeps deviations out of FP16's subnormals); BF16 (FP32's
-      // exponent range), FP32 and FP64 storage are unscaled
+      // FP16 and E3M12 storage: power of two nearest 1/omega_j (exact to
+      // apply and undo, keeps deviations out of the subnormals); BF16
+      // (FP32's exponent range), FP32 and FP64 storage are unscaled
       const int e = scaled ? int(lround(-log2(k.w[j]))) : 0;
-      p.sc[j] = CT(ldexp(1.0, e));
-      p.sinv[j] = CT(ldexp(1.0, -e));
+      p.sc[j] = CT(ldexp(1.0, e + e3));
+      p.sinv[j] = CT(ldexp(1.0, -e - e3));
       p.wd[j] = k.w[j];
     }
   }
@@ -232,6 +238,13 @@ inline int make_consts(Consts& k, int lattice, int nx, int ny, int nz, double dx
   k.forced = (k.source != 0.0) || (nse && (k.force[0] != 0.0 || k.force[1] != 0.0 || k.force[2] != 0.0)) ||
              simple_ncde(eq_kind);   // Eq. (4-16): G from dB/dt on every step
   if (!nse) for (int a = 0; a < 3; ++a) k.force[a] = 0.0;
+  if (storage == RMRTLB_ST_E3M12) {
+    // the format spans [0, 8); a range R maps onto it by 2^shift with
+    // shift = floor(log2(8 / R)): the power of two at or above R
+    const double R = params.storage_range > 0 ? params.storage_range : (nse ? 2.0 : 8.0);
+    if (!(R >= 1.0 / 1048576.0 && R <= 128.0)) return RMRTLB_EINVAL;
+    k.st_shift = int(floor(log2(8.0 / R)));
+  }
   int rc = derive_weights(k);
   if (rc) return rc;
   return derive_rates(k, params);

@@ -13,7 +13,7 @@ enum {
   KIND_NSE = 0, KIND_NSE_HELUO = 1, KIND_NCDE_LINEAR = 2, KIND_NCDE_QUAD = 3,
   KIND_NCDE_SIMPLE_LINEAR = 4, KIND_NCDE_SIMPLE_QUAD = 5   // Eq. (4-16): linear EDF, G from dB/dt
 };
-enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+enum { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3, ST_E3M12 = 4 };
 
 // Constants of one solver in the compute type CT (double for FP64 storage,
 // float otherwise).  Derived once on the host in FP64 and rounded.
@@ -37,7 +37,7 @@ struct KParams {
   double ssd[3], soffd[3];             // s_sa and s_ab (xy, xz, yz) in FP64 (local stress output)
   CT* hist;                            // simplified NCDE: B(t - dt) / c_a per node, d planes (index units)
   int hist_fresh;                      // 1: no previous B yet (dB/dt taken as 0 on this step)
-  int pad2_;
+  unsigned seed;                       // per-step seed of the stochastic rounding of 16-bit stores
 };
 
 enum Op { OP_STEP = 0, OP_INIT_EQ = 1, OP_PLANE = 2, OP_CHECK = 3, OP_STRESS = 4 };
@@ -72,7 +72,8 @@ struct LaunchArgs {
   cudaError_t launch_##lat##_f64(const LaunchArgs& a); \
   cudaError_t launch_##lat##_f32(const LaunchArgs& a); \
   cudaError_t launch_##lat##_f16(const LaunchArgs& a); \
-  cudaError_t launch_##lat##_bf16(const LaunchArgs& a);
+  cudaError_t launch_##lat##_bf16(const LaunchArgs& a); \
+  cudaError_t launch_##lat##_e3m12(const LaunchArgs& a);
 RMRT_DECLARE_LAUNCH(d2q9)
 RMRT_DECLARE_LAUNCH(d3q19)
 RMRT_DECLARE_LAUNCH(d3q27)

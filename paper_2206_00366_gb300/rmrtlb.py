@@ -24,12 +24,12 @@ D2Q9, D3Q19, D3Q27, D2Q5, D3Q7 = 0, 1, 2, 3, 4
 EQ_NSE, EQ_NSE_HELUO, EQ_NCDE_LINEAR, EQ_NCDE_QUAD = 0, 1, 2, 3
 EQ_NCDE_SIMPLE_LINEAR, EQ_NCDE_SIMPLE_QUAD = 4, 5
 BASIS_RAW, BASIS_CENTRAL, BASIS_HERMITE, BASIS_CENTRAL_HERMITE = 0, 1, 2, 3
-ST_F64, ST_F32, ST_F16, ST_BF16 = 0, 1, 2, 3
+ST_F64, ST_F32, ST_F16, ST_BF16, ST_E3M12 = 0, 1, 2, 3, 4
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETOOBIG, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 NOALLOC_MAX_NODES = 67108864
 
 LATTICE_NAMES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27, "D2Q5": D2Q5, "D3Q7": D3Q7}
-STORAGE_NAMES = {"f64": ST_F64, "f32": ST_F32, "f16": ST_F16, "bf16": ST_BF16}
+STORAGE_NAMES = {"f64": ST_F64, "f32": ST_F32, "f16": ST_F16, "bf16": ST_BF16, "e3m12": ST_E3M12}
 EQ_NAMES = {"nse": EQ_NSE, "nse_heluo": EQ_NSE_HELUO, "ncde_linear": EQ_NCDE_LINEAR,
             "ncde_quad": EQ_NCDE_QUAD, "ncde_simple_linear": EQ_NCDE_SIMPLE_LINEAR,
             "ncde_simple_quad": EQ_NCDE_SIMPLE_QUAD}
@@ -60,6 +60,7 @@ class rmrtlb_params(ctypes.Structure):
         ("force", ctypes.c_double * 3),
         ("source", ctypes.c_double),
         ("check_every", ctypes.c_int),
+        ("storage_range", ctypes.c_double),
     ]
 
 

@@ -115,6 +115,49 @@ def gpu_run(case: Case, storage: str, steps: int, fields=None, pops=None):
 
 
 def normwise(a, b):
-    """max |a - b| / max |b| (per field; the spec error measure)."""
+    """max |a - b| / max |b| (per field)."""
     den = np.max(np.abs(b))
     return float(np.max(np.abs(a - b)) / (den if den > 0 else 1.0))
+
+
+def component_scales(u_ref):
+    """Denominator of each velocity component's normwise error: max |u_ref,c|,
+    or max |u_ref| for a component below 1% of it (one that only the
+    nonlinear terms feed, or none)."""
+    umax = float(np.sqrt((u_ref * u_ref).sum(axis=0)).max())
+    dens = []
+    for c in range(u_ref.shape[0]):
+        den = float(np.abs(u_ref[c]).max())
+        dens.append(den if den >= 0.01 * umax else (umax if umax > 0 else 1.0))
+    return np.array(dens)
+
+
+def component_errors(u, u_ref):
+    """max |u_c - u_ref,c| / component_scales(u_ref)_c for every component."""
+    dens = component_scales(u_ref)
+    return np.array([float(np.abs(u[c] - u_ref[c]).max()) for c in range(u_ref.shape[0])]) / dens
+
+
+def normwise_u(u, u_ref):
+    """Largest per-component normwise error of a velocity field (d, ...)."""
+    return float(component_errors(u, u_ref).max())
+
+
+def fp64_component_bounds(steps, q, c_max, f_max, rho_min, u_ref, gate=1e-12):
+    """Per-component tolerance of an FP64 comparison: the gate, or the
+    oracle's own accumulated rounding where that is larger.  The oracle
+    holds full populations (up to f_max); each step its collision passes
+    every population through q multiply-adds and its momentum sums q
+    populations times |c_j| <= c_max, each rounding by at most 2^-53 of its
+    size, so after n steps its velocity carries at most
+    n q^2 2^-53 c_max f_max / rho_min absolute (linear accumulation, the
+    worst case)."""
+    oracle = steps * q * q * 2.0 ** -53 * c_max * f_max / rho_min
+    return np.maximum(gate, oracle / component_scales(u_ref))
+
+
+def of_max_u(u, u_ref):
+    """Largest component error over max |u_ref| (the measure of the 16-bit
+    storage gate: 2e-3 of max |u|)."""
+    umax = float(np.sqrt((u_ref * u_ref).sum(axis=0)).max())
+    return float(np.abs(u - u_ref).max() / (umax if umax > 0 else 1.0))

@@ -112,6 +112,24 @@ def test_create_rejects_invalid(B):
         p = B.make_params(**ok)
         B.rmrtlb_create(B.D2Q9, 8, 8, 1, 1.0, 1.0, 1.0, 1.0, p, 0, 0, B.ST_F32, 256, 16, 0)
     assert ei.value.status == B.ENOMEM
+    for storage, rng in [(5, 0.0), (B.ST_E3M12, 1000.0), (B.ST_E3M12, 1e-9)]:   # unknown storage; E3M12 range
+        p = B.make_params(storage_range=rng, **ok)
+        nbytes = B.rmrtlb_workspace_bytes(B.D2Q9, 8, 8, 1, B.ST_F32)
+        with pytest.raises(B.RmrtlbError) as ei:
+            B.rmrtlb_create(B.D2Q9, 8, 8, 1, 1.0, 1.0, 1.0, 1.0, p, 0, 0, storage, 256, nbytes, 0)
+        assert ei.value.status == B.EINVAL
+
+
+def test_e3m12_workspace_and_range_accepted(B):
+    """E3M12 stores 2 bytes per population like FP16; ranges from 2^-20 to
+    128 are accepted (checked on the host, no kernel runs)."""
+    assert B.rmrtlb_workspace_bytes(B.D3Q27, 64, 64, 32, B.ST_E3M12) == \
+        B.rmrtlb_workspace_bytes(B.D3Q27, 64, 64, 32, B.ST_F16)
+    for rng in (0.0, 2.0 ** -20, 0.3, 8.0, 128.0):
+        p = B.make_params(nu=0.01, nu_bulk=0.05, s_free=1.1, rho0=1.0, storage_range=rng)
+        nbytes = B.rmrtlb_workspace_bytes(B.D2Q9, 8, 8, 1, B.ST_E3M12)
+        h = B.rmrtlb_create(B.D2Q9, 8, 8, 1, 1.0, 1.0, 1.0, 1.0, p, 0, 0, B.ST_E3M12, 256, nbytes, 0)
+        B.rmrtlb_destroy(h)
 
 
 def test_bgk_limit_constants(B):
