@@ -47,11 +47,73 @@ VARIANTS = [
     ("rD3Q27-central-hermite-f32", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f32", "central_hermite", "nse"),
     ("rD2Q9-f64", "D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "f64", "raw", "nse"),
     ("rD3Q27-raw-f64", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "f64", "raw", "nse"),
+    ("rD2Q9-e3m12", "D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "e3m12", "raw", "nse"),
+    ("rD2Q9-ncde-quad-e3m12", "D2Q9", (4096, 2048, 1), (1.0, 0.6, 1.0), "e3m12", "raw", "ncde_quad"),
+    ("rD3Q19-raw-e3m12", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "e3m12", "raw", "nse"),
+    ("rD3Q19-central-e3m12", "D3Q19", (256, 256, 128), (1.0, 1.0, 0.5), "e3m12", "central", "nse"),
+    ("rD3Q27-raw-e3m12", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "e3m12", "raw", "nse"),
+    ("rD3Q27-central-e3m12", "D3Q27", (256, 256, 128), (1.0, 1.0, 0.5), "e3m12", "central", "nse"),
 ]
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
-ESIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+ESIZE = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "e3m12": 2}
+
+# The stored oracle run each workload's accuracy is measured on: the same
+# lattice, basis, physics and step count on a downscaled grid (the oracle
+# cannot run the full grids), written by tests/golden/long_runs.py.
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_for(lattice, basis, kind):
+    if lattice == "D2Q9":
+        return {"nse": "d2q9_nse_modes", "ncde_linear": "d2q9_ncde_linear_hill",
+                "ncde_quad": "d2q9_ncde_quad_hill"}[kind]
+    return f"{lattice.lower()}_{basis}"
+
+
+def _golden(name):
+    """(meta, arrays) of a stored oracle run, or None when it is absent."""
+    sys.path.insert(0, GOLDEN_DIR)
+    import store
+    if not store.available(name):
+        return None
+    return store.load(name)
+
+
+def oracle_error(lattice, storage, basis, kind):
+    """Error against the FP64 oracle of one workload variant: the same
+    kernel, storage and physics run on the stored oracle run's grid to its
+    step count (the workload's own), compared node by node.  NSE: largest
+    component error of u over max |u| and the normwise errors of rho and of
+    each u component; NCDE: normwise phi."""
+    import torch
+    name = golden_for(lattice, basis, kind)
+    g = _golden(name)
+    if g is None:
+        return {"case": name, "unavailable": "stored oracle run not present"}
+    meta, a = g
+    shape = tuple(meta["shape"])
+    sp = tuple(meta["spacing"])
+    s = make_solver(lattice, shape, sp, storage, basis, kind, 0)
+    r_, u_ = initial_fields(lattice, shape, sp, kind, 1)
+    s.init_equilibrium(torch.from_numpy(r_).cuda(), torch.from_numpy(u_).cuda())
+    s.step(int(meta["steps"]))
+    rho, u = s.moments()
+    ro, uo = a["rho"], a["u"]
+    out = {"case": name, "grid": list(shape), "steps": int(meta["steps"])}
+    if kind.startswith("ncde"):
+        out["phi"] = float(np.abs(rho - ro).max() / np.abs(ro).max())
+        return out
+    umax = float(np.sqrt((uo * uo).sum(axis=0)).max())
+    per = []
+    for c in range(uo.shape[0]):
+        den = float(np.abs(uo[c]).max())
+        per.append(float(np.abs(u[c] - uo[c]).max() / (den if den >= 0.01 * umax else umax)))
+    out.update({"u_of_max": float(np.abs(u - uo).max() / umax), "u": max(per),
+                "rho": float(np.abs(rho - ro).max() / np.abs(ro).max())})
+    return out
 CHECK_EVERY = 100
 FALLBACK_HBM_GBS = 6800.0
+TO_STEADY_CAP = 600000     # batched cavities: steps at most to residual 1e-6
 
 
 STEP_KERNEL_SOURCES = ("rmrt_device.cuh", "rmrt_params.h", "rmrt_tuning.h", "rmrt_launch.cuh", "build.py")
@@ -279,7 +341,23 @@ def run_ours(args):
     durs = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     plain = [d for i, d in enumerate(durs) if (args.warmup + i + 1) % CHECK_EVERY != 0]
     kern_ms = statistics.mean(plain) if plain else total_ms / args.steps
-    total_ms = max_over_ranks(total_ms, "cuda")
+    checks_in_region = args.steps - len(plain)
+    # The FP64 check runs every CHECK_EVERY steps; a timed region shorter
+    # than that holds fewer checks than its share.  Time one step that ends
+    # in a check and add the missing share, so that value is the throughput
+    # of the workload with its checks.
+    done = args.warmup + args.steps
+    to_next = CHECK_EVERY - done % CHECK_EVERY
+    if to_next > 1:
+        solver.step(to_next - 1)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    solver.step(1)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    check_ms = max(0.0, c0.elapsed_time(c1) - kern_ms)
+    added_ms = max(0.0, args.steps / CHECK_EVERY - checks_in_region) * check_ms
+    total_ms = max_over_ranks(total_ms + added_ms, "cuda")
     chk = solver.last_check()
     ms_per_step = total_ms / args.steps
     mlups = replica_mlups(world, nodes, args.steps, total_ms * 1e-3)
@@ -317,8 +395,15 @@ def run_ours(args):
     traffic = profiled_traffic("rD2Q9-f32")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "step_kernel<D2Q9, f32, raw>", "algorithmic_bytes_per_launch": bytes_per_launch,
-                "kernel_ms": round(kern_ms, 5)}
+                "kernel": "step_kernel_x2<0, float, float, 0, 0, 1> (rD2Q9, FP32 storage and compute, raw "
+                          "moments, unforced, NSE; two nodes per thread)",
+                "algorithmic_bytes_per_launch": bytes_per_launch, "kernel_ms": round(kern_ms, 5)}
+    accuracy = None
+    if rank == 0:
+        try:
+            accuracy = oracle_error(wl["lattice"], wl["storage"], wl["basis"], wl["kind"])
+        except Exception as ex:  # report, do not hide
+            accuracy = {"error": str(ex)}
 
     variants = {}
     if rank == 0 and not args.no_variants:
@@ -342,6 +427,7 @@ def run_ours(args):
                     variants[name]["alu"] = fp64_alu_roof(name, n, km)
                 del s
                 torch.cuda.empty_cache()
+                variants[name]["oracle_err"] = oracle_error(lat, st, basis, kind)
             except Exception as ex:  # report, do not hide
                 variants[name] = {"error": str(ex)}
 
@@ -369,8 +455,14 @@ def run_ours(args):
             "config": {"workload": "rD2Q9 NSE Taylor-Green modes 4096x2048 dx=1 dy=0.6 FP32 storage",
                        "lattice": "rD2Q9", "nx": nx, "ny": ny, "storage": "f32", "basis": "raw",
                        "check_every": CHECK_EVERY,
+                       "check_in_value": {"checks_in_timed_region": checks_in_region,
+                                          "check_ms": round(check_ms, 5), "added_ms": round(added_ms, 5),
+                                          "note": "the FP64 check every 100 steps is included in value: timed "
+                                                  "in the region, or its share added when the region holds "
+                                                  "fewer checks than steps/100"},
                        "l2": "working set 604 MB > L2 (129 MB); no flush",
                        "parallelism": "replicas" if world > 1 else "single"},
+            "oracle_err": accuracy,
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "cpu_baseline": cpu, "variants": variants, "batched": batched,
             "warm_start": warm,
@@ -381,10 +473,39 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def batched_oracle_error(storage="f32"):
+    """Error against the FP64 oracle of the batch kernels: the stored
+    cavities of the batched workload (the smallest seeded ones that stay
+    stable), 1,000 steps from rest in one batch, each against its oracle
+    run; the largest normwise rho or u error over the cavities."""
+    import workloads as W
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    g = _golden("cavities")
+    if g is None:
+        return {"case": "cavities", "unavailable": "stored oracle run not present"}
+    meta, a = g
+    doms = W.cavity_domains(512, seed=4)
+    idx = meta["indices"]
+    b = Batch([doms[k] for k in idx], storage=storage, check_every=100, tol=1e-300)   # never converged
+    b.tune(5)
+    b.reset()
+    b.step(int(meta["steps"]))
+    worst = 0.0
+    for i, k in enumerate(idx):
+        rg, ug = b.fields(i)
+        ro, uo = a[f"rho_{k}"], a[f"u_{k}"]
+        worst = max(worst, float(np.abs(rg - ro).max() / np.abs(ro).max()),
+                    float(np.abs(ug - uo).max() / np.abs(uo).max()))
+    return {"case": "cavities", "domains": [int(k) for k in idx], "steps": int(meta["steps"]),
+            "storage": storage, "max_normwise": worst,
+            "oracle_unstable": {k: int(v) for k, v in meta["unstable"].items()}}
+
+
 def run_batched(args):
-    """Batched lid-driven cavities: throughput of 512 seeded domains (sizes
-    32..512, dy/dx in {1/4..4}, Re 100..1000) after tuning the tile width,
-    and cold-start time to residual 1e-6 of 64 smaller stable cavities."""
+    """Batched lid-driven cavities (512 seeded domains: sizes 32..512, dy/dx
+    in {1/4..4}, Re 100..1000): throughput after tuning the launch shape,
+    and cold-start time to residual 1e-6 of all 512 (capped at
+    TO_STEADY_CAP steps), with the oracle error of the batch kernels."""
     import numpy as np
     import torch
 
@@ -412,23 +533,48 @@ def run_batched(args):
                          "unstable_domains": int((act == -1).sum()),
                          "note": "FP32, check every 100 steps in a CUDA graph; MLUPS counts every node of every "
                                  "domain while it is stepped"}
-    del b
-    torch.cuda.empty_cache()
-    small = W.cavity_domains(64, seed=7, size=(32, 96), ratios=(0.5, 1.0, 2.0), re=(100.0, 400.0))
-    b = Batch(small, storage="f32", check_every=100, tol=1e-6)
-    b.tune(10)
+    # all 512 to steady state from rest (the same batch, reset)
+    b.reset()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    b.run(400000)
+    issued = b.run(TO_STEADY_CAP)
     wall = time.perf_counter() - t0
     res, conv, act, done = b.status()
     ok = conv[act == 0]
-    out["time_to_steady"] = {"domains": len(small), "tol": 1e-6, "start": "cold (rest)",
+    nn = np.array([d["nx"] * d["ny"] for d in doms])
+    work = float((nn * np.where(act == 0, conv, issued)).sum())
+    out["time_to_steady"] = {"domains": len(doms), "tol": 1e-6, "start": "cold (rest)",
+                             "distribution": "sizes 32..512, dy/dx in {1/4,1/2,1,2,4}, Re 100..1000 (seed 4)",
+                             "cap_steps": TO_STEADY_CAP, "steps_issued": int(issued), "wall_s": round(wall, 2),
                              "converged": int((act == 0).sum()), "unstable": int((act == -1).sum()),
-                             "steps_issued": int(done), "wall_s": round(wall, 2),
+                             "capped": int((act == 1).sum()),
                              "median_steps_to_tol": int(np.median(ok)) if len(ok) else None,
-                             "max_steps_to_tol": int(ok.max()) if len(ok) else None}
+                             "p90_steps_to_tol": int(np.percentile(ok, 90)) if len(ok) else None,
+                             "max_steps_to_tol": int(ok.max()) if len(ok) else None,
+                             "node_updates": work, "mlups_effective": round(work / wall / 1e6, 1)}
+    del b
+    torch.cuda.empty_cache()
+    out["oracle_err"] = batched_oracle_error()
     return out
+
+
+def cavity3d_oracle_error(storage="f32"):
+    """Error against the FP64 oracle of the rD3Q27 batch kernels the warm
+    start runs on: the stored 32 x 32 x 16 lid-driven cavity (Re 300), 1,000
+    steps from rest, normwise rho and u."""
+    from paper_2206_00366_gb300.rmrtlb import Batch
+    g = _golden("cavity3d")
+    if g is None:
+        return {"case": "cavity3d", "unavailable": "stored oracle run not present"}
+    meta, a = g
+    b = Batch([meta["domain"]], storage=storage, check_every=100, tol=1e-300, lattice="D3Q27")
+    b.reset()
+    b.step(int(meta["steps"]))
+    rg, ug = b.fields(0)
+    ro, uo = a["rho"], a["u"]
+    return {"case": "cavity3d", "grid": [meta["domain"][k] for k in ("nx", "ny", "nz")], "steps": int(meta["steps"]),
+            "storage": storage, "rho": float(np.abs(rg - ro).max() / np.abs(ro).max()),
+            "u": float(np.abs(ug - uo).max() / np.abs(uo).max())}
 
 
 def run_warmstart(args, re_seed=0):
@@ -458,6 +604,7 @@ def run_warmstart(args, re_seed=0):
             "step_ratio_warm_over_cold": round(warm["steps"] / cold["steps"], 3) if ok else None,
             "time_ratio_warm_over_cold": round(warm["wall_s"] / cold["wall_s"], 3) if ok else None,
             "final_u_maxdiff_rel": diff,
+            "oracle_err": cavity3d_oracle_error(),
             "network": {k: net.meta.get(k) for k in ("states", "converged", "shape", "epochs", "final_loss",
                                                       "holdout_u_rel_l2_median")}}
 

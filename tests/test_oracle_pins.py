@@ -941,6 +941,36 @@ def test_cavity_walls_conserve_mass():
     assert abs(f.sum() - m0) < 1e-12 * m0
 
 
+def _cavity_leaves_range(d, steps, check=100):
+    """Step one seeded cavity from rest in the oracle; the first check step at
+    which its state leaves the method's range (a non-finite value or
+    max |u|^2 >= c_s^2), else None."""
+    lat = R.make_lattice("D2Q9", (d["dx"], d["dy"]), 1.0, d["cs2"] if d["cs2"] > 0 else None)
+    S = R.relaxation_matrix(lat, R.rates_from_viscosity(lat, d["nu"], d["nu_bulk"], d["s_free"]))
+    m = R.Model(R.NSE, rho0=1.0)
+    f = R.init_equilibrium(lat, m, S, np.ones((1, d["ny"], d["nx"])), np.zeros((2, 1, d["ny"], d["nx"])))
+    for s in range(check, steps + 1, check):
+        with np.errstate(all="ignore"):
+            f = R.step(lat, m, S, f, check, walls=(0, 1), lid=(1, (d["lid_u"], 0.0), 1.0))
+            u = R.fields(lat, m, f)[1]
+            if not np.isfinite(f).all() or float((u * u).sum(axis=0).max()) >= lat.cs2:
+                return s
+    return None
+
+
+def test_underresolved_batched_cavity_is_unstable_in_the_method():
+    """Cavity 460 of the 512 seeded cavities of the batched workload (seed 4:
+    46 x 33 nodes, dy/dx = 2, Re 943, lid 0.05) leaves the method's range
+    within 600 steps from rest in the FP64 oracle itself, so a batch that
+    retires it as unstable reports the method, not the kernels; cavity 410
+    (84 x 33, dy/dx = 4, Re 272) stays in range for 1000 steps."""
+    doms = W.cavity_domains(512, seed=4)
+    d = doms[460]
+    assert (d["nx"], d["ny"], d["dy"] / d["dx"]) == (46, 33, 2.0)
+    assert _cavity_leaves_range(d, 600) is not None
+    assert _cavity_leaves_range(doms[410], 1000) is None
+
+
 # ---------------------------------------------------------------- Eqs. (4-35), (fne)
 @pytest.mark.parametrize("name,dx", [("D2Q9", (1.0, 0.5)), ("D3Q27", (1.0, 0.5, 0.8))])
 def test_velocity_gradient_exact_for_linear_fields(name, dx):
