@@ -121,12 +121,13 @@ __device__ __forceinline__ unsigned e3m12_encode2_sr(float x, float y, unsigned 
   return (ax >> 11) | ((ux >> 16) & 0x8000u) | ((ay << 5) & 0x7FFF0000u) | (uy & 0x80000000u);
 }
 
-// Random bits for stochastic rounding: a 32-bit linear congruential state per
-// thread, seeded from the step's seed and the thread's first node, each
-// output xor-folded with its upper half (the upper bits of the state have the
-// long periods).  The rounding only needs bits that are uniform and
-// unrelated to the values rounded; the sequence is reproducible for a given
-// step and grid.
+// Random bits for stochastic rounding: one 32-bit hash of the step's seed
+// and the thread's first node, and from it word K = hash * (an odd constant
+// per K), one integer multiply per word.  Multiplying by an odd number is a
+// bijection, so every word is uniformly distributed over the nodes and
+// steps, and the words of one thread differ by their multipliers.  The
+// rounding only needs bits that are uniform and unrelated to the values
+// rounded; the sequence is reproducible for a given step and grid.
 struct SrBits {
   unsigned s;
   __device__ __forceinline__ explicit SrBits(unsigned seed, unsigned node) {
@@ -134,9 +135,9 @@ struct SrBits {
     x ^= x >> 16; x *= 0x7FEB352Du; x ^= x >> 15; x *= 0x846CA68Bu; x ^= x >> 16;
     s = x;
   }
-  __device__ __forceinline__ unsigned next() {
-    s = s * 747796405u + 2891336453u;
-    return s ^ (s >> 16);
+  template <int K>
+  __device__ __forceinline__ unsigned word() const {
+    return s * (0x9E3779B1u + 2u * unsigned(K) * 0x632BE5ABu);
   }
 };
 
@@ -494,7 +495,100 @@ __device__ __forceinline__ Macro<V> macroscopic(V m000, const V jh[3], const P& 
   return r;
 }
 
-// Collision of one node (or a pair of nodes, V = F2) in moment space,
+// The other bases for the NSE kinds, without a second cube of moments.
+// With Mbar = T M (T unit lower-triangular by order: the central shift N(u)
+// and/or the Hermite map, Eq. 5-1-1) and Sbar = s_free I + D, D nonzero only
+// up to second order, the collision operator of Eq. (5-1-2) applied to the
+// non-equilibrium moments X is s_free X + T^-1 D T X.  For the NSE family
+// X vanishes at orders 0 and 1, so (T X) at second order is X's own second
+// order (the shift and the Hermite map only add lower orders to it) and
+// E = D T X = (Sbar_2 - s_free I) X_2 has second-order entries only.  T^-1
+// is a tensor product of one 3 x 3 lower-triangular matrix per axis,
+// G = [[1, 0, 0], [g1, 1, 0], [g2, g21, 1]]: central g1 = u, g2 = u^2,
+// g21 = 2u; Hermite g1 = 0, g2 = mu, g21 = 0; central-Hermite g1 = u,
+// g2 = u^2 + mu, g21 = 2u (index units, mu = c_s^2 / c_a^2).  So the step
+// is the raw step at the single rate s_free minus T^-1 E, whose entries are
+// sums of at most six products; moments the lattice does not carry are
+// zeroed afterwards as in every basis.
+template <int LAT, int BASIS, typename V, typename P>
+__device__ __forceinline__ void subtract_transported(Cube<LAT, V>& q, const V (&X)[3][3][Lat<LAT>::NZ],
+                                                     const V u[3], const P& p) {
+  using S = PScalar<P>;
+  constexpr int NZ = Lat<LAT>::NZ;
+  constexpr bool SH = (BASIS & 1) != 0, HE = (BASIS & 2) != 0;
+  // E = (Sbar_2 - s_free) X_2: the dense block on the normal moments, the
+  // off-diagonal rates on the mixed ones
+  const V x0 = X[2][0][0], x1 = X[0][2][0];
+  const V x2 = NZ == 3 ? X[0][0][NZ - 1] : V(0.0f);
+  V En[3];
+#pragma unroll
+  for (int r = 0; r < (NZ == 3 ? 3 : 2); ++r) {
+    const V xr = r == 0 ? x0 : (r == 1 ? x1 : x2);
+    V t = xr * V(-p.sfree);
+    t = fmav(x0, V(p.s2h[r][0]), t);
+    t = fmav(x1, V(p.s2h[r][1]), t);
+    if constexpr (NZ == 3) t = fmav(x2, V(p.s2h[r][2]), t);
+    En[r] = t;
+  }
+  if constexpr (NZ != 3) En[2] = V(0.0f);
+  const V Exy = X[1][1][0] * V(p.soff[0] - p.sfree);
+  const V Exz = NZ == 3 ? X[1][0][NZ - 2] * V(p.soff[1] - p.sfree) : V(0.0f);
+  const V Eyz = NZ == 3 ? X[0][1][NZ - 2] * V(p.soff[2] - p.sfree) : V(0.0f);
+  // per-axis entries of G
+  V g1[3], g2[3], g21[3];
+#pragma unroll
+  for (int al = 0; al < 3; ++al) {
+    g1[al] = u[al];
+    g21[al] = V(2.0f) * u[al];
+    if constexpr (SH && HE) g2[al] = fmav(u[al], u[al], V(p.mu2[al]));
+    else if constexpr (SH) g2[al] = u[al] * u[al];
+    else g2[al] = V(p.mu2[al]);
+  }
+  // G[axis][a][a'] with the structural zeros and ones resolved at compile time
+  auto coef = [&](int al, int a, int ap, bool& one, bool& zero) -> V {
+    one = false; zero = false;
+    if (a == ap) { one = true; return V(1.0f); }
+    if (a < ap) { zero = true; return V(0.0f); }
+    if (a - ap == 1) {
+      if (!SH) { zero = true; return V(0.0f); }
+      return a == 1 ? g1[al] : g21[al];
+    }
+    return g2[al];                                   // a = 2, a' = 0
+  };
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < NZ; ++c) {
+        if (absent<LAT>(a, b, c) || a + b + c < 2) continue;
+        const int cc = NZ == 3 ? c : 0;
+        V acc = V(0.0f);
+        bool any = false;
+        // the six second-order sources (a', b', c')
+#pragma unroll
+        for (int sidx = 0; sidx < 6; ++sidx) {
+          const int ap = sidx == 0 ? 2 : (sidx == 3 || sidx == 4 ? 1 : 0);
+          const int bp = sidx == 1 ? 2 : (sidx == 3 || sidx == 5 ? 1 : 0);
+          const int cp = sidx == 2 ? 2 : (sidx == 4 || sidx == 5 ? 1 : 0);
+          if (NZ != 3 && cp != 0) continue;
+          if (ap > a || bp > b || cp > cc) continue;
+          bool o1, z1, o2, z2, o3, z3;
+          const V fx = coef(0, a, ap, o1, z1), fy = coef(1, b, bp, o2, z2), fz = coef(2, cc, cp, o3, z3);
+          if (z1 || z2 || z3) continue;
+          const V src = sidx < 3 ? En[sidx] : (sidx == 3 ? Exy : (sidx == 4 ? Exz : Eyz));
+          V term = src;
+          if (!o1) term = term * fx;
+          if (!o2) term = term * fy;
+          if (!o3) term = term * fz;
+          acc = any ? acc + term : term;
+          any = true;
+        }
+        if (any) q.v[a][b][c] -= acc;
+      }
+}
+
+// Collision of one node (or a pair of nodes, V = F2) in moment space,// Collision of one node (or a pair of nodes, V = F2) in moment space,
 // Eq. (2-2-3):
 //   m* - m0 = m(delta) + dt (m_G + m_F) - S (m^ne + dt m_F / 2),
 // central variant: S replaced by N(u)^-1 Sbar N(u) (Eq. 5-1-2).
@@ -574,7 +668,17 @@ __device__ __forceinline__ void collide(Cube<LAT, V>& q, const P& p, const V* bp
           q.v[a][b][c] = fmav(mG + mF, V(p.dt), q.v[a][b][c]);
         }
       }
-  if constexpr (BASIS != 0) {
+  if constexpr (BASIS != 0 && NSE) {
+    // raw step at the single rate s_free, then the transported correction
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < NZ; ++c)
+          if (!absent<LAT>(a, b, c) && a + b + c >= 2) q.v[a][b][c] = fmav(X[a][b][c], V(-p.sfree), q.v[a][b][c]);
+    subtract_transported<LAT, BASIS>(q, X, mc.u, p);
+  } else if constexpr (BASIS != 0) {
     Cube<LAT, V> k;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -651,9 +755,9 @@ __device__ __forceinline__ unsigned sr_pack2(float lo, float hi, unsigned r) {
 // The stores of the step kernels: 16-bit storage rounds stochastically,
 // FP32 and FP64 store the value.
 template <typename ST, typename CT>
-__device__ __forceinline__ void store_step(ST* p, CT v, SrBits& rng) {
+__device__ __forceinline__ void store_step(ST* p, CT v, unsigned r) {
   if constexpr (storage16<ST>()) {
-    const unsigned w = sr_pack2<ST>(float(v), 0.0f, rng.next());
+    const unsigned w = sr_pack2<ST>(float(v), 0.0f, r);
     *reinterpret_cast<unsigned short*>(p) = (unsigned short)(w & 0xFFFFu);
   } else {
     store_st<ST, CT>(p, v);
@@ -705,13 +809,13 @@ __global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, S
   } else {
     collide<LAT, BASIS, FORCED, NSE>(q, p);
   }
-  SrBits rng(p.seed, unsigned(own));
+  SrBits rng(p.seed, unsigned(own) + p.node_base);
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
     CT v = q.v[ex + 1][ey + 1][zi<LAT>(ez)];
     if constexpr (scaled_storage<ST>()) v *= p.sc[j];
-    store_step<ST, CT>(fout + j * N + own, v, rng);
+    store_step<ST, CT>(fout + j * N + own, v, rng.template word<j>());
   });
 }
 
@@ -835,7 +939,7 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>:
   if constexpr (!PACKED) collide<LAT, BASIS, FORCED, NSE>(qb, p);
   if (!active) return;
   const int own = (z * p.ny + y) * p.nx + x0;
-  SrBits rng(p.seed, unsigned(own));
+  SrBits rng(p.seed, unsigned(own) + p.node_base);
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
@@ -850,7 +954,7 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>:
       if constexpr (scaled_storage<ST>()) { va *= p.sc[j]; vb *= p.sc[j]; }
     }
     if constexpr (storage16<ST>())
-      *reinterpret_cast<unsigned*>(fout + j * N + own) = sr_pack2<ST>(float(va), float(vb), rng.next());
+      *reinterpret_cast<unsigned*>(fout + j * N + own) = sr_pack2<ST>(float(va), float(vb), rng.template word<j>());
     else
       store_pair<ST, CT>(fout + j * N + own, va, vb);
   });
@@ -862,37 +966,60 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>:
 // 4): every population is one aligned 8-byte load of four values, which
 // doubles the bytes per load and halves the loads, shuffles and index
 // arithmetic per node against step_kernel_x2 (the 16-bit kernels were
-// limited by memory-level parallelism and issue, not by DRAM).  For e_x = +1 the
-// thread needs x0 - 1: the last value of the lane below (warp shuffle), lane 0
-// loading it; for e_x = -1 it needs x0 + 4 from the lane above, the last lane
-// of a warp or of a row loading it (periodic wrap).  The four nodes collide
-// as two packed FP32 pairs.
+// limited by memory-level parallelism and issue, not by DRAM).  The loaded
+// codes stay packed, two 16-bit codes per 32-bit word: pair A holds nodes
+// (x0, x0 + 1), pair B (x0 + 2, x0 + 3).  For e_x = +1 the thread needs
+// x0 - 1: the last code of the lane below (warp shuffle of one word), lane 0
+// loading it; for e_x = -1 it needs x0 + 4 from the lane above, the last
+// lane of a warp or of a row loading it (periodic wrap); byte permutes
+// assemble the shifted pairs.  Pair A is decoded, collided (packed FP32)
+// and re-encoded into its words before pair B is decoded, so the packed
+// codes of the other pair, not a second FP32 cube, are what stays live
+// beside the collision.
 template <typename ST>
-__device__ __forceinline__ void load_quad(const ST* p, float (&v)[4]) {
-  const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
-  using H2 = typename Pair<ST>::T;
-  H2 a, b;
-  memcpy(&a, &w.x, 4);
-  memcpy(&b, &w.y, 4);
-  float2 fa, fb;
+__device__ __forceinline__ float2 decode2(unsigned w) {
   if constexpr (std::is_same<ST, __half>::value) {
-    fa = __half22float2(a);
-    fb = __half22float2(b);
+    __half2 h;
+    memcpy(&h, &w, 4);
+    return __half22float2(h);
   } else if constexpr (std::is_same<ST, E3M12>::value) {
-    fa = e3m12_decode2(w.x);
-    fb = e3m12_decode2(w.y);
+    return e3m12_decode2(w);
   } else {
-    fa = __bfloat1622float2(a);
-    fb = __bfloat1622float2(b);
+    __nv_bfloat162 h;
+    memcpy(&h, &w, 4);
+    return __bfloat1622float2(h);
   }
-  v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
 }
-template <typename ST>
-__device__ __forceinline__ void store_quad(ST* p, F2 a, F2 b, SrBits& rng) {
-  uint2 w;
-  w.x = sr_pack2<ST>(a.v.x, a.v.y, rng.next());
-  w.y = sr_pack2<ST>(b.v.x, b.v.y, rng.next());
-  *reinterpret_cast<uint2*>(p) = w;
+__device__ __forceinline__ unsigned load_code(const void* p) {
+  return __ldg(reinterpret_cast<const unsigned short*>(p));
+}
+
+template <int LAT, typename ST, int BASIS, bool FORCED, bool NSE>
+__device__ __forceinline__ void collide_pair(unsigned (&w)[Lat<LAT>::Q], const KParams<float>& p, const SrBits& rng,
+                                             int slot) {
+  using L = Lat<LAT>;
+  Cube<LAT, F2> q;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < L::NZ; ++c) q.v[a][b][c] = F2(0.0f);
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    F2 v(decode2<ST>(w[j]));
+    if constexpr (scaled_storage<ST>()) v = v * F2(p.sinv[j]);
+    q.v[ex + 1][ey + 1][zi<LAT>(ez)] = v;
+  });
+  collide<LAT, BASIS, FORCED, NSE>(q, p);
+  static_for<L::Q>([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+    F2 v = q.v[ex + 1][ey + 1][zi<LAT>(ez)];
+    if constexpr (scaled_storage<ST>()) v = v * F2(p.sc[j]);
+    w[j] = sr_pack2<ST>(v.v.x, v.v.y, slot == 0 ? rng.template word<2 * j>() : rng.template word<2 * j + 1>());
+  });
 }
 
 template <int LAT, typename ST, int BASIS, bool FORCED, bool NSE>
@@ -921,52 +1048,36 @@ __global__ void __launch_bounds__(128, Tuning<LAT, 2, BASIS != 0>::X4_MIN_BLOCKS
       const int sy = Nbr::up(ey, ym, y, yp), sz = Nbr::up(ez, zm, z, zp);
       roff[ey + 1][zi<LAT>(ez)] = (sz * p.ny + sy) * p.nx + xc;
     }
-  Cube<LAT, F2> qa, qb;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < L::NZ; ++c) { qa.v[a][b][c] = F2(0.0f); qb.v[a][b][c] = F2(0.0f); }
+  unsigned wa[L::Q], wb[L::Q];
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
     const ST* src = fin + j * N + roff[ey + 1][zi<LAT>(ez)];
-    float v[4], o[4];
-    load_quad<ST>(src, v);
+    const uint2 w = __ldg(reinterpret_cast<const uint2*>(src));   // codes x0 .. x0 + 3
     if constexpr (ex == 0) {
-      o[0] = v[0]; o[1] = v[1]; o[2] = v[2]; o[3] = v[3];
+      wa[j] = w.x; wb[j] = w.y;
     } else if constexpr (ex == 1) {
-      float prev = __shfl_up_sync(0xffffffffu, v[3], 1);
-      if (fix_lo) prev = load_st<ST, float>(src + d_lo);
-      o[0] = prev; o[1] = v[0]; o[2] = v[1]; o[3] = v[2];
+      // (x0 - 1, x0), (x0 + 1, x0 + 2): the code below x0 sits in the high half of prev
+      unsigned prev = __shfl_up_sync(0xffffffffu, w.y, 1);
+      if (fix_lo) prev = load_code(src + d_lo) << 16;
+      wa[j] = __byte_perm(prev, w.x, 0x5432);
+      wb[j] = __byte_perm(w.x, w.y, 0x5432);
     } else {
-      float next = __shfl_down_sync(0xffffffffu, v[0], 1);
-      if (fix_hi) next = load_st<ST, float>(src + d_hi);
-      o[0] = v[1]; o[1] = v[2]; o[2] = v[3]; o[3] = next;
+      // (x0 + 1, x0 + 2), (x0 + 3, x0 + 4): the code above x0 + 3 sits in the low half of next
+      unsigned next = __shfl_down_sync(0xffffffffu, w.x, 1);
+      if (fix_hi) next = load_code(src + d_hi);
+      wa[j] = __byte_perm(w.x, w.y, 0x5432);
+      wb[j] = __byte_perm(w.y, next, 0x5432);
     }
-    F2 a(o[0], o[1]), b(o[2], o[3]);
-    if constexpr (scaled_storage<ST>()) {
-      a = a * F2(p.sinv[j]);
-      b = b * F2(p.sinv[j]);
-    }
-    qa.v[ex + 1][ey + 1][zi<LAT>(ez)] = a;
-    qb.v[ex + 1][ey + 1][zi<LAT>(ez)] = b;
   });
-  collide<LAT, BASIS, FORCED, NSE>(qa, p);
-  collide<LAT, BASIS, FORCED, NSE>(qb, p);
+  const int own = (z * p.ny + y) * p.nx + xc;
+  const SrBits rng(p.seed, unsigned(own) + p.node_base);
+  collide_pair<LAT, ST, BASIS, FORCED, NSE>(wa, p, rng, 0);
+  collide_pair<LAT, ST, BASIS, FORCED, NSE>(wb, p, rng, 1);
   if (!active) return;
-  const int own = (z * p.ny + y) * p.nx + x0;
-  SrBits rng(p.seed, unsigned(own));
   static_for<L::Q>([&](auto J) {
     constexpr int j = decltype(J)::value;
-    constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-    F2 a = qa.v[ex + 1][ey + 1][zi<LAT>(ez)], b = qb.v[ex + 1][ey + 1][zi<LAT>(ez)];
-    if constexpr (scaled_storage<ST>()) {
-      a = a * F2(p.sc[j]);
-      b = b * F2(p.sc[j]);
-    }
-    store_quad<ST>(fout + j * N + own, a, b, rng);
+    *reinterpret_cast<uint2*>(fout + j * N + own) = make_uint2(wa[j], wb[j]);
   });
 }
 

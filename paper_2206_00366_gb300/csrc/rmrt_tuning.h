@@ -23,6 +23,14 @@
 #ifndef RMRT_X2_MINB_D3Q19_W4
 #define RMRT_X2_MINB_D3Q19_W4 6
 #endif
+// FP32 central and central-Hermite bases: the same caps as the raw kernels.
+// With the central shift applied as a full second cube of moments they
+// spilled 124-168 bytes per thread at these caps; the transported
+// second-order correction (subtract_transported) needs no second cube and
+// they compile without spills at 80 / 96 registers.
+#ifndef RMRT_X2_MINB_D3Q19_W4_CENTRAL
+#define RMRT_X2_MINB_D3Q19_W4_CENTRAL 6
+#endif
 #ifndef RMRT_X2_MINB_D3Q19_W2
 #define RMRT_X2_MINB_D3Q19_W2 8
 #endif
@@ -31,6 +39,9 @@
 #endif
 #ifndef RMRT_X2_MINB_D3Q27_W4
 #define RMRT_X2_MINB_D3Q27_W4 5
+#endif
+#ifndef RMRT_X2_MINB_D3Q27_W4_CENTRAL
+#define RMRT_X2_MINB_D3Q27_W4_CENTRAL 5
 #endif
 #ifndef RMRT_X2_MINB_D3Q27_W2
 #define RMRT_X2_MINB_D3Q27_W2 6
@@ -41,12 +52,16 @@
 
 // The same hint for the four-nodes-per-thread kernel (16-bit storage).  A
 // hint of 1 still changes the compiler's choice (it allows up to 255
-// registers; without a hint it keeps fewer).  Measured (MLUPS, best first):
-//   rD2Q9           9: 170,508   1: 168,989   none: 170,323
-//   rD3Q19 raw      1:  83,456   5:  81,669   none:  82,548
-//   rD3Q19 central  4:  67,137   1:  55,090   none:  65,967
-//   rD3Q27 raw      4:  58,009   1:  57,441   none:  57,624
-//   rD3Q27 central  3:  45,451   1:  41,471   none:  41,766
+// registers; without a hint it keeps fewer).  Measured (MLUPS, FP16 with
+// stochastic rounding, best first):
+//   rD2Q9           9: 168,330   6: 162,976
+//   rD3Q19 raw      1:  78,746   3:  78,659
+//   rD3Q19 central  5:  75,435   4:  70,189   3:  69,221
+//   rD3Q27 raw      4:  59,177   3:  56,261
+//   rD3Q27 central  4:  52,169   3:  51,119   2:  42,802
+// (the central bases at these caps since their collision is the raw one
+// plus a transported second-order correction, which needs no second cube
+// of moments)
 #ifndef RMRT_X4_MINB_D2Q9
 #define RMRT_X4_MINB_D2Q9 9
 #endif
@@ -54,13 +69,13 @@
 #define RMRT_X4_MINB_D3Q19 1
 #endif
 #ifndef RMRT_X4_MINB_D3Q19_CENTRAL
-#define RMRT_X4_MINB_D3Q19_CENTRAL 4
+#define RMRT_X4_MINB_D3Q19_CENTRAL 5
 #endif
 #ifndef RMRT_X4_MINB_D3Q27
 #define RMRT_X4_MINB_D3Q27 4
 #endif
 #ifndef RMRT_X4_MINB_D3Q27_CENTRAL
-#define RMRT_X4_MINB_D3Q27_CENTRAL 3
+#define RMRT_X4_MINB_D3Q27_CENTRAL 4
 #endif
 
 namespace rmrt {
@@ -70,9 +85,9 @@ struct Tuning {
   static constexpr int X2_MIN_BLOCKS =
       BYTES == 8 ? 1
       : LAT == 0 ? (BYTES == 4 ? RMRT_X2_MINB_D2Q9_W4 : RMRT_X2_MINB_D2Q9_W2)
-      : LAT == 1 ? (BYTES == 4 ? RMRT_X2_MINB_D3Q19_W4
+      : LAT == 1 ? (BYTES == 4 ? (CENTRAL ? RMRT_X2_MINB_D3Q19_W4_CENTRAL : RMRT_X2_MINB_D3Q19_W4)
                                : (CENTRAL ? RMRT_X2_MINB_D3Q19_W2_CENTRAL : RMRT_X2_MINB_D3Q19_W2))
-                 : (BYTES == 4 ? RMRT_X2_MINB_D3Q27_W4
+                 : (BYTES == 4 ? (CENTRAL ? RMRT_X2_MINB_D3Q27_W4_CENTRAL : RMRT_X2_MINB_D3Q27_W4)
                                : (CENTRAL ? RMRT_X2_MINB_D3Q27_W2_CENTRAL : RMRT_X2_MINB_D3Q27_W2));
   static constexpr int X4_MIN_BLOCKS =
       LAT == 0 ? RMRT_X4_MINB_D2Q9
