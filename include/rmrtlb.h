@@ -167,6 +167,12 @@ typedef struct {
                             Mach number of about 0.3) and 8 for the NCDE
                             kinds (phi - rho0 of order 1).  Ignored by the
                             other storages. */
+    long long node_offset;/* index of this grid's first node within a larger
+                            grid it is a slab of (rmrtlb_halo_pack): the
+                            16-bit stochastic rounding draws its random bits
+                            from the step and the node's index in the larger
+                            grid, so slabs reproduce the whole grid's run
+                            bit for bit.  0 for a grid of its own. */
 } rmrtlb_params;
 
 typedef struct rmrtlb_solver* rmrtlb_t;   /* opaque, library-owned */
@@ -377,6 +383,44 @@ int rmrtlb_batch_init_fields(rmrtlb_batch_t batch, int domain, const double* rho
 /* rho (one plane) and u (d planes) of one domain; host or device; either
  * may be NULL.  Synchronises. */
 int rmrtlb_batch_fields(rmrtlb_batch_t batch, int domain, double* rho, double* u);
+
+/* ------------------------------------------------ slab decomposition */
+/* A periodic grid cut into slabs along its slowest axis (y on rD2Q9 and
+ * rD2Q5, z on the 3-D lattices), one solver per slab, created with the
+ * slab's own extent and periodic like any grid.  Propagation (Eq. 2-2b)
+ * moves the populations with e_axis = +1 out of a slab's last plane into
+ * the next slab's first, and those with e_axis = -1 the other way.  With
+ * pull streaming a solver keeps each post-collision population at its own
+ * node, and its first plane reads the e = +1 ones through the periodic
+ * wrap from its own last plane, which no other node of the slab reads
+ * (likewise e = -1 at the other end).  So after every rmrtlb_step(solver, 1)
+ * a slab hands those planes round the ring of slabs:
+ *   rmrtlb_halo_pack(s, up, down)   up   <- last plane, e_axis = +1 populations
+ *                                   down <- first plane, e_axis = -1 populations
+ *   send up to the next slab and down to the previous one (periodic ring)
+ *   rmrtlb_halo_unpack(s, from_below, from_above)
+ *                                   the previous slab's up buffer -> the last
+ *                                   plane's e = +1 slots; the next slab's down
+ *                                   buffer -> the first plane's e = -1 slots
+ * after which the slabs together hold exactly the single grid's state.  A
+ * single slab (no neighbours) needs no exchange.  Initialisation needs
+ * none either (rmrtlb_init_equilibrium and rmrtlb_set_populations place
+ * every value where its own node reads it).  Buffers: device memory of
+ * rmrtlb_halo_bytes each (crossing directions in increasing j, one plane
+ * each, x fastest, storage type), caller-owned; pack and unpack are
+ * asynchronous on the solver's stream.  RMRTLB_EINVAL for NULL or host
+ * buffers. */
+int rmrtlb_halo_bytes(rmrtlb_t solver, size_t* bytes);
+int rmrtlb_halo_pack(rmrtlb_t solver, void* up, void* down);
+int rmrtlb_halo_unpack(rmrtlb_t solver, const void* from_below, const void* from_above);
+
+/* Raw sums of the last periodic check, for a reduction over slabs:
+ *   out[0] sum rho (or phi)   out[1..3] momentum   out[4] kinetic energy
+ *   out[5] sum |u - u_prev|^2 (-1 if the check had no previous snapshot)
+ *   out[6] sum |u|^2          out[7] flags
+ * The residual of the whole grid is sqrt(sum out[5] / sum out[6]) over the
+ * slabs.  No check yet: zeros with out[6] = -1.  Synchronises the stream. */
+int rmrtlb_check_sums(rmrtlb_t solver, double out[8]);
 
 /* ------------------------------------------------ allocation-free totals */
 /* The paper has no counterpart to this entry point.  It is for callers that

@@ -193,6 +193,68 @@ cudaError_t run_check(rmrtlb_solver* s, int slot, double* rho_out, double* u_out
   return cudaSuccess;
 }
 
+// ------------------------------------------------------------------ slab faces
+// The axis along which a grid is cut into slabs: y on rD2Q9 / rD2Q5, z on
+// the 3-D lattices.  The populations that cross a face are those with
+// e_axis = +1 (going up) or -1 (going down), in increasing j.
+int slab_axis(const rmrtlb_solver* s) { return s->k.d == 2 ? 1 : 2; }
+
+int crossing(const rmrtlb_solver* s, int sign, int* dirs) {
+  int n = 0;
+  for (int j = 0; j < s->k.q; ++j) {
+    int e[3];
+    lattice_dir(s->k.lat, j, e);
+    if (e[slab_axis(s)] == sign) dirs[n++] = j;
+  }
+  return n;
+}
+
+// Elements of one plane normal to the slab axis, and the offset of plane i.
+size_t plane_elems(const rmrtlb_solver* s) {
+  return s->k.d == 2 ? size_t(s->k.nx) : size_t(s->k.nx) * s->k.ny;
+}
+
+struct FaceCopy {
+  int dirs[9];        // crossing directions
+  int n;              // their count
+  size_t off;         // element offset of the face plane inside a direction's plane
+};
+
+// Gather (to_buf) or scatter one face: buf[k * P + i] <-> f[dirs[k] * N + off + i].
+template <typename E>
+__global__ void face_kernel(E* __restrict__ f, E* __restrict__ buf, FaceCopy fc, size_t N, size_t P, int to_buf) {
+  const size_t total = size_t(fc.n) * P;
+  for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+    const size_t k = t / P, i = t - k * P;
+    E* cell = f + size_t(fc.dirs[k]) * N + fc.off + i;
+    if (to_buf) buf[t] = *cell;
+    else *cell = buf[t];
+  }
+}
+
+cudaError_t face_copy(rmrtlb_solver* s, int sign, void* buf, bool to_buf) {
+  FaceCopy fc;
+  fc.n = crossing(s, sign, fc.dirs);
+  const size_t P = plane_elems(s);
+  // up (+1): the last plane; down (-1): the first
+  const size_t nplanes = s->k.d == 2 ? size_t(s->k.ny) : size_t(s->k.nz);
+  fc.off = sign > 0 ? (nplanes - 1) * P : 0;
+  const size_t total = size_t(fc.n) * P;
+  const int threads = 256;
+  const unsigned blocks = unsigned((total + threads - 1) / threads < 4096 ? (total + threads - 1) / threads : 4096);
+  void* f = pop_ptr(s, s->cur);
+  const size_t N = s->k.N;
+  switch (storage_size(s->k.storage)) {
+    case 8: face_kernel<unsigned long long><<<blocks, threads, 0, s->stream>>>(
+        static_cast<unsigned long long*>(f), static_cast<unsigned long long*>(buf), fc, N, P, to_buf); break;
+    case 4: face_kernel<unsigned><<<blocks, threads, 0, s->stream>>>(
+        static_cast<unsigned*>(f), static_cast<unsigned*>(buf), fc, N, P, to_buf); break;
+    default: face_kernel<unsigned short><<<blocks, threads, 0, s->stream>>>(
+        static_cast<unsigned short*>(f), static_cast<unsigned short*>(buf), fc, N, P, to_buf); break;
+  }
+  return cudaGetLastError();
+}
+
 int read_slot(rmrtlb_solver* s, int slot, double out[8]) {
   double raw[8];
   int flags = 0;
@@ -271,6 +333,7 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
   s->kp64.hist = reinterpret_cast<double*>(s->ws + L.hist);
   s->kp32.hist = reinterpret_cast<float*>(s->ws + L.hist);
   s->kp64.hist_fresh = s->kp32.hist_fresh = 1;
+  s->kp64.node_base = s->kp32.node_base = unsigned((unsigned long long)params->node_offset);
   s->check_every = params->check_every;
   s->pairs = (nx % 2 == 0) && !axis_lattice(lattice) && !simple_ncde(eq_kind);
   s->quads = s->pairs && nx % 4 == 0 &&
@@ -456,6 +519,51 @@ int rmrtlb_last_check(rmrtlb_t s, double out[8]) {
     return RMRTLB_OK;
   }
   return read_slot(s, 0, out);
+}
+
+int rmrtlb_check_sums(rmrtlb_t s, double out[8]) {
+  if (!s || !out) return RMRTLB_EINVAL;
+  for (int i = 0; i < 8; ++i) out[i] = 0.0;
+  if (!s->slot_valid[0]) {
+    out[6] = -1.0;
+    return RMRTLB_OK;
+  }
+  double raw[8];
+  int flags = 0;
+  if (cudaMemcpyAsync(raw, s->ws + s->L.stats, sizeof(raw), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&flags, s->ws + s->L.flags, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return RMRTLB_ECUDA;
+  out[0] = double(s->k.N) * s->k.rho0 + raw[0];
+  out[1] = raw[1]; out[2] = raw[2]; out[3] = raw[3];
+  out[4] = raw[4];
+  out[5] = s->slot_prev[0] ? raw[5] : -1.0;
+  out[6] = raw[6];
+  out[7] = double(flags);
+  return RMRTLB_OK;
+}
+
+int rmrtlb_halo_bytes(rmrtlb_t s, size_t* bytes) {
+  if (!s || !bytes) return RMRTLB_EINVAL;
+  int dirs[9];
+  *bytes = size_t(crossing(s, +1, dirs)) * plane_elems(s) * storage_size(s->k.storage);
+  return RMRTLB_OK;
+}
+
+int rmrtlb_halo_pack(rmrtlb_t s, void* up, void* down) {
+  if (!s || !up || !down || !is_device_ptr(up) || !is_device_ptr(down)) return RMRTLB_EINVAL;
+  if (face_copy(s, +1, up, true) != cudaSuccess || face_copy(s, -1, down, true) != cudaSuccess)
+    return RMRTLB_ECUDA;
+  return RMRTLB_OK;
+}
+
+int rmrtlb_halo_unpack(rmrtlb_t s, const void* from_below, const void* from_above) {
+  if (!s || !from_below || !from_above || !is_device_ptr(from_below) || !is_device_ptr(from_above))
+    return RMRTLB_EINVAL;
+  if (face_copy(s, +1, const_cast<void*>(from_below), false) != cudaSuccess ||
+      face_copy(s, -1, const_cast<void*>(from_above), false) != cudaSuccess)
+    return RMRTLB_ECUDA;
+  return RMRTLB_OK;
 }
 
 }  // extern "C"

@@ -61,6 +61,7 @@ class rmrtlb_params(ctypes.Structure):
         ("source", ctypes.c_double),
         ("check_every", ctypes.c_int),
         ("storage_range", ctypes.c_double),
+        ("node_offset", ctypes.c_longlong),
     ]
 
 
@@ -115,6 +116,10 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_moments": (i, [_vp, _vp, _vp]),
         "rmrtlb_stats": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_last_check": (i, [_vp, ctypes.POINTER(d)]),
+        "rmrtlb_check_sums": (i, [_vp, ctypes.POINTER(d)]),
+        "rmrtlb_halo_bytes": (i, [_vp, ctypes.POINTER(sz)]),
+        "rmrtlb_halo_pack": (i, [_vp, _vp, _vp]),
+        "rmrtlb_halo_unpack": (i, [_vp, _vp, _vp]),
         "rmrtlb_stress": (i, [_vp, _vp, _vp]),
         "rmrtlb_population_totals_noalloc": (i, [i, i, i, i, d, d, d, d, _vp, _vp, _vp]),
         "rmrtlb_batch_workspace_bytes": (i, [i, i, ctypes.POINTER(rmrtlb_domain), i, ctypes.POINTER(sz)]),
@@ -158,7 +163,8 @@ def exported_symbols() -> list:
     return ["rmrtlb_strerror", "rmrtlb_lattice_info", "rmrtlb_workspace_bytes", "rmrtlb_create",
             "rmrtlb_destroy", "rmrtlb_get_constants", "rmrtlb_init_equilibrium",
             "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
-            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_stress", "rmrtlb_population_totals_noalloc",
+            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_check_sums", "rmrtlb_halo_bytes", "rmrtlb_halo_pack",
+            "rmrtlb_halo_unpack", "rmrtlb_stress", "rmrtlb_population_totals_noalloc",
             "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
             "rmrtlb_batch_tune", "rmrtlb_batch_set_launch", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
             "rmrtlb_batch_get_populations", "rmrtlb_batch_fields", "rmrtlb_batch_run", "rmrtlb_batch_init_fields",
@@ -243,6 +249,26 @@ def rmrtlb_last_check(h, allow_unstable: bool = False) -> np.ndarray:
     if not (allow_unstable and st == EUNSTABLE):
         _check(st, "rmrtlb_last_check")
     return np.array(out[:])
+
+
+def rmrtlb_check_sums(h) -> np.ndarray:
+    out = (ctypes.c_double * 8)()
+    _check(lib().rmrtlb_check_sums(h, out), "rmrtlb_check_sums")
+    return np.array(out[:])
+
+
+def rmrtlb_halo_bytes(h) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().rmrtlb_halo_bytes(h, ctypes.byref(b)), "rmrtlb_halo_bytes")
+    return b.value
+
+
+def rmrtlb_halo_pack(h, up: int, down: int):
+    _check(lib().rmrtlb_halo_pack(h, up, down), "rmrtlb_halo_pack")
+
+
+def rmrtlb_halo_unpack(h, from_below: int, from_above: int):
+    _check(lib().rmrtlb_halo_unpack(h, from_below, from_above), "rmrtlb_halo_unpack")
 
 
 def rmrtlb_population_totals_noalloc(lattice, nx, ny, nz, dx, dy, dz, dt, f: int, out: int, stream: int):

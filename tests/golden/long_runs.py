@@ -59,10 +59,11 @@ SHAPE_3D = (64, 64, 32)
 SPACING_3D = (1.0, 1.0, 0.5)
 
 
-def _case_2d(kind):
+def _case_2d(kind, f32_params=False):
     if kind == "nse":
         return Case("D2Q9", SHAPE_2D, SPACING_2D, kind="nse", nu=0.01, nu_bulk=0.02, s_free=1.1, rho0=1.0)
-    return Case("D2Q9", SHAPE_2D, SPACING_2D, kind=kind, diffusivity=0.005, adv=(0.05, 0.02, 0.0),
+    r = (lambda v: float(np.float32(v))) if f32_params else float
+    return Case("D2Q9", SHAPE_2D, SPACING_2D, kind=kind, diffusivity=r(0.005), adv=(r(0.05), r(0.02), 0.0),
                 rho0=0.0, s_free=1.1)
 
 
@@ -86,8 +87,18 @@ CASES = {
     # makes); how far it ends from the unperturbed run is what the discrete
     # problem itself does to an FP32 rounding
     "d2q9_ncde_quad_hill_f32init": (_case_2d("ncde_quad"), 10000, (100, 300, 1000, 3000), (8, 8, 1)),
+    # the same with the state rounded to FP32 at step 1500, after the front
+    # of the quadratic (Burgers) flux has steepened to the grid scale
+    "d2q9_ncde_quad_hill_f32at1500": (_case_2d("ncde_quad"), 10000, (1500, 3000), (8, 8, 1)),
+    # the same with the advection velocity and the diffusivity rounded to
+    # FP32, the precision in which an FP32 implementation holds them
+    "d2q9_ncde_quad_hill_f32params": (_case_2d("ncde_quad", f32_params=True), 10000, (1000, 3000), (8, 8, 1)),
 }
-PERTURBED = {"d2q9_ncde_quad_hill_f32init"}
+# perturbed runs: ("state", step at which the state is rounded to FP32) or
+# ("params", 0) for constants rounded to FP32
+PERTURBED = {"d2q9_ncde_quad_hill_f32init": ("state", 0), "d2q9_ncde_quad_hill_f32at1500": ("state", 1500),
+             "d2q9_ncde_quad_hill_f32params": ("params", 0)}
+ROUNDED_AT = {k: v[1] for k, v in PERTURBED.items() if v[0] == "state"}
 
 
 def initial_fields(case: Case):
@@ -113,7 +124,7 @@ def run(name: str) -> str:
     lat, m, S = case.oracle_setup()
     rho, u = initial_fields(case)
     f = R.init_equilibrium(lat, m, S, rho, u)
-    if name in PERTURBED:
+    if ROUNDED_AT.get(name) == 0:
         f = f.astype(np.float32).astype(np.float64)
     arrays = {}
     t0 = time.time()
@@ -121,6 +132,8 @@ def run(name: str) -> str:
     for s in sorted(snaps) + [steps]:
         f = R.step(lat, m, S, f, s - done)
         done = s
+        if ROUNDED_AT.get(name) == s:
+            f = f.astype(np.float32).astype(np.float64)
         r, v = R.fields(lat, m, f)
         if s == steps:
             arrays["rho"], arrays["u"] = r, v
@@ -131,7 +144,7 @@ def run(name: str) -> str:
             "kind": case.kind, "basis": case.basis, "rho0": case.rho0, "nu": case.nu, "nu_bulk": case.nu_bulk,
             "s_free": case.s_free, "diffusivity": case.diffusivity, "adv": list(case.adv), "steps": steps,
             "snapshots": list(snaps), "stride": list(stride), "cs2": lat.cs2,
-            "initial_populations_rounded_to_f32": name in PERTURBED,
+            "rounded_to_f32_at_step": ROUNDED_AT.get(name),
             "writer": "tests/golden/long_runs.py (FP64 oracle only)", "oracle_seconds": round(time.time() - t0, 1)}
     return store.save(name, meta, arrays)
 
