@@ -414,6 +414,14 @@ int rmrtlb_halo_bytes(rmrtlb_t solver, size_t* bytes);
 int rmrtlb_halo_pack(rmrtlb_t solver, void* up, void* down);
 int rmrtlb_halo_unpack(rmrtlb_t solver, const void* from_below, const void* from_above);
 
+/* Run the periodic FP64 check now, on the current state, into the record
+ * that rmrtlb_last_check and rmrtlb_check_sums read (the residual is taken
+ * against the previous check's snapshot, which this call replaces), as
+ * rmrtlb_step does every check_every steps.  For slabs, which must check
+ * after their exchange: create them with check_every = 0 and call this
+ * after rmrtlb_halo_unpack.  Asynchronous on the solver's stream. */
+int rmrtlb_check(rmrtlb_t solver);
+
 /* Raw sums of the last periodic check, for a reduction over slabs:
  *   out[0] sum rho (or phi)   out[1..3] momentum   out[4] kinetic energy
  *   out[5] sum |u - u_prev|^2 (-1 if the check had no previous snapshot)

@@ -521,6 +521,11 @@ int rmrtlb_last_check(rmrtlb_t s, double out[8]) {
   return read_slot(s, 0, out);
 }
 
+int rmrtlb_check(rmrtlb_t s) {
+  if (!s) return RMRTLB_EINVAL;
+  return run_check(s, 0, nullptr, nullptr, true, true) == cudaSuccess ? RMRTLB_OK : RMRTLB_ECUDA;
+}
+
 int rmrtlb_check_sums(rmrtlb_t s, double out[8]) {
   if (!s || !out) return RMRTLB_EINVAL;
   for (int i = 0; i < 8; ++i) out[i] = 0.0;

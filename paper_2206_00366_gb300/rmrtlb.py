@@ -116,6 +116,7 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_moments": (i, [_vp, _vp, _vp]),
         "rmrtlb_stats": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_last_check": (i, [_vp, ctypes.POINTER(d)]),
+        "rmrtlb_check": (i, [_vp]),
         "rmrtlb_check_sums": (i, [_vp, ctypes.POINTER(d)]),
         "rmrtlb_halo_bytes": (i, [_vp, ctypes.POINTER(sz)]),
         "rmrtlb_halo_pack": (i, [_vp, _vp, _vp]),
@@ -163,7 +164,7 @@ def exported_symbols() -> list:
     return ["rmrtlb_strerror", "rmrtlb_lattice_info", "rmrtlb_workspace_bytes", "rmrtlb_create",
             "rmrtlb_destroy", "rmrtlb_get_constants", "rmrtlb_init_equilibrium",
             "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
-            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_check_sums", "rmrtlb_halo_bytes", "rmrtlb_halo_pack",
+            "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_check", "rmrtlb_check_sums", "rmrtlb_halo_bytes", "rmrtlb_halo_pack",
             "rmrtlb_halo_unpack", "rmrtlb_stress", "rmrtlb_population_totals_noalloc",
             "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
             "rmrtlb_batch_tune", "rmrtlb_batch_set_launch", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
@@ -249,6 +250,10 @@ def rmrtlb_last_check(h, allow_unstable: bool = False) -> np.ndarray:
     if not (allow_unstable and st == EUNSTABLE):
         _check(st, "rmrtlb_last_check")
     return np.array(out[:])
+
+
+def rmrtlb_check(h):
+    _check(lib().rmrtlb_check(h), "rmrtlb_check")
 
 
 def rmrtlb_check_sums(h) -> np.ndarray:

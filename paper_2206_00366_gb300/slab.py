@@ -97,6 +97,11 @@ class Slab:
         # draws the same random bits as the whole grid would
         p = dict(params or {})
         p["node_offset"] = off * (nx if d == 2 else nx * ny)
+        # the periodic check must see the state after the exchange: the slab
+        # runs it itself (rmrtlb_check) instead of inside rmrtlb_step
+        self.check_every = int(p.get("check_every", 0))
+        p["check_every"] = 0
+        self.steps = 0
         self.solver = B.Solver(lattice, local, spacing, dt, p, eq_kind, basis, storage, device=device)
         nbytes = B.rmrtlb_halo_bytes(self.solver.h)
         self.bufs = [torch.empty(nbytes, dtype=torch.uint8, device=device) for _ in range(4)]
@@ -115,6 +120,13 @@ class Slab:
         if u is not None:
             lu = np.ascontiguousarray(self.local(u)) if isinstance(u, np.ndarray) else self.local(u).contiguous()
         self.solver.init_equilibrium(lr, lu)
+        self.steps = 0
+
+    def after_exchange(self):
+        """Count the step and run the periodic check when one is due."""
+        self.steps += 1
+        if self.check_every > 0 and self.steps % self.check_every == 0:
+            B.rmrtlb_check(self.solver.h)
 
     def pack(self):
         up, down = self.bufs[0], self.bufs[1]
@@ -129,13 +141,13 @@ class Slab:
         import torch
         for _ in range(n):
             self.solver.step(1)
-            if self.world == 1:
-                continue
-            up, down = self.pack()
-            with torch.cuda.stream(self.solver.stream):
-                # the library's pack and unpack run on the solver's stream, and so does the exchange
-                ring_exchange(up, down, self.bufs[2], self.bufs[3], self.rank, self.world, self.group)
-            self.unpack(self.bufs[2], self.bufs[3])
+            if self.world > 1:
+                up, down = self.pack()
+                with torch.cuda.stream(self.solver.stream):
+                    # the library's pack and unpack run on the solver's stream, and so does the exchange
+                    ring_exchange(up, down, self.bufs[2], self.bufs[3], self.rank, self.world, self.group)
+                self.unpack(self.bufs[2], self.bufs[3])
+            self.after_exchange()
 
     def moments(self, rho=None, u=None):
         return self.solver.moments(rho, u)
@@ -184,13 +196,14 @@ class LocalSlabs:
         for _ in range(n):
             for s in self.slabs:
                 s.solver.step(1)
-            if w == 1:
-                continue
-            packed = [s.pack() for s in self.slabs]
-            torch.cuda.synchronize()
-            for r, s in enumerate(self.slabs):
-                s.unpack(packed[(r - 1) % w][0], packed[(r + 1) % w][1])
-            torch.cuda.synchronize()
+            if w > 1:
+                packed = [s.pack() for s in self.slabs]
+                torch.cuda.synchronize()
+                for r, s in enumerate(self.slabs):
+                    s.unpack(packed[(r - 1) % w][0], packed[(r + 1) % w][1])
+                torch.cuda.synchronize()
+            for s in self.slabs:
+                s.after_exchange()
 
     def moments(self):
         """Global (rho, u) assembled from the slabs."""
