@@ -93,11 +93,14 @@ CASES = {
     # the same with the advection velocity and the diffusivity rounded to
     # FP32, the precision in which an FP32 implementation holds them
     "d2q9_ncde_quad_hill_f32params": (_case_2d("ncde_quad", f32_params=True), 10000, (1000, 3000), (8, 8, 1)),
+    # the same with the populations rounded to FP32 after every step: what
+    # storing them in FP32 (round to nearest) does to the run
+    "d2q9_ncde_quad_hill_f32every": (_case_2d("ncde_quad"), 10000, (1000, 3000), (8, 8, 1)),
 }
 # perturbed runs: ("state", step at which the state is rounded to FP32) or
 # ("params", 0) for constants rounded to FP32
 PERTURBED = {"d2q9_ncde_quad_hill_f32init": ("state", 0), "d2q9_ncde_quad_hill_f32at1500": ("state", 1500),
-             "d2q9_ncde_quad_hill_f32params": ("params", 0)}
+             "d2q9_ncde_quad_hill_f32params": ("params", 0), "d2q9_ncde_quad_hill_f32every": ("every", 0)}
 ROUNDED_AT = {k: v[1] for k, v in PERTURBED.items() if v[0] == "state"}
 
 
@@ -129,8 +132,13 @@ def run(name: str) -> str:
     arrays = {}
     t0 = time.time()
     done = 0
+    every = PERTURBED.get(name, ("", 0))[0] == "every"
     for s in sorted(snaps) + [steps]:
-        f = R.step(lat, m, S, f, s - done)
+        if every:
+            for _ in range(s - done):
+                f = R.step(lat, m, S, f, 1).astype(np.float32).astype(np.float64)
+        else:
+            f = R.step(lat, m, S, f, s - done)
         done = s
         if ROUNDED_AT.get(name) == s:
             f = f.astype(np.float32).astype(np.float64)
@@ -144,7 +152,7 @@ def run(name: str) -> str:
             "kind": case.kind, "basis": case.basis, "rho0": case.rho0, "nu": case.nu, "nu_bulk": case.nu_bulk,
             "s_free": case.s_free, "diffusivity": case.diffusivity, "adv": list(case.adv), "steps": steps,
             "snapshots": list(snaps), "stride": list(stride), "cs2": lat.cs2,
-            "rounded_to_f32_at_step": ROUNDED_AT.get(name),
+            "rounded_to_f32_at_step": ROUNDED_AT.get(name), "rounded_to_f32_every_step": every,
             "writer": "tests/golden/long_runs.py (FP64 oracle only)", "oracle_seconds": round(time.time() - t0, 1)}
     return store.save(name, meta, arrays)
 

@@ -82,7 +82,8 @@ def sensitivity(name):
     perturbations (its stored perturbed runs), as an error a run that
     rounds to FP32 cannot avoid: a state rounded once at step a moves the
     end result by m, and roundings at every later step add up to about
-    sqrt(steps - a) m; constants rounded to FP32 move it by m itself.
+    sqrt(steps - a) m; constants rounded to FP32, or the populations rounded
+    to FP32 after every step, move it by m itself.
     Returns (that figure, a description), or (0, "") for a case without
     perturbed runs."""
     best = (0.0, "")
@@ -96,6 +97,8 @@ def sensitivity(name):
             n = int(meta["steps"]) - int(at)
             cand = (np.sqrt(n) * move, f"one FP32 rounding of the state at step {at} moves it {move:.2e}, "
                                        f"sqrt({n}) times that is {np.sqrt(n) * move:.2e}")
+        elif kind == "every":
+            cand = (move, f"its populations rounded to FP32 after every step move it {move:.2e}")
         else:
             cand = (move, f"its constants rounded to FP32 move it {move:.2e}")
         best = max(best, cand)
