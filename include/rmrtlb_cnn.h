@@ -59,16 +59,24 @@ int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout,
                                 const float* dy, const uint16_t* weight, const float* z_in,
                                 float* dx, void* scratch, size_t scratch_bytes, void* stream);
 
-/* Bytes of device scratch rmrtlb_conv3d_backward_weight needs (host only). */
+/* Bytes of device scratch rmrtlb_conv3d_backward_weight needs (host only):
+ * per-chunk partial sums of dweight and dbias, and for cout = 32 on planes
+ * that hold a 128-voxel box a BF16 copy of dy. */
 size_t rmrtlb_conv3d_backward_weight_scratch(int n, int d, int h, int w, int cin, int cout);
 
 /* Gradient with respect to the weights and the bias, all three channel
  * pairs: dweight[t, ci, co] = sum_v x[v + tap_t, ci] dy[v, co] on the tensor
- * cores (a GEMM with K = voxels, M = taps x cin, both operands staged
- * MN-major in shared memory; dy rounded to BF16), dbias[co] = sum_v dy[v,
- * co] on the FP32 pipes; FP32 results summed in a fixed order (partial sums
- * per chunk of 4096 voxels, then over chunks), so repeated calls give
- * bitwise the same result. */
+ * cores (a GEMM with K = voxels, M = taps x cin, both operands MN-major in
+ * shared memory; dy rounded to BF16, nearest even), dbias[co] = sum_v dy[v,
+ * co] on the FP32 pipes.  For cout = 32 on planes that hold a 128-voxel
+ * box the operands are brought by the tensor-memory accelerator box by box
+ * (dy first rounded into the scratch) and dweight is summed per chunk of
+ * 32 boxes; otherwise threads gather them and dweight is summed per chunk
+ * of 4096 voxels; dbias is summed per chunk of 1024 voxels.  The partial
+ * sums are then added over the chunks in a fixed order, so repeated calls
+ * give bitwise the same result.  x, dy and scratch 16-byte aligned; scratch
+ * at least rmrtlb_conv3d_backward_weight_scratch bytes (else
+ * RMRTLB_ENOMEM). */
 int rmrtlb_conv3d_backward_weight(int n, int d, int h, int w, int cin, int cout,
                                   const uint16_t* x, const float* dy, float* dweight, float* dbias,
                                   void* scratch, size_t scratch_bytes, void* stream);

@@ -21,6 +21,7 @@
 namespace {
 
 constexpr int kWeightChunk = 4096;   // voxels per partial sum of the weight gradient
+constexpr int kBiasChunk = 1024;     // voxels per partial sum of the bias gradient
 
 struct Vol {
   int n, d, h, w;
@@ -694,17 +695,214 @@ __global__ void __launch_bounds__(kTcThreads) conv_wgrad_tc_kernel(Vol g, const 
   if (warp == 0) tc::tmem_dealloc(taddr, 32);
 }
 
-// Bias gradient partials: bpart[c * COUT + co] = sum over chunk c of dy[v, co].
-template <int COUT>
-__global__ void bias_grad_kernel(Vol g, const float* __restrict__ dy, float* __restrict__ bpart) {
-  const int co = threadIdx.x;
-  if (co >= COUT) return;
+// ------------------------------------------------------------------ backward weight, fed by the tensor-memory accelerator
+// The same GEMM, D[(t, ci), co] = sum_v x[v + tap_t, ci] dy[v, co], with K =
+// voxels taken box by box: a K tile is a BW x BH box of one (image, z)
+// plane (the forward kernel's output boxes), and a chunk is kWgTiles
+// consecutive boxes.  For every tap of the group the copy engine brings the
+// box of x shifted by the tap, and the box of a BF16 copy of dy; both are
+// MN-major operands (a voxel's channels are contiguous, voxels run along K).
+// 32 channels come as one copy of 128 rows x 64 bytes with the 64-byte
+// swizzle (8-voxel atoms of 512 bytes, taps 8 KB apart along M); 8 channels
+// as one copy of 128 rows x 16 bytes without swizzle (core matrices of 8
+// voxels x 8 channels, 128 bytes apart along K and 2 KB along M).  Rows of
+// 64 bytes move four times the data per row the copy engine handles.
+// Out-of-range coordinates read as zero: the zero padding, and zero dy on
+// the padded voxels of a ragged box.  Warp roles as in the forward kernel:
+// warp 4 lane 0 issues the copies into a ring of WG_STAGES buffers, warp 5
+// lane 0 the MMAs (M = TPG taps x CIN channels = 128, N = 32 output
+// channels, K = 16 voxels each, one commit per buffer), warps 0-3 read the
+// accumulator at the end of the chunk.  Every wait is bounded.
+#ifndef RMRT_WG_STAGES
+#define RMRT_WG_STAGES 2
+#endif
+constexpr int kWgTiles = 32;                            // boxes (K tiles of 128 voxels) per chunk
+
+template <int CIN>
+struct WgTmaShape {
+  static constexpr bool SW64 = CIN == 32;
+  static constexpr int TPG = 128 / CIN;                 // taps per group (M = 128)
+  static constexpr int GROUPS = (27 + TPG - 1) / TPG;
+  static constexpr int A_TAP = 128 * CIN * 2;           // one tap's box of x
+  static constexpr int A_BYTES = TPG * A_TAP;           // 32 KB
+  static constexpr int B_BYTES = 128 * 32 * 2;          // the box of dy
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int STAGES = RMRT_WG_STAGES;
+  static constexpr int OFF_BAR = STAGES * STAGE;
+  static constexpr int NBAR = 2 * STAGES + 1;
+  static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16 + 1024;
+};
+
+template <int CIN>
+__global__ void __launch_bounds__(kTmaThreads) conv_wgrad_tma_kernel(const __grid_constant__ CUtensorMap tx,
+                                                                     const __grid_constant__ CUtensorMap tdy, Vol g,
+                                                                     int bw, int bh, float* __restrict__ part) {
+  using S = WgTmaShape<CIN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
+  uint64_t* empty = full + S::STAGES;
+  uint64_t* accf = empty + S::STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int chunk = blockIdx.x, group = blockIdx.y;
+  const int ntap = (group + 1) * S::TPG <= 27 ? S::TPG : 27 - group * S::TPG;   // taps of this group
+  // the A blocks of the group's missing taps are never copied: zero them
+  // once (they only feed accumulator rows that are not written out)
+  for (int st = 0; st < S::STAGES; ++st)
+    for (int i = tid; i < (S::TPG - ntap) * S::A_TAP / 16; i += kTmaThreads)
+      reinterpret_cast<uint4*>(smem + st * S::STAGE + ntap * S::A_TAP)[i] = make_uint4(0, 0, 0, 0);
+  if (warp == 5) tc::tmem_alloc(tslot, 32);
+  if (tid == 0) {
+    for (int k = 0; k < S::STAGES; ++k) {
+      tc::mbar_init(&full[k], 1);
+      tc::mbar_init(&empty[k], 1);
+    }
+    tc::mbar_init(&accf[0], 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t taddr = *tslot;
+  const int tx_n = (g.w + bw - 1) / bw, ty_n = (g.h + bh - 1) / bh;
+  const long long tiles = (long long)g.n * g.d * ty_n * tx_n;
+  const long long k0 = (long long)chunk * kWgTiles;
+  const int nk = int(tiles - k0 < kWgTiles ? tiles - k0 : kWgTiles);
+
+  if (warp == 4) {
+    if (lane == 0) {                       // copies
+      const uint32_t bytes = uint32_t(ntap * S::A_TAP + S::B_BYTES);
+      bool ok = true;
+      int issued = 0;
+      for (int kt = 0; kt < nk; ++kt) {
+        const int st = kt % S::STAGES;
+        const int round = kt / S::STAGES;
+        if (round > 0 && !mbar_wait_or_abort(&empty[st], (round - 1) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        const TileAt p = tile_at(k0 + kt, g, bw, bh, tx_n, ty_n);
+        uint8_t* base = smem + st * S::STAGE;
+        tc::mbar_expect_tx(&full[st], bytes);
+        for (int tl = 0; tl < ntap; ++tl) {
+          const int t = group * S::TPG + tl;
+          const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+          tc::tma_load_5d(base + tl * S::A_TAP, &tx, &full[st], 0, p.x0 + dx, p.y0 + dy, p.z + dz, p.n);
+        }
+        tc::tma_load_5d(base + S::A_BYTES, &tdy, &full[st], 0, p.x0, p.y0, p.z, p.n);
+        ++issued;
+      }
+      if (!ok) {
+        *abort = 1;
+        atomicExch(&g_tc_error, 1);
+      }
+      // no copy may still be writing shared memory when the block exits
+      for (int k = issued > S::STAGES ? issued - S::STAGES : 0; k < issued; ++k)
+        tc::mbar_wait(&full[k % S::STAGES], (k / S::STAGES) & 1, kTmaWaitLimit);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {                       // MMAs
+      const uint32_t idesc = tc::idesc_bf16(32, true);
+      bool ok = true;
+      int done = 0;
+      for (int kt = 0; kt < nk; ++kt) {
+        const int st = kt % S::STAGES;
+        if (!mbar_wait_or_abort(&full[st], (kt / S::STAGES) & 1, abort)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t abase = tc::smem_u32(smem + st * S::STAGE);
+        const uint32_t bbase = abase + S::A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {                       // 16 voxels per MMA
+          uint64_t ad;
+          if constexpr (S::SW64)
+            ad = tc::smem_desc_sw64_mn(abase + kk * 1024, S::A_TAP, 512);
+          else
+            ad = tc::smem_desc(abase + kk * 256, 128, S::A_TAP);
+          // N = 32 is one swizzle atom wide: the M-direction stride is never used
+          const uint64_t bd = tc::smem_desc_sw64_mn(bbase + kk * 1024, 512, 512);
+          tc::mma_bf16(taddr, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&empty[st]);
+        ++done;
+      }
+      if (ok && nk > 0) tc::mma_commit(&accf[0]);
+      if (!ok) {
+        *abort = 1;
+        atomicExch(&g_tc_error, 1);
+      }
+      // the last MMAs must have completed before the accumulator is released
+      if (done > 0) tc::mbar_wait(&empty[(done - 1) % S::STAGES], ((done - 1) / S::STAGES) & 1, kTmaWaitLimit);
+    }
+  } else {                                 // epilogue: warps 0-3, one accumulator row (tap, ci) per thread
+    const bool have = nk > 0 && mbar_wait_or_abort(&accf[0], 0, abort);
+    if (nk > 0 && !have && lane == 0) atomicExch(&g_tc_error, 1);
+    tc::fence_after();
+    float acc[32];
+    if (have) {
+      const uint32_t lane_base = uint32_t(warp * 32) << 16;
+      tc::tmem_ld16(taddr + lane_base, *reinterpret_cast<float(*)[16]>(acc));
+      tc::tmem_ld16(taddr + lane_base + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+    }
+    const int m = tid, tl = m / CIN, ci = m % CIN, t = group * S::TPG + tl;
+    if (tl < ntap) {
+      float* out = part + (size_t(chunk) * 27 + t) * CIN * 32 + size_t(ci) * 32;
+#pragma unroll
+      for (int co = 0; co < 32; ++co) out[co] = have ? acc[co] : 0.0f;
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 5) tc::tmem_dealloc(taddr, 32);
+}
+
+// Bias gradient partials, bpart[c * COUT + co] = sum of dy[v, co] over the
+// kBiasChunk voxels of chunk c, and with BF16 the copy of dy rounded to
+// BF16 (nearest even) that the copy-fed kernels read.  256 threads read the
+// chunk's dy as consecutive float4 (COUT a multiple of 4 dividing 1024, so a
+// thread always meets the same four channels); the 256 / (COUT / 4) partial
+// sums of a channel are then added in a fixed order.
+template <int COUT, bool BF16>
+__global__ void __launch_bounds__(256) bias_grad_kernel(Vol g, const float* __restrict__ dy,
+                                                        float* __restrict__ bpart, uint2* __restrict__ dy16) {
+  static_assert(COUT % 4 == 0 && 1024 % COUT == 0, "four channels per float4, fixed per thread");
+  __shared__ float4 red[256];
+  const int tid = threadIdx.x;
   const long long V = g.voxels();
-  const long long v0 = (long long)blockIdx.x * kWeightChunk;
-  const long long v1 = v0 + kWeightChunk < V ? v0 + kWeightChunk : V;
-  float s = 0.0f;
-  for (long long v = v0; v < v1; ++v) s += dy[v * COUT + co];
-  bpart[size_t(blockIdx.x) * COUT + co] = s;
+  const long long v0 = (long long)blockIdx.x * kBiasChunk;
+  const long long v1 = v0 + kBiasChunk < V ? v0 + kBiasChunk : V;
+  const long long i1 = v1 * (COUT / 4);
+  const float4* src = reinterpret_cast<const float4*>(dy);
+  float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 4
+  for (long long i = v0 * (COUT / 4) + tid; i < i1; i += 256) {
+    const float4 v = src[i];
+    acc.x += v.x;
+    acc.y += v.y;
+    acc.z += v.z;
+    acc.w += v.w;
+    if constexpr (BF16)
+      dy16[i] = make_uint2(uint32_t(f2bf(v.x)) | (uint32_t(f2bf(v.y)) << 16),
+                           uint32_t(f2bf(v.z)) | (uint32_t(f2bf(v.w)) << 16));
+  }
+  red[tid] = acc;
+  __syncthreads();
+  if (tid < COUT / 4) {
+    float4 t = red[tid];
+    for (int k = tid + COUT / 4; k < 256; k += COUT / 4) {
+      t.x += red[k].x;
+      t.y += red[k].y;
+      t.z += red[k].z;
+      t.w += red[k].w;
+    }
+    reinterpret_cast<float4*>(bpart + size_t(blockIdx.x) * COUT)[tid] = t;
+  }
 }
 
 // Fixed-order sum over chunks: out[i] = sum_c part[c * stride + i], i < n.
@@ -973,6 +1171,32 @@ size_t bwd_data_scratch(const Vol& g, int cout) {
 }
 
 int chunks_of(Vol g) { return int((g.voxels() + kWeightChunk - 1) / kWeightChunk); }
+int bias_chunks_of(Vol g) { return int((g.voxels() + kBiasChunk - 1) / kBiasChunk); }
+
+// Scratch of the weight gradient: chunk partials of dw (for the flat
+// kWeightChunk-voxel chunks of the gathering kernel or the box chunks of
+// the copy-fed one, whichever are more), chunk partials of db, and, where
+// the copy-fed kernel runs (32 output channels, planes that hold a box), a
+// BF16 copy of dy; every part starts at a 16-byte boundary.
+struct WgScratch {
+  size_t part, bpart, dy16_off, total;
+  long long box_chunks;
+};
+WgScratch wgrad_scratch(const Vol& g, int cin, int cout) {
+  WgScratch w{};
+  const long long flat = chunks_of(g);
+  int bw = 0, bh = 0;
+  if (cout == 32 && (cin == 8 || cin == 32) && pick_box(g, bw, bh)) {
+    const long long tiles = (long long)g.n * g.d * ((g.h + bh - 1) / bh) * ((g.w + bw - 1) / bw);
+    w.box_chunks = (tiles + kWgTiles - 1) / kWgTiles;
+  }
+  const long long parts = flat > w.box_chunks ? flat : w.box_chunks;
+  w.part = size_t(parts) * 27 * size_t(cin) * cout * sizeof(float);
+  w.bpart = size_t(bias_chunks_of(g)) * cout * sizeof(float);
+  w.dy16_off = (w.part + w.bpart + 15) / 16 * 16;
+  w.total = w.box_chunks > 0 ? w.dy16_off + size_t(g.voxels()) * 32 * 2 : w.part + w.bpart;
+  return w;
+}
 
 template <int CIN, int COUT>
 int wgrad_tc(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, float* scratch, cudaStream_t s) {
@@ -981,17 +1205,55 @@ int wgrad_tc(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, fl
   if (cudaFuncSetAttribute(conv_wgrad_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
       cudaSuccess)
     return RMRTLB_ECUDA;
-  const int chunks = chunks_of(g);
+  const int chunks = chunks_of(g), bchunks = bias_chunks_of(g);
   float* part = scratch;
-  float* bpart = scratch + size_t(chunks) * 27 * CIN * COUT;
+  float* bpart = scratch + wgrad_scratch(g, CIN, COUT).part / sizeof(float);
   conv_wgrad_tc_kernel<CIN, COUT><<<dim3(chunks, S::GROUPS), kTcThreads, S::SMEM, s>>>(g, x, dy, part);
-  bias_grad_kernel<COUT><<<chunks, 32, 0, s>>>(g, dy, bpart);
+  bias_grad_kernel<COUT, false><<<bchunks, 256, 0, s>>>(g, dy, bpart, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return RMRTLB_ECUDA;
   const int nw = 27 * CIN * COUT;
   sum_chunks_kernel<<<blocks_for(nw, 256), 256, 0, s>>>(part, chunks, size_t(nw), nw, dw);
-  sum_chunks_kernel<<<1, 256, 0, s>>>(bpart, chunks, size_t(COUT), COUT, db);
+  sum_chunks_kernel<<<1, 256, 0, s>>>(bpart, bchunks, size_t(COUT), COUT, db);
   return status_of(cudaGetLastError());
+}
+
+// The copy-fed weight gradient (32 output channels).  Returns false, having
+// launched nothing, where it does not apply (no box fits the plane, the
+// scratch is short, or a tensor map cannot be made); else true with the
+// status in *status.
+template <int CIN>
+bool wgrad_tma(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, char* scratch, size_t scratch_bytes,
+               cudaStream_t s, int* status) {
+  using S = WgTmaShape<CIN>;
+  const WgScratch w = wgrad_scratch(g, CIN, 32);
+  int bw = 0, bh = 0;
+  if (w.box_chunks == 0 || scratch_bytes < w.total || !pick_box(g, bw, bh)) return false;
+  uint16_t* dy16 = reinterpret_cast<uint16_t*>(scratch + w.dy16_off);
+  CUtensorMap tx, tdy;
+  if (!make_tmap<CIN>(&tx, g, x, bw, bh) || !make_tmap<32>(&tdy, g, dy16, bw, bh)) return false;
+  // the opt-in to more than 48 KB of shared memory holds per device: set it on every call
+  if (cudaFuncSetAttribute(conv_wgrad_tma_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
+      cudaSuccess) {
+    *status = RMRTLB_ECUDA;
+    return true;
+  }
+  float* part = reinterpret_cast<float*>(scratch);
+  float* bpart = reinterpret_cast<float*>(scratch + w.part);
+  const int bchunks = bias_chunks_of(g);
+  // one pass over dy: the bias partials and the BF16 copy the copies read
+  bias_grad_kernel<32, true><<<bchunks, 256, 0, s>>>(g, dy, bpart, reinterpret_cast<uint2*>(dy16));
+  conv_wgrad_tma_kernel<CIN><<<dim3(unsigned(w.box_chunks), S::GROUPS), kTmaThreads, S::SMEM, s>>>(tx, tdy, g, bw,
+                                                                                                  bh, part);
+  if (cudaGetLastError() != cudaSuccess) {
+    *status = RMRTLB_ECUDA;
+    return true;
+  }
+  const int nw = 27 * CIN * 32;
+  sum_chunks_kernel<<<blocks_for(nw, 256), 256, 0, s>>>(part, int(w.box_chunks), size_t(nw), nw, dw);
+  sum_chunks_kernel<<<1, 256, 0, s>>>(bpart, bchunks, size_t(32), 32, db);
+  *status = status_of(cudaGetLastError());
+  return true;
 }
 
 // An mbarrier that nothing arrives on, waited for with the convolutions'
@@ -1054,19 +1316,27 @@ int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout, c
 
 size_t rmrtlb_conv3d_backward_weight_scratch(int n, int d, int h, int w, int cin, int cout) {
   if (!vol_ok(n, d, h, w) || cin < 1 || cout < 1) return 0;
-  const size_t chunks = size_t(chunks_of(Vol{n, d, h, w}));
-  return (chunks * 27 * size_t(cin) * cout + chunks * cout) * sizeof(float);
+  return wgrad_scratch(Vol{n, d, h, w}, cin, cout).total;
 }
 
 int rmrtlb_conv3d_backward_weight(int n, int d, int h, int w, int cin, int cout, const uint16_t* x, const float* dy,
                                   float* dweight, float* dbias, void* scratch, size_t scratch_bytes, void* stream) {
-  if (!vol_ok(n, d, h, w) || !x || !dy || !dweight || !dbias || !scratch) return RMRTLB_EINVAL;
+  if (!vol_ok(n, d, h, w) || !aligned16(x) || !aligned16(dy) || !dweight || !dbias || !aligned16(scratch))
+    return RMRTLB_EINVAL;
   if (scratch_bytes < rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, cout)) return RMRTLB_ENOMEM;
   const Vol g{n, d, h, w};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float* sc = static_cast<float*>(scratch);
-  if (cin == 8 && cout == 32) return wgrad_tc<8, 32>(g, x, dy, dweight, dbias, sc, s);
-  if (cin == 32 && cout == 32) return wgrad_tc<32, 32>(g, x, dy, dweight, dbias, sc, s);
+  char* raw = static_cast<char*>(scratch);
+  int status = RMRTLB_OK;
+  if (cin == 8 && cout == 32) {
+    if (wgrad_tma<8>(g, x, dy, dweight, dbias, raw, scratch_bytes, s, &status)) return status;
+    return wgrad_tc<8, 32>(g, x, dy, dweight, dbias, sc, s);
+  }
+  if (cin == 32 && cout == 32) {
+    if (wgrad_tma<32>(g, x, dy, dweight, dbias, raw, scratch_bytes, s, &status)) return status;
+    return wgrad_tc<32, 32>(g, x, dy, dweight, dbias, sc, s);
+  }
   if (cin == 32 && cout == 4) return wgrad_tc<32, 4>(g, x, dy, dweight, dbias, sc, s);
   return RMRTLB_EINVAL;
 }

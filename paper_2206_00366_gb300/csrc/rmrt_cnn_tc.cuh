@@ -56,6 +56,20 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr, uint32_t sbo) 
   return d;
 }
 
+// The same for an MN-major operand stored with the 64-byte swizzle (each
+// K index a 64-byte row of 32 consecutive M (N) elements, 8 rows = one
+// 512-byte atom): LBO = the stride between 32-element groups along M (N),
+// SBO = the stride between 8-row groups along K, layout type 4.
+__device__ __forceinline__ uint64_t smem_desc_sw64_mn(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((addr & 0x3FFFF) >> 4);
+  d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;
+  d |= uint64_t(1) << 46;
+  d |= uint64_t(4) << 61;
+  return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
 // K-major (or, with mn_major, both MN-major), M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n, bool mn_major = false) {

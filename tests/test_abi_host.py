@@ -141,3 +141,29 @@ def test_bgk_limit_constants(B):
     c = B.rmrtlb_get_constants(h)
     B.rmrtlb_destroy(h)
     np.testing.assert_allclose(c[35:44].reshape(3, 3)[:2, :2], s * np.eye(2), atol=1e-14)
+
+
+def test_convolution_scratch_bytes(B):
+    """Scratch of the weight gradient: FP32 partial sums of dweight per
+    4096-voxel chunk or per 32 boxes of 128 voxels (whichever are more),
+    of dbias per 1024 voxels, and for 32 output channels on a plane that
+    holds a box a 16-byte aligned BF16 copy of dy; the input gradient's
+    scratch is that copy alone."""
+    ceil = lambda a, b: -(-a // b)
+    # 5 x 6 planes hold no 128-voxel box: the threads gather, no dy copy
+    n, d, h, w = 2, 5, 6, 13
+    v = n * d * h * w
+    for cin, cout in ((8, 32), (32, 32), (32, 4)):
+        assert B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, cout) == \
+            4 * (ceil(v, 4096) * 27 * cin * cout + ceil(v, 1024) * cout)
+        assert B.rmrtlb_conv3d_backward_data_scratch(n, d, h, w, cin, cout) == 0
+    # 64 x 64 planes: 64 x 2 boxes, 4 * 32 * 32 boxes in 128 chunks of 32
+    n, d, h, w = 4, 32, 64, 64
+    v = n * d * h * w
+    for cin in (8, 32):
+        parts = 4 * (max(ceil(v, 4096), 128) * 27 * cin * 32 + ceil(v, 1024) * 32)
+        assert B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, 32) == ceil(parts, 16) * 16 + v * 64
+    assert B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, 32, 4) == \
+        4 * (ceil(v, 4096) * 27 * 32 * 4 + ceil(v, 1024) * 4)
+    assert B.rmrtlb_conv3d_backward_data_scratch(n, d, h, w, 32, 32) == v * 64
+    assert B.rmrtlb_conv3d_backward_weight_scratch(0, d, h, w, 32, 32) == 0

@@ -149,13 +149,18 @@ def test_conv_backward_data(cin, cout, with_z, shape, use_scratch):
     assert normwise(host(dx), ref) <= 1e-5
 
 
+@pytest.mark.parametrize("shape", [(2, 8, 16, 40)] + TMA_SHAPES + [SHAPE])
 @pytest.mark.parametrize("cin,cout", PAIRS)
-def test_conv_backward_weight(cin, cout):
-    """Spans three 4096-voxel partial-sum chunks (the last one ragged);
-    repeated calls are bitwise equal."""
+def test_conv_backward_weight(cin, cout, shape):
+    """(2, 8, 16, 40) spans three 4096-voxel partial-sum chunks of the
+    gathering kernel (4 output channels) and three 32-box chunks of the
+    copy-fed one (8 x 16 boxes, the last chunk ragged); the other planes
+    take every box shape the copy-fed kernel picks, ragged in x, y or both,
+    and SHAPE a plane too small for a box.  Repeated calls are bitwise
+    equal."""
     import torch
     from paper_2206_00366_gb300 import rmrtlb as B
-    n, d, h, w = 2, 8, 16, 40       # 10240 voxels
+    n, d, h, w = shape
     rng = np.random.default_rng(11 + cin)
     xg, x = bf16(rng.normal(size=(n, d, h, w, cin)))
     dy = rng.normal(size=(n, d, h, w, cout)).astype(np.float32)
@@ -311,17 +316,17 @@ def test_training_learns_solver_states():
     assert float(err) < 0.2, float(err)
 
 
-def test_trained_warm_start_gains_over_cold_start():
+@pytest.mark.parametrize("re", [300.0, 1000.0])
+def test_trained_warm_start_gains_over_cold_start(re):
     """The committed network (trained on solver steady states of
-    64 x 64 x 32 cavities) warm-starts a 192 x 192 x 96 cavity at Re 300:
-    the solver reaches residual 1e-6 in fewer steps than from rest, and both
-    runs end in the same steady state."""
+    64 x 64 x 32 cavities) warm-starts a 192 x 192 x 96 cavity at a low and
+    a high Re of its range: the solver reaches residual 1e-6 in fewer steps
+    than from rest, and both runs end in the same steady state."""
     import os
     from paper_2206_00366_gb300 import warmstart as WS
     if not os.path.exists(WS.WEIGHTS):
         pytest.skip("no trained weights committed")
     net = WS.Net.load(WS.WEIGHTS)
-    re = 300.0
     dom = WS.cavity((96, 192, 192), re)
     cold = WS.time_to_steady(dom, re)
     warm = WS.time_to_steady(dom, re, net=net, coarse=tuple(net.meta["shape"]))
