@@ -157,7 +157,9 @@ def test_long_run_matches_oracle(name, storage):
     scale = {"f32": 1.0, "f16": 2.0 ** 13, "e3m12": 2.0 ** 11, "bf16": 2.0 ** 16}[storage]
     if floor * scale > GATE[storage] and val > GATE[storage]:
         assert val <= 10 * floor * scale, err
-        pytest.xfail(f"{name} {storage}: error {val:.2e} (gate {GATE[storage]:g}); the oracle's own run: {why}")
+        pytest.xfail(f"{name} {storage}: error {val:.2e} (gate {GATE[storage]:g}); the oracle's own run: {why}"
+                     + (f"; times this storage's unit roundoff over FP32's ({scale:.0f}): {floor * scale:.2e}"
+                        if scale > 1 else ""))
     if storage == "bf16":
         assert val <= 5e-2, err
         if val > GATE[storage]:
