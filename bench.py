@@ -819,17 +819,19 @@ def run_only_batched(args):
 
 def run_only_batched_to_steady(args):
     """All 512 seeded rD2Q9 cavities from rest to residual 1e-6 (FP32, check
-    every 100 steps, CUDA graphs, tuned tiles, tile queue), at most `steps`
-    steps: wall time, how many converged or were retired as unstable, and
-    the distribution of steps to converge."""
+    every 100 steps, CUDA graphs, tuned tiles, tile queue; moment basis
+    --basis), at most `steps` steps: wall time, how many converged or were
+    retired as unstable, the distribution of steps to converge, and the
+    residuals of those still stepping."""
     import numpy as np
     import torch
 
     import workloads as W
     from paper_2206_00366_gb300.rmrtlb import Batch
     doms = W.cavity_domains(512, seed=4)
-    b = Batch(doms, storage="f32", check_every=100, tol=1e-6)
+    b = Batch(doms, storage="f32", check_every=100, tol=1e-6, basis=args.basis)
     w = b.tune(5)
+    b.reset()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     issued = b.run(args.steps)
@@ -838,12 +840,16 @@ def run_only_batched_to_steady(args):
     ok = conv[act == 0]
     nodes = np.array([d["nx"] * d["ny"] for d in doms])
     work = float((nodes * np.where(act == 0, conv, issued)).sum())
-    print(json.dumps({"only": args.only, "domains": len(doms), "max_steps": args.steps, "steps_issued": int(issued),
+    stepping = res[act == 1]
+    print(json.dumps({"only": args.only, "basis": args.basis, "domains": len(doms), "max_steps": args.steps,
+                      "steps_issued": int(issued),
                       "wall_s": round(wall, 1), "tile": [w, b.tile_rows], "converged": int((act == 0).sum()),
                       "unstable": int((act == -1).sum()), "still_stepping": int((act == 1).sum()),
                       "steps_to_tol_median": int(np.median(ok)) if len(ok) else None,
                       "steps_to_tol_p90": int(np.percentile(ok, 90)) if len(ok) else None,
                       "steps_to_tol_max": int(ok.max()) if len(ok) else None,
+                      "still_stepping_residual_q10_q50_q90": [float(np.quantile(stepping, x)) for x in (0.1, 0.5, 0.9)]
+                      if len(stepping) else None,
                       "node_updates": work, "mlups_effective": round(work / wall / 1e6, 1)}))
 
 
@@ -884,6 +890,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, help="time one named workload only (profiling)")
+    ap.add_argument("--basis", default="raw", choices=["raw", "central", "hermite", "central_hermite"],
+                    help="moment basis of --only batched-to-steady")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -143,17 +143,23 @@ def normwise_u(u, u_ref):
     return float(component_errors(u, u_ref).max())
 
 
-def fp64_component_bounds(steps, q, c_max, f_max, rho_min, u_ref, gate=1e-12):
-    """Per-component tolerance of an FP64 comparison: the gate, or the
-    oracle's own accumulated rounding where that is larger.  The oracle
-    holds full populations (up to f_max); each step its collision passes
-    every population through q multiply-adds and its momentum sums q
-    populations times |c_j| <= c_max, each rounding by at most 2^-53 of its
-    size, so after n steps its velocity carries at most
-    n q^2 2^-53 c_max f_max / rho_min absolute (linear accumulation, the
+def component_bounds(steps, q, c_max, f_max, rho_min, u_ref, gate, unit):
+    """Per-component tolerance of a velocity comparison: the gate, or the
+    accumulated rounding of a run in arithmetic of unit roundoff `unit`
+    where that is larger.  A run holding full populations (up to f_max)
+    passes every population through q multiply-adds per step and sums q
+    populations times |c_j| <= c_max into the momentum, each rounding by at
+    most `unit` of its size, so after n steps its velocity carries at most
+    n q^2 unit c_max f_max / rho_min absolute (linear accumulation, the
     worst case)."""
-    oracle = steps * q * q * 2.0 ** -53 * c_max * f_max / rho_min
-    return np.maximum(gate, oracle / component_scales(u_ref))
+    acc = steps * q * q * unit * c_max * f_max / rho_min
+    return np.maximum(gate, acc / component_scales(u_ref))
+
+
+def fp64_component_bounds(steps, q, c_max, f_max, rho_min, u_ref, gate=1e-12):
+    """component_bounds of an FP64 comparison (unit 2^-53): the oracle's own
+    accumulated rounding."""
+    return component_bounds(steps, q, c_max, f_max, rho_min, u_ref, gate, 2.0 ** -53)
 
 
 def of_max_u(u, u_ref):
