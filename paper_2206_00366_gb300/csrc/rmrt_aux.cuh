@@ -82,18 +82,36 @@ __global__ void plane_kernel(ST* __restrict__ f, double* __restrict__ plane, int
 // Macroscopic fields and FP64 check sums of the current populations.
 // Grid-stride over the nodes (1-D grid of CHECK_THREADS-thread blocks);
 // sums per block: [0] sum drho, [1..3] momentum, [4] kinetic energy,
-// [5] sum |u - u_prev|^2, [6] sum |u|^2, [7] unused.
+// [5] sum |u - u_prev|^2, [6] sum |u|^2, [7] unused.  A thread takes
+// several nodes of its stride at a time (four on rD2Q9, two on the 3-D
+// lattices; half that in FP64) and issues all their population and
+// snapshot loads before using any or storing the new snapshot (loads
+// behind the snapshot stores, which the compiler cannot move past them,
+// made the check four times slower).  Per-node arithmetic is in the compute type CT,
+// and so are a thread's running sums over at most CHECK_RUN nodes; each
+// run is then added into FP64 sums, and threads, warps and blocks are
+// reduced in FP64 in a fixed order.  (FP64 accumulation per node made the
+// check FP64-pipe bound on GB300: about 20 FP64 operations per node.)  The
+// residual snapshot holds u in CT (exact: u is computed in CT).
 constexpr int CHECK_THREADS = 256;
 constexpr int CHECK_MAX_BLOCKS = 4096;
+constexpr int CHECK_RUN = 16;
+template <int LAT, typename CT>
+__host__ __device__ constexpr int check_batch() {
+  return sizeof(CT) == 8 ? (Lat<LAT>::Q <= 9 ? 2 : 1) : (Lat<LAT>::Q <= 9 ? 4 : 2);
+}
 
 template <int LAT, typename ST, typename CT>
-__global__ void __launch_bounds__(CHECK_THREADS) check_kernel(
+__global__ void __launch_bounds__(CHECK_THREADS, 2) check_kernel(
     const ST* __restrict__ fin, double* __restrict__ rho_out, double* __restrict__ u_out,
     double* __restrict__ uprev, int use_prev, int write_prev, double* __restrict__ partials,
     int* __restrict__ flags, const KParams<CT> p) {
   using L = Lat<LAT>;
-  constexpr int D = L::D;
+  constexpr int D = L::D, B = check_batch<LAT, CT>();
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  CT run[7] = {CT(0), CT(0), CT(0), CT(0), CT(0), CT(0), CT(0)};
+  int in_run = 0;
+  CT* up = reinterpret_cast<CT*>(uprev);
   int flag = 0;
   const size_t N = p.N;
   const bool nse = p.kind == KIND_NSE || p.kind == KIND_NSE_HELUO;
@@ -103,64 +121,95 @@ __global__ void __launch_bounds__(CHECK_THREADS) check_kernel(
   const size_t n0 = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int gx = int(G % p.nx), gy = int((G / p.nx) % p.ny), gz = int(G / (size_t(p.nx) * p.ny));
   int x = int(n0 % p.nx), y = int((n0 / p.nx) % p.ny), z = int(n0 / (size_t(p.nx) * p.ny));
-  for (size_t n = n0; n < N; n += G) {
-    const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
-    // per-node arithmetic in the compute type; only the sums are FP64
-    CT s0 = CT(0), s1[3] = {CT(0), CT(0), CT(0)};
-    static_for<L::Q>([&](auto J) {
-      constexpr int j = decltype(J)::value;
-      constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
-      const int sx = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
-      const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
-      const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
-      const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
-      const CT raw = load_st<ST, CT>(fin + j * N + idx);
-      if constexpr (std::is_same<ST, E3M12>::value) {
-        if ((__float_as_uint(raw) & 0x7FFFFFFFu) >= E3M12_MAX_W) flag |= 8;   // saturated code
-      }
-      const CT dj = raw * p.sinv[j];
-      s0 += dj;
-      if (ex) s1[0] += CT(ex) * dj;
-      if (ey) s1[1] += CT(ey) * dj;
-      if (ez) s1[2] += CT(ez) * dj;
-    });
-    const CT hdtc = CT(0.5) * p.dt;
-    const CT drho = s0 + hdtc * p.source;
-    const CT rho = p.rho0 + drho;
-    CT u[3] = {CT(0), CT(0), CT(0)}, jm[3] = {CT(0), CT(0), CT(0)};
-    const CT inv = nse ? CT(1) / (p.kind == KIND_NSE ? rho : p.rho0) : CT(0);
-    for (int al = 0; al < D; ++al) {
-      jm[al] = s1[al] * p.c[al] + hdtc * p.force[al];
-      u[al] = nse ? jm[al] * inv : p.adv[al];
+  const CT hdtc = CT(0.5) * p.dt;
+  for (size_t nb0 = n0; nb0 < N; nb0 += B * G) {
+    // the populations (and the residual snapshot) of up to B nodes
+    // n = nb0 + b G, all loads before any use or store
+    CT f[B][L::Q], uo[B][D];
+    bool ok[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      ok[b] = nb0 + b * G < N;
+#pragma unroll
+      for (int al = 0; al < D; ++al) uo[b][al] = (ok[b] && up && use_prev) ? up[al * N + nb0 + b * G] : CT(0);
+      const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
+      static_for<L::Q>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+        const int sx = Nbr::up(ex, nb.xm, nb.x0, nb.xp);
+        const int sy = Nbr::up(ey, nb.ym, nb.y0, nb.yp);
+        const int sz = Nbr::up(ez, nb.zm, nb.z0, nb.zp);
+        const size_t idx = (size_t(sz) * p.ny + sy) * p.nx + sx;
+        f[b][j] = ok[b] ? load_st<ST, CT>(fin + j * N + idx) : CT(0);
+      });
+      x += gx;
+      if (x >= p.nx) { x -= p.nx; ++y; }
+      y += gy;
+      if (y >= p.ny) { y -= p.ny; ++z; }
+      z += gz;
     }
-    if (!nse)
-      for (int al = 0; al < D; ++al) jm[al] = rho * u[al];
-    if (rho_out) rho_out[n] = double(rho);
-    CT u2 = CT(0);
-    double du2 = 0;
-    for (int al = 0; al < D; ++al) {
-      if (u_out) u_out[al * N + n] = double(u[al]);
-      u2 += u[al] * u[al];
-      if (uprev) {
-        const double d = double(u[al]) - (use_prev ? uprev[al * N + n] : 0.0);
-        du2 += d * d;
-        if (write_prev) uprev[al * N + n] = double(u[al]);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      if (!ok[b]) continue;
+      const size_t n = nb0 + b * G;
+      CT s0 = CT(0), s1[3] = {CT(0), CT(0), CT(0)};
+      static_for<L::Q>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        constexpr int ex = L::EX[j], ey = L::EY[j], ez = L::EZ[j];
+        const CT raw = f[b][j];
+        if constexpr (std::is_same<ST, E3M12>::value) {
+          if ((__float_as_uint(raw) & 0x7FFFFFFFu) >= E3M12_MAX_W) flag |= 8;   // saturated code
+        }
+        const CT dj = raw * p.sinv[j];
+        s0 += dj;
+        if (ex) s1[0] += CT(ex) * dj;
+        if (ey) s1[1] += CT(ey) * dj;
+        if (ez) s1[2] += CT(ez) * dj;
+      });
+      const CT drho = s0 + hdtc * p.source;
+      const CT rho = p.rho0 + drho;
+      CT u[3] = {CT(0), CT(0), CT(0)}, jm[3] = {CT(0), CT(0), CT(0)};
+      const CT inv = nse ? CT(1) / (p.kind == KIND_NSE ? rho : p.rho0) : CT(0);
+      for (int al = 0; al < D; ++al) {
+        jm[al] = s1[al] * p.c[al] + hdtc * p.force[al];
+        u[al] = nse ? jm[al] * inv : p.adv[al];
       }
+      if (!nse)
+        for (int al = 0; al < D; ++al) jm[al] = rho * u[al];
+      if (rho_out) rho_out[n] = double(rho);
+      CT u2 = CT(0), du2 = CT(0);
+      for (int al = 0; al < D; ++al) {
+        if (u_out) u_out[al * N + n] = double(u[al]);
+        u2 += u[al] * u[al];
+        if (up) {
+          const CT d = u[al] - uo[b][al];
+          du2 += d * d;
+          if (write_prev) up[al * N + n] = u[al];
+        }
+      }
+      run[0] += drho;
+      run[1] += jm[0];
+      if constexpr (D > 1) run[2] += jm[1];
+      if constexpr (D > 2) run[3] += jm[2];
+      run[4] += CT(0.5) * rho * u2;
+      run[5] += du2;
+      run[6] += u2;
+      if (!(drho == drho) || !(u2 == u2) || isinf(drho) || isinf(u2)) flag |= 1;
+      if (nse && rho <= CT(0)) flag |= 2;
+      if (nse && u2 >= p.cs2) flag |= 4;
     }
-    acc[0] += double(drho);
-    acc[1] += double(jm[0]); acc[2] += double(jm[1]); acc[3] += double(jm[2]);
-    acc[4] += double(CT(0.5) * rho * u2);
-    acc[5] += du2;
-    acc[6] += double(u2);
-    if (!(drho == drho) || !(u2 == u2) || isinf(double(drho)) || isinf(double(u2))) flag |= 1;
-    if (nse && rho <= CT(0)) flag |= 2;
-    if (nse && u2 >= p.cs2) flag |= 4;
-    x += gx;
-    if (x >= p.nx) { x -= p.nx; ++y; }
-    y += gy;
-    if (y >= p.ny) { y -= p.ny; ++z; }
-    z += gz;
+    in_run += B;
+    if (in_run >= CHECK_RUN) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        acc[k] += double(run[k]);
+        run[k] = CT(0);
+      }
+      in_run = 0;
+    }
   }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) acc[k] += double(run[k]);
   if (partials) {
     // warp then block reduction in FP64, fixed order (deterministic)
 #pragma unroll

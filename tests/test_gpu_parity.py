@@ -437,6 +437,38 @@ def test_stats_large_grid_stride(lattice, shape):
     assert abs(st[4] - ke) <= 1e-10 * ke
 
 
+def test_stats_fp32_runs_of_partial_sums():
+    """FP32 storage: the check keeps each thread's running sums in FP32 over
+    runs of at most 16 nodes and adds the runs in FP64.  On a grid where
+    every thread walks many nodes its totals stay within the FP32 rounding
+    of those runs (each run's sum rounds by at most 15 units of 2^-24 of the
+    sum of its magnitudes) plus the FP32 rounding of every node's rho, of
+    the FP64 sums of the fields the same kernel returns; the residual
+    against two snapshots likewise."""
+    import torch
+    nx, ny = 4096, 1536                      # 6.3 M nodes: 6 nodes per thread of the 1 M-thread grid
+    case = Case("D2Q9", (nx, ny, 1), (1.0, 0.6, 1.0), nu=0.01, nu_bulk=0.02)
+    rho, u = W.random_fields(case.field_shape, 2, seed=12, umax=0.03)
+    s = gpu_solver(case, "f32", check_every=10)
+    s.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    s.step(10)
+    r1, u1 = s.moments()
+    s.step(10)
+    r2, u2 = s.moments()
+    chk = s.last_check()
+    assert chk[6] == 20 and chk[7] == 0
+    unit, n = 2.0 ** -24, r2.size
+    dr = np.abs(r2 - 1.0).sum()
+    # rho near 1 comes back rounded to FP32: at most 2^-24 per node
+    assert abs(chk[0] - r2.sum()) <= 15 * unit * dr + unit * n
+    mom = (r2[None] * u2).reshape(2, -1).sum(1)
+    mag = np.abs(r2[None] * u2).reshape(2, -1).sum(1)
+    # the kernel's momentum is its own FP32 jm = rho u before the division: one more rounding per node
+    assert (np.abs(chk[1:3] - mom) <= 15 * unit * mag + 2 * unit * mag).all()
+    want = np.sqrt(((u2 - u1) ** 2).sum() / (u2 ** 2).sum())
+    assert abs(chk[5] / want - 1) < 1e-5
+
+
 # ---------------------------------------------------------------- local stress, Eqs. (4-32), (4-33)
 @pytest.mark.parametrize("lattice", ["D2Q9", "D3Q19", "D3Q27"])
 @pytest.mark.parametrize("kind", ["nse", "nse_heluo"])
