@@ -430,6 +430,32 @@ int rmrtlb_check(rmrtlb_t solver);
  * slabs.  No check yet: zeros with out[6] = -1.  Synchronises the stream. */
 int rmrtlb_check_sums(rmrtlb_t solver, double out[8]);
 
+/* ------------------------------------------------ checkpoint / resume */
+/* The paper has no counterpart.  A solver's state as one self-describing
+ * blob: a header (format version, grid, storage, basis, equilibrium kind,
+ * the step counter, the periodic check's bookkeeping, and every constant
+ * the step derives from the parameters, as a fingerprint), then the
+ * population codes exactly as stored, the residual snapshot of the last
+ * check (if any), the simplified NCDE's B(t - dt) planes (that kind only)
+ * and the last check's sums and flag word.  Loading it into a solver
+ * created with the same lattice, grid, storage, basis, kind and parameters
+ * and stepping on gives bitwise the same populations and checks as the
+ * uninterrupted run (the 16-bit stochastic rounding draws its bits from
+ * the step counter and the node index, both restored).
+ *
+ * rmrtlb_state_bytes: the blob's size for the solver's current state (it
+ * grows by the snapshot once a check has run).  Host only.
+ * rmrtlb_save_state: writes the blob to dst (host or device memory of at
+ * least rmrtlb_state_bytes bytes, caller-owned); synchronises the stream.
+ * rmrtlb_load_state: restores the state from src (host or device memory);
+ * RMRTLB_EINVAL, with the solver unchanged, if the blob is not a state
+ * blob, is shorter than its sections, or was saved from a solver with
+ * another lattice, grid, storage, basis, kind or any other constant;
+ * synchronises the stream. */
+int rmrtlb_state_bytes(rmrtlb_t solver, size_t* bytes);
+int rmrtlb_save_state(rmrtlb_t solver, void* dst, size_t bytes);
+int rmrtlb_load_state(rmrtlb_t solver, const void* src, size_t bytes);
+
 /* ------------------------------------------------ allocation-free totals */
 /* The paper has no counterpart to this entry point.  It is for callers that
  * cannot allocate device memory: code whose device memory is owned by

@@ -572,3 +572,148 @@ int rmrtlb_halo_unpack(rmrtlb_t s, const void* from_below, const void* from_abov
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ checkpoint / resume
+// A state blob: a header (format, grid, storage, basis, kind, the step
+// counter and check bookkeeping, and every derived constant of the step as
+// a fingerprint of the parameters), then the raw population codes of the
+// current lattice, the residual snapshot (when a check has written one),
+// the simplified NCDE's B(t - dt) planes (that kind only), and the periodic
+// check's stats and flag words.  The codes are copied as stored, so a
+// resumed run draws the same stochastic-rounding bits and is bitwise
+// identical to an uninterrupted one.
+namespace {
+
+constexpr int kFingerprint = 80;
+
+struct StateHeader {
+  char magic[8];
+  unsigned version, header_bytes;
+  int lattice, nx, ny, nz, storage, basis, eq_kind, has_prev;
+  long long step;
+  int hist_fresh, slot_valid, slot_prev, pad_;
+  long long slot_step;
+  double fp[kFingerprint];
+  unsigned long long pop_bytes, prev_bytes, hist_bytes, stats_bytes, flags_bytes;
+};
+const char kStateMagic[8] = {'R', 'M', 'R', 'T', 'L', 'B', 'S', '1'};
+
+void fingerprint(const Consts& k, double fp[kFingerprint]) {
+  int i = 0;
+  for (int a = 0; a < 3; ++a) fp[i++] = k.c[a];
+  fp[i++] = k.cs2; fp[i++] = k.dt; fp[i++] = k.rho0; fp[i++] = k.source;
+  for (int j = 0; j < 27; ++j) fp[i++] = k.w[j];
+  fp[i++] = k.s0;
+  for (int a = 0; a < 3; ++a) fp[i++] = k.s1[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) fp[i++] = k.s2[a][b];
+  for (int a = 0; a < 3; ++a) fp[i++] = k.soff[a];
+  fp[i++] = k.sfree;
+  for (int a = 0; a < 3; ++a) { fp[i++] = k.ss[a]; fp[i++] = k.sb[a]; fp[i++] = k.force[a]; fp[i++] = k.adv[a]; }
+  fp[i++] = double(k.st_shift);
+  fp[i++] = double(k.forced);
+  while (i < kFingerprint) fp[i++] = 0.0;
+}
+
+size_t round16(size_t v) { return (v + 15) / 16 * 16; }
+
+// Section sizes of this solver's state.
+void state_sections(const rmrtlb_solver* s, size_t& pop, size_t& prev, size_t& hist, size_t& stats, size_t& flags) {
+  const size_t ct = s->k.storage == RMRTLB_ST_F64 ? sizeof(double) : sizeof(float);
+  pop = size_t(s->k.q) * s->k.N * storage_size(s->k.storage);
+  prev = s->has_prev ? size_t(s->k.d) * s->k.N * ct : 0;
+  hist = simple_ncde(s->k.kind) ? size_t(s->k.d) * s->k.N * ct : 0;
+  stats = 8 * sizeof(double);
+  flags = sizeof(int);
+}
+
+}  // namespace
+
+int rmrtlb_state_bytes(rmrtlb_t s, size_t* bytes) {
+  if (!s || !bytes) return RMRTLB_EINVAL;
+  size_t pop, prev, hist, stats, flags;
+  state_sections(s, pop, prev, hist, stats, flags);
+  *bytes = round16(sizeof(StateHeader)) + round16(pop) + round16(prev) + round16(hist) + round16(stats) +
+           round16(flags);
+  return RMRTLB_OK;
+}
+
+int rmrtlb_save_state(rmrtlb_t s, void* dst, size_t bytes) {
+  size_t need = 0;
+  if (!s || !dst || rmrtlb_state_bytes(s, &need) != RMRTLB_OK || bytes < need) return RMRTLB_EINVAL;
+  size_t pop, prev, hist, stats, flags;
+  state_sections(s, pop, prev, hist, stats, flags);
+  StateHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kStateMagic, 8);
+  h.version = 1;
+  h.header_bytes = unsigned(sizeof(StateHeader));
+  h.lattice = s->k.lat; h.nx = s->k.nx; h.ny = s->k.ny; h.nz = s->k.nz;
+  h.storage = s->k.storage; h.basis = s->k.central; h.eq_kind = s->k.kind;
+  h.has_prev = s->has_prev ? 1 : 0;
+  h.step = s->step;
+  h.hist_fresh = s->kp32.hist_fresh;
+  h.slot_valid = s->slot_valid[0] ? 1 : 0;
+  h.slot_prev = s->slot_prev[0] ? 1 : 0;
+  h.slot_step = s->slot_step[0];
+  fingerprint(s->k, h.fp);
+  h.pop_bytes = pop; h.prev_bytes = prev; h.hist_bytes = hist; h.stats_bytes = stats; h.flags_bytes = flags;
+  char* d = static_cast<char*>(dst);
+  size_t off = 0;
+  static const char zeros[16] = {0};
+  // each section, then zeros up to its 16-byte boundary (a blob is fully defined)
+  auto put = [&](const void* src, size_t n) {
+    bool ok = n == 0 || cudaMemcpyAsync(d + off, src, n, cudaMemcpyDefault, s->stream) == cudaSuccess;
+    if (round16(n) > n)
+      ok = ok && cudaMemcpyAsync(d + off + n, zeros, round16(n) - n, cudaMemcpyDefault, s->stream) == cudaSuccess;
+    off += round16(n);
+    return ok;
+  };
+  const bool ok = put(&h, sizeof(h)) && put(pop_ptr(s, s->cur), pop) && put(s->ws + s->L.uprev, prev) &&
+                  put(s->ws + s->L.hist, hist) && put(s->ws + s->L.stats, stats) && put(s->ws + s->L.flags, flags);
+  // the header lives on this stack frame: the copies end before returning
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess || !ok) return RMRTLB_ECUDA;
+  return RMRTLB_OK;
+}
+
+int rmrtlb_load_state(rmrtlb_t s, const void* src, size_t bytes) {
+  if (!s || !src || bytes < sizeof(StateHeader)) return RMRTLB_EINVAL;
+  StateHeader h;
+  if (cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDefault, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return RMRTLB_ECUDA;
+  double fp[kFingerprint];
+  fingerprint(s->k, fp);
+  if (memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1 || h.header_bytes != sizeof(StateHeader) ||
+      h.lattice != s->k.lat || h.nx != s->k.nx || h.ny != s->k.ny || h.nz != s->k.nz ||
+      h.storage != s->k.storage || h.basis != s->k.central || h.eq_kind != s->k.kind ||
+      memcmp(h.fp, fp, sizeof(fp)) != 0 || h.step < 0)
+    return RMRTLB_EINVAL;
+  // the section sizes this solver expects with the blob's snapshot flag
+  const bool had_prev = s->has_prev;
+  s->has_prev = h.has_prev != 0;
+  size_t pop, prev, hist, stats, flags, need = 0;
+  state_sections(s, pop, prev, hist, stats, flags);
+  rmrtlb_state_bytes(s, &need);
+  s->has_prev = had_prev;
+  if (bytes < need || h.pop_bytes != pop || h.prev_bytes != prev || h.hist_bytes != hist || h.stats_bytes != stats ||
+      h.flags_bytes != flags)
+    return RMRTLB_EINVAL;
+  const char* p = static_cast<const char*>(src) + round16(sizeof(StateHeader));
+  auto get = [&](void* dst, size_t n) {
+    const bool ok = n == 0 || cudaMemcpyAsync(dst, p, n, cudaMemcpyDefault, s->stream) == cudaSuccess;
+    p += round16(n);
+    return ok;
+  };
+  const bool ok = get(pop_ptr(s, 0), pop) && get(s->ws + s->L.uprev, prev) && get(s->ws + s->L.hist, hist) &&
+                  get(s->ws + s->L.stats, stats) && get(s->ws + s->L.flags, flags);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess || !ok) return RMRTLB_ECUDA;
+  s->cur = 0;
+  s->step = h.step;
+  s->has_prev = h.has_prev != 0;
+  s->kp64.hist_fresh = s->kp32.hist_fresh = h.hist_fresh;
+  s->slot_valid[0] = h.slot_valid != 0;
+  s->slot_prev[0] = h.slot_prev != 0;
+  s->slot_step[0] = h.slot_step;
+  return RMRTLB_OK;
+}

@@ -121,6 +121,9 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_halo_bytes": (i, [_vp, ctypes.POINTER(sz)]),
         "rmrtlb_halo_pack": (i, [_vp, _vp, _vp]),
         "rmrtlb_halo_unpack": (i, [_vp, _vp, _vp]),
+        "rmrtlb_state_bytes": (i, [_vp, ctypes.POINTER(sz)]),
+        "rmrtlb_save_state": (i, [_vp, _vp, sz]),
+        "rmrtlb_load_state": (i, [_vp, _vp, sz]),
         "rmrtlb_stress": (i, [_vp, _vp, _vp]),
         "rmrtlb_population_totals_noalloc": (i, [i, i, i, i, d, d, d, d, _vp, _vp, _vp]),
         "rmrtlb_batch_workspace_bytes": (i, [i, i, ctypes.POINTER(rmrtlb_domain), i, ctypes.POINTER(sz)]),
@@ -165,6 +168,7 @@ def exported_symbols() -> list:
             "rmrtlb_destroy", "rmrtlb_get_constants", "rmrtlb_init_equilibrium",
             "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
             "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_check", "rmrtlb_check_sums", "rmrtlb_halo_bytes", "rmrtlb_halo_pack",
+            "rmrtlb_state_bytes", "rmrtlb_save_state", "rmrtlb_load_state",
             "rmrtlb_halo_unpack", "rmrtlb_stress", "rmrtlb_population_totals_noalloc",
             "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
             "rmrtlb_batch_tune", "rmrtlb_batch_set_launch", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
@@ -250,6 +254,20 @@ def rmrtlb_last_check(h, allow_unstable: bool = False) -> np.ndarray:
     if not (allow_unstable and st == EUNSTABLE):
         _check(st, "rmrtlb_last_check")
     return np.array(out[:])
+
+
+def rmrtlb_state_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().rmrtlb_state_bytes(h, ctypes.byref(n)), "rmrtlb_state_bytes")
+    return int(n.value)
+
+
+def rmrtlb_save_state(h, dst: int, nbytes: int):
+    _check(lib().rmrtlb_save_state(h, dst, nbytes), "rmrtlb_save_state")
+
+
+def rmrtlb_load_state(h, src: int, nbytes: int):
+    _check(lib().rmrtlb_load_state(h, src, nbytes), "rmrtlb_load_state")
 
 
 def rmrtlb_check(h):
@@ -425,6 +443,17 @@ def rmrtlb_pack_fields(n, d, rho, u, rho0, rho_scale, u_scale, out, stream=0):
 
 
 # ------------------------------------------------------------------ convenience
+def _raw_ptr(x) -> int:
+    """Address of a contiguous numpy array or torch tensor of any type."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("numpy arrays must be contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return x.data_ptr()
+
+
 def _ptr(x) -> int:
     """Address of a torch tensor or numpy array (must be contiguous float64)."""
     if x is None:
@@ -502,6 +531,24 @@ class Solver:
 
     def last_check(self, allow_unstable=False):
         return rmrtlb_last_check(self.h, allow_unstable)
+
+    def save_state(self, out=None):
+        """The solver's state blob (rmrtlb_save_state) in a new uint8 numpy
+        array, or written into `out` (numpy array or CUDA tensor of at least
+        rmrtlb_state_bytes bytes), which is returned."""
+        n = rmrtlb_state_bytes(self.h)
+        if out is None:
+            out = np.empty(n, dtype=np.uint8)
+        size = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        if size < n:
+            raise ValueError(f"state needs {n} bytes, the buffer holds {size}")
+        rmrtlb_save_state(self.h, _raw_ptr(out), n)
+        return out
+
+    def load_state(self, blob):
+        """Restore a state saved by save_state (numpy array or CUDA tensor)."""
+        nbytes = blob.nbytes if isinstance(blob, np.ndarray) else blob.numel() * blob.element_size()
+        rmrtlb_load_state(self.h, _raw_ptr(blob), nbytes)
 
     def stress(self):
         """(stress, strain rate) as numpy arrays (d(d+1)/2, nz, ny, nx),

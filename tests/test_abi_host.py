@@ -167,3 +167,40 @@ def test_convolution_scratch_bytes(B):
         4 * (ceil(v, 4096) * 27 * 32 * 4 + ceil(v, 1024) * 4)
     assert B.rmrtlb_conv3d_backward_data_scratch(n, d, h, w, 32, 32) == v * 64
     assert B.rmrtlb_conv3d_backward_weight_scratch(0, d, h, w, 32, 32) == 0
+
+
+def test_state_bytes(B):
+    """The checkpoint blob of a new solver: a header, the population codes as
+    stored (q N elements of the storage), the simplified NCDE's B(t - dt)
+    planes (d N of the compute type, that kind only), the check's sums and
+    flag word, each section rounded up to 16 bytes; no residual snapshot
+    before a check.  NULL buffers are rejected before any copy (host only)."""
+    import ctypes
+    ok = dict(nu=0.01, nu_bulk=0.05, s_free=1.1, rho0=1.0, diffusivity=0.02)
+    r16 = lambda n: -(-n // 16) * 16
+    sizes = []
+    for lat, st, kind, esize, ct in [(B.D2Q9, B.ST_F32, 0, 4, 4), (B.D3Q27, B.ST_F16, 0, 2, 4),
+                                     (B.D2Q9, B.ST_F64, 0, 8, 8), (B.D2Q5, B.ST_F32, B.EQ_NAMES["ncde_simple_linear"],
+                                                                   4, 4)]:
+        nx, ny, nz = (12, 10, 1) if lat in (B.D2Q9, B.D2Q5) else (8, 6, 4)
+        spacing = (1.0, 0.7, 1.0) if nz == 1 else (1.0, 0.7, 0.5)
+        q, d, _ = B.rmrtlb_lattice_info(lat)
+        p = B.make_params(**ok)
+        nbytes = B.rmrtlb_workspace_bytes(lat, nx, ny, nz, st)
+        h = B.rmrtlb_create(lat, nx, ny, nz, *spacing, 1.0, p, kind, 0, st, 256, nbytes, 0)
+        try:
+            n = nx * ny * nz
+            hist = d * n * ct if kind == B.EQ_NAMES["ncde_simple_linear"] else 0
+            body = r16(q * n * esize) + r16(hist) + 64 + 16
+            total = B.rmrtlb_state_bytes(h)
+            sizes.append(total - body)                      # the header, the same for every solver
+            assert total > body
+            for fn in (lib_call(B, "rmrtlb_save_state"), lib_call(B, "rmrtlb_load_state")):
+                assert fn(h, None, total) == B.EINVAL
+        finally:
+            B.rmrtlb_destroy(h)
+    assert len(set(sizes)) == 1 and sizes[0] % 16 == 0
+
+
+def lib_call(B, name):
+    return getattr(B.lib(), name)
