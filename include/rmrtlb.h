@@ -414,6 +414,23 @@ int rmrtlb_halo_bytes(rmrtlb_t solver, size_t* bytes);
 int rmrtlb_halo_pack(rmrtlb_t solver, void* up, void* down);
 int rmrtlb_halo_unpack(rmrtlb_t solver, const void* from_below, const void* from_above);
 
+/* One step in two parts, for overlapping a slab's halo exchange with its
+ * interior (the populations that cross a face only enter the two planes
+ * next to it).  Along the slab axis (y on rD2Q9 / rD2Q5, z on the 3-D
+ * lattices) of n planes, rmrtlb_step_interior steps planes 2 .. n - 3: it
+ * reads only planes 1 .. n - 2 of the current populations and writes only
+ * the other lattice, so it may run while rmrtlb_halo_pack's buffers are in
+ * flight and before rmrtlb_halo_unpack.  rmrtlb_step_boundary then steps
+ * every plane the step has not stepped yet (planes 0, 1, n - 2, n - 1, or
+ * all of them without an interior part) and completes the step exactly as
+ * rmrtlb_step does (counter, periodic check); rmrtlb_step after an interior
+ * part does the same.  The two parts give bitwise the step of rmrtlb_step.
+ * With n < 5 the interior part steps nothing.  rmrtlb_step_interior twice
+ * without completing the step, RMRTLB_EINVAL.  Asynchronous on the
+ * solver's stream. */
+int rmrtlb_step_interior(rmrtlb_t solver);
+int rmrtlb_step_boundary(rmrtlb_t solver);
+
 /* Run the periodic FP64 check now, on the current state, into the record
  * that rmrtlb_last_check and rmrtlb_check_sums read (the residual is taken
  * against the previous check's snapshot, which this call replaces), as

@@ -49,6 +49,7 @@ using namespace rmrt::host;
 namespace {
 
 constexpr int kSlots = 2;          // 0: periodic check in rmrtlb_step, 1: rmrtlb_stats
+constexpr int kInteriorMinPlanes = 5;   // rmrtlb_step_interior steps planes 2 .. n - 3 when n >= 5
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -109,6 +110,7 @@ struct rmrtlb_solver {
   int check_every;
   int pairs;          // step kernel handles two nodes per thread (nx even)
   int quads;          // four nodes per thread (16-bit storage, nx % 4 == 0)
+  bool interior_done; // rmrtlb_step_interior has stepped planes 2 .. n - 3 of the current step
   bool has_prev;      // a periodic check wrote the residual snapshot
   long long slot_step[kSlots];
   bool slot_prev[kSlots];
@@ -338,6 +340,7 @@ int rmrtlb_create(rmrtlb_t* solver, int lattice, int nx, int ny, int nz, double 
   s->pairs = (nx % 2 == 0) && !axis_lattice(lattice) && !simple_ncde(eq_kind);
   s->quads = s->pairs && nx % 4 == 0 &&
              (storage == RMRTLB_ST_F16 || storage == RMRTLB_ST_BF16 || storage == RMRTLB_ST_E3M12);
+  s->interior_done = false;
   *solver = s;
   return RMRTLB_OK;
 }
@@ -391,6 +394,7 @@ int rmrtlb_init_equilibrium(rmrtlb_t s, const double* rho, const double* u) {
   if (launch(s, a) != cudaSuccess) return RMRTLB_ECUDA;
   s->step = 0;
   s->has_prev = false;
+  s->interior_done = false;
   s->kp64.hist_fresh = s->kp32.hist_fresh = 1;
   if (synced && cudaStreamSynchronize(s->stream) != cudaSuccess) return RMRTLB_ECUDA;
   return RMRTLB_OK;
@@ -417,6 +421,7 @@ int rmrtlb_set_populations(rmrtlb_t s, const double* f) {
   }
   s->step = 0;
   s->has_prev = false;
+  s->interior_done = false;
   s->kp64.hist_fresh = s->kp32.hist_fresh = 1;
   if (!dev && cudaStreamSynchronize(s->stream) != cudaSuccess) return RMRTLB_ECUDA;
   return RMRTLB_OK;
@@ -442,10 +447,18 @@ int rmrtlb_get_populations(rmrtlb_t s, double* f) {
   return RMRTLB_OK;
 }
 
-int rmrtlb_step(rmrtlb_t s, int n) {
-  if (!s || n < 0) return RMRTLB_EINVAL;
-  for (int i = 0; i < n; ++i) {
-    LaunchArgs a = base_args(s, OP_STEP);
+}  // extern "C"
+
+namespace {
+
+// Extent of the slab axis (y on the 2-D lattices, z on the 3-D ones).
+int axis_planes(const rmrtlb_solver* s) { return s->k.d == 2 ? s->k.ny : s->k.nz; }
+
+// The step kernel over planes [first, first + count) of the slab axis:
+// reads the current lattice, writes the other one.
+cudaError_t launch_step_planes(rmrtlb_solver* s, int first, int count) {
+  if (count <= 0) return cudaSuccess;
+  LaunchArgs a = base_args(s, OP_STEP);
     if (s->quads) {
       const int quarter = s->k.nx / 4;
       const int bx = block_x(quarter);
@@ -461,18 +474,60 @@ int rmrtlb_step(rmrtlb_t s, int n) {
     }
     a.fin = pop_ptr(s, s->cur);
     a.fout = pop_ptr(s, 1 - s->cur);
+    if (s->k.d == 2) a.grid.y = unsigned(count);
+    else a.grid.z = unsigned(count);
     // seed of the stochastic rounding of 16-bit stores: a function of the
     // step index only, so a run is reproducible
     s->kp32.seed = unsigned((unsigned long long)s->step * 0x9E3779B97F4A7C15ull >> 32);
-    if (launch(s, a) != cudaSuccess) return RMRTLB_ECUDA;   // the parameters are copied at launch
-    s->kp64.hist_fresh = s->kp32.hist_fresh = 0;
-    s->cur = 1 - s->cur;
-    ++s->step;
-    if (s->check_every > 0 && s->step % s->check_every == 0)
-      if (run_check(s, 0, nullptr, nullptr, true, true) != cudaSuccess) return RMRTLB_ECUDA;
+    s->kp64.plane0 = s->kp32.plane0 = first;
+    const cudaError_t e = launch(s, a);   // the parameters are copied at launch
+    s->kp64.plane0 = s->kp32.plane0 = 0;
+    return e;
+}
+
+// Completes a step whose planes have all been stepped: swaps the lattices,
+// advances the counter, runs the periodic check when one is due.
+int finish_step(rmrtlb_solver* s) {
+  s->kp64.hist_fresh = s->kp32.hist_fresh = 0;
+  s->cur = 1 - s->cur;
+  ++s->step;
+  s->interior_done = false;
+  if (s->check_every > 0 && s->step % s->check_every == 0)
+    if (run_check(s, 0, nullptr, nullptr, true, true) != cudaSuccess) return RMRTLB_ECUDA;
+  return RMRTLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rmrtlb_step(rmrtlb_t s, int n) {
+  if (!s || n < 0) return RMRTLB_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const int planes = axis_planes(s);
+    // a step begun by rmrtlb_step_interior is completed first
+    if (s->interior_done) {
+      if (launch_step_planes(s, 0, 2) != cudaSuccess || launch_step_planes(s, planes - 2, 2) != cudaSuccess)
+        return RMRTLB_ECUDA;
+    } else if (launch_step_planes(s, 0, planes) != cudaSuccess) {
+      return RMRTLB_ECUDA;
+    }
+    const int rc = finish_step(s);
+    if (rc != RMRTLB_OK) return rc;
   }
   return RMRTLB_OK;
 }
+
+int rmrtlb_step_interior(rmrtlb_t s) {
+  if (!s || s->interior_done) return RMRTLB_EINVAL;
+  const int planes = axis_planes(s);
+  if (planes < kInteriorMinPlanes) return RMRTLB_OK;   // every plane is a boundary plane
+  if (launch_step_planes(s, 2, planes - 4) != cudaSuccess) return RMRTLB_ECUDA;
+  s->interior_done = true;
+  return RMRTLB_OK;
+}
+
+int rmrtlb_step_boundary(rmrtlb_t s) { return rmrtlb_step(s, 1); }
 
 int rmrtlb_moments(rmrtlb_t s, double* rho, double* u) {
   if (!s) return RMRTLB_EINVAL;
@@ -709,6 +764,7 @@ int rmrtlb_load_state(rmrtlb_t s, const void* src, size_t bytes) {
                   get(s->ws + s->L.stats, stats) && get(s->ws + s->L.flags, flags);
   if (cudaStreamSynchronize(s->stream) != cudaSuccess || !ok) return RMRTLB_ECUDA;
   s->cur = 0;
+  s->interior_done = false;
   s->step = h.step;
   s->has_prev = h.has_prev != 0;
   s->kp64.hist_fresh = s->kp32.hist_fresh = h.hist_fresh;

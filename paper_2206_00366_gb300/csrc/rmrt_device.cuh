@@ -765,6 +765,19 @@ __device__ __forceinline__ void store_step(ST* p, CT v, unsigned r) {
 }
 
 // ------------------------------------------------------------------ kernels
+// Coordinates of a step block's row: grid.y = y and grid.z = z, offset by
+// p.plane0 along the slab axis (y on the 2-D lattices, z on the 3-D ones)
+// when a launch covers only some of the planes (rmrtlb_step_interior /
+// rmrtlb_step_boundary).
+template <int LAT, typename P>
+__device__ __forceinline__ int plane_y(const P& p) {
+  return int(blockIdx.y) + (Lat<LAT>::D == 2 ? p.plane0 : 0);
+}
+template <int LAT, typename P>
+__device__ __forceinline__ int plane_z(const P& p) {
+  return int(blockIdx.z) + (Lat<LAT>::D == 3 ? p.plane0 : 0);
+}
+
 // One time step: pull gather from fin (post-collision of the previous step,
 // x - e_j), collide, store the post-collision state of node x in fout.
 template <int LAT, typename ST, typename CT, int BASIS, bool FORCED, bool NSE>
@@ -772,7 +785,7 @@ __global__ void __launch_bounds__(128) step_kernel(const ST* __restrict__ fin, S
                                                    const KParams<CT> p) {
   using L = Lat<LAT>;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = plane_y<LAT>(p), z = plane_z<LAT>(p);
   if (x >= p.nx) return;
   const Nbr nb(x, y, z, p.nx, p.ny, p.nz);
   const size_t N = p.N;
@@ -883,7 +896,7 @@ __global__ void __launch_bounds__(128, Tuning<LAT, int(sizeof(ST)), BASIS != 0>:
   const bool active = x0 < p.nx;
   const int xc = active ? x0 : p.nx - 2;
   const int lane = threadIdx.x & 31;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = plane_y<LAT>(p), z = plane_z<LAT>(p);
   const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
   const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
   const bool fix_lo = lane == 0;                       // needs x0 - 1 from memory
@@ -1031,7 +1044,7 @@ __global__ void __launch_bounds__(128, Tuning<LAT, 2, BASIS != 0>::X4_MIN_BLOCKS
   const bool active = x0 < p.nx;
   const int xc = active ? x0 : p.nx - 4;
   const int lane = threadIdx.x & 31;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = plane_y<LAT>(p), z = plane_z<LAT>(p);
   const int ym = y == 0 ? p.ny - 1 : y - 1, yp = y == p.ny - 1 ? 0 : y + 1;
   const int zm = z == 0 ? p.nz - 1 : z - 1, zp = z == p.nz - 1 ? 0 : z + 1;
   const bool fix_lo = lane == 0;                       // needs x0 - 1 from memory

@@ -39,6 +39,7 @@ struct KParams {
   int hist_fresh;                      // 1: no previous B yet (dB/dt taken as 0 on this step)
   unsigned seed;                       // per-step seed of the stochastic rounding of 16-bit stores
   unsigned node_base;                  // index of node 0 in the grid the random bits are drawn over
+  int plane0;                          // first plane (y in 2-D, z in 3-D) of a step launch over some planes
 };
 
 enum Op { OP_STEP = 0, OP_INIT_EQ = 1, OP_PLANE = 2, OP_CHECK = 3, OP_STRESS = 4 };

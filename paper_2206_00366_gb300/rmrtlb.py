@@ -121,6 +121,8 @@ def lib() -> ctypes.CDLL:
         "rmrtlb_halo_bytes": (i, [_vp, ctypes.POINTER(sz)]),
         "rmrtlb_halo_pack": (i, [_vp, _vp, _vp]),
         "rmrtlb_halo_unpack": (i, [_vp, _vp, _vp]),
+        "rmrtlb_step_interior": (i, [_vp]),
+        "rmrtlb_step_boundary": (i, [_vp]),
         "rmrtlb_state_bytes": (i, [_vp, ctypes.POINTER(sz)]),
         "rmrtlb_save_state": (i, [_vp, _vp, sz]),
         "rmrtlb_load_state": (i, [_vp, _vp, sz]),
@@ -168,7 +170,8 @@ def exported_symbols() -> list:
             "rmrtlb_destroy", "rmrtlb_get_constants", "rmrtlb_init_equilibrium",
             "rmrtlb_set_populations", "rmrtlb_get_populations", "rmrtlb_step", "rmrtlb_moments",
             "rmrtlb_stats", "rmrtlb_last_check", "rmrtlb_check", "rmrtlb_check_sums", "rmrtlb_halo_bytes", "rmrtlb_halo_pack",
-            "rmrtlb_state_bytes", "rmrtlb_save_state", "rmrtlb_load_state",
+            "rmrtlb_state_bytes", "rmrtlb_save_state", "rmrtlb_load_state", "rmrtlb_step_interior",
+            "rmrtlb_step_boundary",
             "rmrtlb_halo_unpack", "rmrtlb_stress", "rmrtlb_population_totals_noalloc",
             "rmrtlb_batch_workspace_bytes", "rmrtlb_batch_create", "rmrtlb_batch_destroy", "rmrtlb_batch_reset",
             "rmrtlb_batch_tune", "rmrtlb_batch_set_launch", "rmrtlb_batch_step", "rmrtlb_batch_status", "rmrtlb_batch_set_populations",
@@ -254,6 +257,14 @@ def rmrtlb_last_check(h, allow_unstable: bool = False) -> np.ndarray:
     if not (allow_unstable and st == EUNSTABLE):
         _check(st, "rmrtlb_last_check")
     return np.array(out[:])
+
+
+def rmrtlb_step_interior(h):
+    _check(lib().rmrtlb_step_interior(h), "rmrtlb_step_interior")
+
+
+def rmrtlb_step_boundary(h):
+    _check(lib().rmrtlb_step_boundary(h), "rmrtlb_step_boundary")
 
 
 def rmrtlb_state_bytes(h) -> int:

@@ -8,6 +8,13 @@ rmrtlb_halo_pack / rmrtlb_halo_unpack (the C ABI documents why the periodic
 wrap of a slab is exactly where its neighbours' values belong).  The check
 sums are reduced over the ranks in FP64 every check.
 
+The exchange overlaps the next step's interior: populations that cross a
+face only enter the two planes next to it, so each step runs as
+rmrtlb_step_interior (planes 2 .. n - 3, needing no halo) while the previous
+step's crossing planes are in flight, then the halo is unpacked and
+rmrtlb_step_boundary steps the four planes next to the faces and completes
+the step (bitwise the same step as rmrtlb_step).
+
 This module holds the host-side bookkeeping only: the partition, the ring
 exchange of device buffers over torch.distributed (NCCL between GPUs; any
 backend that moves tensors works), and the global reductions; every step of
@@ -45,23 +52,34 @@ def crossing(e: np.ndarray, d: int, sign: int):
     return [j for j in range(e.shape[0]) if int(e[j, a]) == sign]
 
 
-def ring_exchange(send_up, send_down, recv_from_below, recv_from_above, rank: int, world: int, group=None):
-    """One exchange on the periodic ring of slabs: send_up goes to rank + 1
-    and send_down to rank - 1; recv_from_below receives rank - 1's up
-    buffer and recv_from_above rank + 1's down buffer.  The four operations
-    are posted in the same order on every rank, so the two messages between
-    a pair of neighbours (or, with two ranks, the two each way) match."""
+def start_exchange(send_up, send_down, recv_from_below, recv_from_above, rank: int, world: int, group=None):
+    """Posts one exchange on the periodic ring of slabs and returns its
+    requests: send_up goes to rank + 1 and send_down to rank - 1;
+    recv_from_below receives rank - 1's up buffer and recv_from_above rank +
+    1's down buffer.  The four operations are posted in the same order on
+    every rank, so the two messages between a pair of neighbours (or, with
+    two ranks, the two each way) match.  With NCCL the transfers wait for
+    the work already on the current CUDA stream and run beside what is
+    enqueued after them."""
     import torch.distributed as dist
     up, down = (rank + 1) % world, (rank - 1) % world
     if dist.get_backend(group) == "nccl":
         ops = [dist.P2POp(dist.isend, send_up, up, group), dist.P2POp(dist.irecv, recv_from_below, down, group),
                dist.P2POp(dist.isend, send_down, down, group), dist.P2POp(dist.irecv, recv_from_above, up, group)]
-        reqs = dist.batch_isend_irecv(ops)
-    else:
-        reqs = [dist.isend(send_up, up, group), dist.irecv(recv_from_below, down, group),
-                dist.isend(send_down, down, group), dist.irecv(recv_from_above, up, group)]
+        return dist.batch_isend_irecv(ops)
+    return [dist.isend(send_up, up, group), dist.irecv(recv_from_below, down, group),
+            dist.isend(send_down, down, group), dist.irecv(recv_from_above, up, group)]
+
+
+def finish_exchange(reqs):
+    """Waits for an exchange (with NCCL: makes the current CUDA stream wait)."""
     for r in reqs:
         r.wait()
+
+
+def ring_exchange(send_up, send_down, recv_from_below, recv_from_above, rank: int, world: int, group=None):
+    """start_exchange and finish_exchange in one call."""
+    finish_exchange(start_exchange(send_up, send_down, recv_from_below, recv_from_above, rank, world, group))
 
 
 def global_check(sums) -> np.ndarray:
@@ -137,17 +155,32 @@ class Slab:
         B.rmrtlb_halo_unpack(self.solver.h, from_below.data_ptr(), from_above.data_ptr())
 
     def step(self, n=1):
-        """n steps, each followed by the exchange of the crossing planes."""
+        """n steps, each followed by the exchange of the crossing planes; the
+        exchange of one step runs beside the interior of the next, and the
+        last one is complete when this returns."""
         import torch
-        for _ in range(n):
-            self.solver.step(1)
-            if self.world > 1:
+        if self.world == 1:
+            for _ in range(n):
+                self.solver.step(1)
+                self.after_exchange()
+            return
+        h = self.solver.h
+        pending = None
+        # the library's kernels run on the solver's stream, and the exchange is ordered against it
+        with torch.cuda.stream(self.solver.stream):
+            for _ in range(n):
+                B.rmrtlb_step_interior(h)
+                if pending is not None:
+                    finish_exchange(pending)
+                    self.unpack(self.bufs[2], self.bufs[3])
+                    self.after_exchange()
+                B.rmrtlb_step_boundary(h)
                 up, down = self.pack()
-                with torch.cuda.stream(self.solver.stream):
-                    # the library's pack and unpack run on the solver's stream, and so does the exchange
-                    ring_exchange(up, down, self.bufs[2], self.bufs[3], self.rank, self.world, self.group)
+                pending = start_exchange(up, down, self.bufs[2], self.bufs[3], self.rank, self.world, self.group)
+            if pending is not None:
+                finish_exchange(pending)
                 self.unpack(self.bufs[2], self.bufs[3])
-            self.after_exchange()
+                self.after_exchange()
 
     def moments(self, rho=None, u=None):
         return self.solver.moments(rho, u)
@@ -191,19 +224,34 @@ class LocalSlabs:
             s.init_equilibrium(rho, u)
 
     def step(self, n=1):
+        """The schedule of Slab.step with the exchange as device copies: each
+        step's interior runs before the previous step's halo is unpacked."""
         import torch
         w = len(self.slabs)
-        for _ in range(n):
-            for s in self.slabs:
-                s.solver.step(1)
-            if w > 1:
-                packed = [s.pack() for s in self.slabs]
-                torch.cuda.synchronize()
-                for r, s in enumerate(self.slabs):
-                    s.unpack(packed[(r - 1) % w][0], packed[(r + 1) % w][1])
-                torch.cuda.synchronize()
+        if w == 1:
+            for _ in range(n):
+                self.slabs[0].solver.step(1)
+                self.slabs[0].after_exchange()
+            return
+        packed = None
+
+        def land():
+            torch.cuda.synchronize()
+            for r, s in enumerate(self.slabs):
+                s.unpack(packed[(r - 1) % w][0], packed[(r + 1) % w][1])
+            torch.cuda.synchronize()
             for s in self.slabs:
                 s.after_exchange()
+        for _ in range(n):
+            for s in self.slabs:
+                B.rmrtlb_step_interior(s.solver.h)
+            if packed is not None:
+                land()
+            for s in self.slabs:
+                B.rmrtlb_step_boundary(s.solver.h)
+            packed = [s.pack() for s in self.slabs]
+        if packed is not None:
+            land()
 
     def moments(self):
         """Global (rho, u) assembled from the slabs."""

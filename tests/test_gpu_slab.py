@@ -90,3 +90,52 @@ def test_halo_rejects_host_buffers():
         B.rmrtlb_halo_pack(s.h, host.ctypes.data, dev.data_ptr())
     with pytest.raises(B.RmrtlbError):
         B.rmrtlb_halo_unpack(s.h, dev.data_ptr(), host.ctypes.data)
+
+
+SPLIT_CASES = [("D2Q9", (40, 12, 1), "nse", "raw"), ("D2Q9", (36, 4, 1), "nse", "raw"),
+               ("D3Q19", (16, 8, 9), "nse", "central"), ("D3Q27", (12, 6, 7), "nse", "raw"),
+               ("D2Q5", (18, 12, 1), "ncde_simple_linear", "raw"), ("D3Q7", (10, 6, 8), "ncde_simple_linear", "raw")]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "e3m12"])
+@pytest.mark.parametrize("lattice,shape,kind,basis", SPLIT_CASES)
+def test_interior_and_boundary_parts_equal_the_step(lattice, shape, kind, basis, storage):
+    """rmrtlb_step_interior (planes 2 .. n - 3 of the slab axis) followed by
+    rmrtlb_step_boundary, or by rmrtlb_step, is bitwise rmrtlb_step, periodic
+    check included; with fewer than five planes the interior part steps
+    nothing; a second interior part before the step is completed is
+    refused."""
+    from paper_2206_00366_gb300 import rmrtlb as B
+    from paper_2206_00366_gb300.rmrtlb import Solver
+    params = dict(nu=0.02, nu_bulk=0.03, s_free=1.1, rho0=1.0 if kind == "nse" else 0.0, diffusivity=0.02,
+                  adv=(0.05, -0.03, 0.02), check_every=3)
+    nx, ny, nz = shape
+    d = 2 if lattice.startswith("D2") else 3
+    rho, u = W.random_fields((nz, ny, nx), d, seed=23, umax=0.03)
+    if kind != "nse":
+        rho = rho - 0.9
+    sp = (1.0, 0.6, 1.0) if d == 2 else (1.0, 0.8, 0.5)
+    whole = Solver(lattice, shape, sp, 1.0, params, kind, basis, storage)
+    whole.init_equilibrium(rho, u)
+    whole.step(7)
+    split = Solver(lattice, shape, sp, 1.0, params, kind, basis, storage)
+    split.init_equilibrium(rho, u)
+    for k in range(7):
+        B.rmrtlb_step_interior(split.h)
+        if k % 2:
+            B.rmrtlb_step_boundary(split.h)
+        else:
+            split.step(1)
+    np.testing.assert_array_equal(split.get_populations(), whole.get_populations())
+    np.testing.assert_array_equal(split.last_check(), whole.last_check())
+    planes = ny if d == 2 else nz
+    B.rmrtlb_step_interior(split.h)
+    if planes >= 5:
+        with pytest.raises(B.RmrtlbError) as ei:
+            B.rmrtlb_step_interior(split.h)
+        assert ei.value.status == B.EINVAL
+    else:
+        B.rmrtlb_step_interior(split.h)                  # nothing stepped, nothing pending
+    B.rmrtlb_step_boundary(split.h)
+    whole.step(1)
+    np.testing.assert_array_equal(split.get_populations(), whole.get_populations())
