@@ -42,8 +42,8 @@ int rmrtlb_conv3d_forward(int n, int d, int h, int w, int cin, int cout,
                           int apply_silu, float* z, uint16_t* a, void* stream);
 
 /* Bytes of device scratch rmrtlb_conv3d_backward_data can use (host only):
- * a BF16 copy of dy when cout = 32 and the plane holds a 128-voxel box (the
- * copy-fed kernel then runs), else 0. */
+ * a BF16 copy of dy (cout = 32, or cout = 4 padded to 8 channels) when the
+ * plane holds a 128-voxel box (the copy-fed kernel then runs), else 0. */
 size_t rmrtlb_conv3d_backward_data_scratch(int n, int d, int h, int w, int cin, int cout);
 
 /* Gradient with respect to the input, channel pairs (32, 32), (32, 4):
@@ -60,16 +60,16 @@ int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout,
                                 float* dx, void* scratch, size_t scratch_bytes, void* stream);
 
 /* Bytes of device scratch rmrtlb_conv3d_backward_weight needs (host only):
- * per-chunk partial sums of dweight and dbias, and for cout = 32 on planes
- * that hold a 128-voxel box a BF16 copy of dy. */
+ * per-chunk partial sums of dweight and dbias, and on planes that hold a
+ * 128-voxel box a BF16 copy of dy (cout = 4 padded to 8 channels). */
 size_t rmrtlb_conv3d_backward_weight_scratch(int n, int d, int h, int w, int cin, int cout);
 
 /* Gradient with respect to the weights and the bias, all three channel
  * pairs: dweight[t, ci, co] = sum_v x[v + tap_t, ci] dy[v, co] on the tensor
  * cores (a GEMM with K = voxels, M = taps x cin, both operands MN-major in
  * shared memory; dy rounded to BF16, nearest even), dbias[co] = sum_v dy[v,
- * co] on the FP32 pipes.  For cout = 32 on planes that hold a 128-voxel
- * box the operands are brought by the tensor-memory accelerator box by box
+ * co] on the FP32 pipes.  On planes that hold a 128-voxel box the
+ * operands are brought by the tensor-memory accelerator box by box
  * (dy first rounded into the scratch) and dweight is summed per chunk of
  * 32 boxes; otherwise threads gather them and dweight is summed per chunk
  * of 4096 voxels; dbias is summed per chunk of 1024 voxels.  The partial

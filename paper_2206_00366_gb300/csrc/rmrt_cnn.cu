@@ -244,11 +244,17 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_kernel(Vol g, const void* 
         }
       } else {
         if (zin) {
-          const float* zr = zin + v * NOUT;
+          // the pre-activation row in 16-byte loads (z_in is 16-byte aligned, NOUT a multiple of 4)
+          const float4* zr = reinterpret_cast<const float4*>(zin + v * NOUT);
 #pragma unroll
-          for (int n = 0; n < NOUT; ++n) {
-            const float zz = zr[n], sg = sigm(zz);
-            acc[n] *= sg * (1.0f + zz * (1.0f - sg));
+          for (int q4 = 0; q4 < NOUT / 4; ++q4) {
+            const float4 z4 = zr[q4];
+            const float zs[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float zz = zs[e], sg = sigm(zz);
+              acc[4 * q4 + e] *= sg * (1.0f + zz * (1.0f - sg));
+            }
           }
         }
         float4* dx = reinterpret_cast<float4*>(zout + v * NOUT);
@@ -309,14 +315,15 @@ struct TmaShape {
   static constexpr int NP = NOUT < 16 ? 16 : NOUT;
   static constexpr int KC = KP / 8;                   // 16-byte chunks of K
   // 32 channels: one copy per tap of 128 rows x 64 bytes, 64-byte swizzle;
-  // 8 channels: one copy of 128 rows x 16 bytes (no swizzle) plus a zero block for K 8..15
+  // 8 channels (or 4 padded to 8 in the tensor): one copy of 128 rows x 16
+  // bytes (no swizzle) plus a zero block for K 8..15
   static constexpr bool SW64 = KIN == 32;
-  static constexpr int LOADED = SW64 ? 1 : KIN / 8;   // copies per tap
+  static constexpr int LOADED = SW64 ? 1 : (KIN + 7) / 8;   // copies per tap
   static constexpr int CHUNK = SW64 ? 128 * 64 : 128 * 16;
   static constexpr int TAP = LOADED * CHUNK;          // bytes of one tap's A tile
-  static constexpr int GROUP = KIN == 8 ? RMRT_TMA_GROUP_K8 : RMRT_TMA_GROUP_K32;   // taps per buffer
+  static constexpr int GROUP = KIN <= 8 ? RMRT_TMA_GROUP_K8 : RMRT_TMA_GROUP_K32;   // taps per buffer
   static constexpr int STAGE = GROUP * TAP;
-  static constexpr int STAGES = KIN == 8 ? RMRT_TMA_STAGES_K8 : RMRT_TMA_STAGES_K32;
+  static constexpr int STAGES = KIN <= 8 ? RMRT_TMA_STAGES_K8 : RMRT_TMA_STAGES_K32;
   static_assert(27 % GROUP == 0, "taps per buffer must divide 27");
   static constexpr int B_TAP = NP * KP * 2;
   static constexpr int OFF_B = STAGES * STAGE;
@@ -517,11 +524,17 @@ __global__ void __launch_bounds__(kTmaThreads) conv_tma_kernel(const __grid_cons
       if (MODE == 1 && y < g.h && x < g.w) {
         const long long v = (((long long)p.n * g.d + p.z) * g.h + y) * g.w + x;
         if (zin) {
-          const float* zr = zin + v * NOUT;
+          // the pre-activation row in 16-byte loads (z_in is 16-byte aligned, NOUT a multiple of 4)
+          const float4* zr = reinterpret_cast<const float4*>(zin + v * NOUT);
 #pragma unroll
-          for (int n = 0; n < NOUT; ++n) {
-            const float zz = zr[n], sgm = sigm(zz);
-            acc[n] *= sgm * (1.0f + zz * (1.0f - sgm));
+          for (int q4 = 0; q4 < NOUT / 4; ++q4) {
+            const float4 z4 = zr[q4];
+            const float zs[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float zz = zs[e], sgm = sigm(zz);
+              acc[4 * q4 + e] *= sgm * (1.0f + zz * (1.0f - sgm));
+            }
           }
         }
         float4* dxo = reinterpret_cast<float4*>(zout + v * NOUT);
@@ -712,32 +725,39 @@ __global__ void __launch_bounds__(kTcThreads) conv_wgrad_tc_kernel(Vol g, const 
 // warp 4 lane 0 issues the copies into a ring of WG_STAGES buffers, warp 5
 // lane 0 the MMAs (M = TPG taps x CIN channels = 128, N = 32 output
 // channels, K = 16 voxels each, one commit per buffer), warps 0-3 read the
-// accumulator at the end of the chunk.  Every wait is bounded.
+// accumulator at the end of the chunk.  Every wait is bounded.  With 4
+// output channels dy's copy is padded to 8 channels (16-byte rows, no
+// swizzle) and the MMA takes N = 16, its second 8-channel core matrix read
+// from a zero block (the stride byte offset points there).
 #ifndef RMRT_WG_STAGES
 #define RMRT_WG_STAGES 2
 #endif
 constexpr int kWgTiles = 32;                            // boxes (K tiles of 128 voxels) per chunk
 
-template <int CIN>
+template <int CIN, int COUT>
 struct WgTmaShape {
   static constexpr bool SW64 = CIN == 32;
+  static constexpr bool NARROW = COUT == 4;             // dy padded to 8 channels, N = 16
+  static constexpr int NP = NARROW ? 16 : 32;           // MMA N
   static constexpr int TPG = 128 / CIN;                 // taps per group (M = 128)
   static constexpr int GROUPS = (27 + TPG - 1) / TPG;
   static constexpr int A_TAP = 128 * CIN * 2;           // one tap's box of x
   static constexpr int A_BYTES = TPG * A_TAP;           // 32 KB
-  static constexpr int B_BYTES = 128 * 32 * 2;          // the box of dy
+  static constexpr int B_BYTES = 128 * (NARROW ? 8 : 32) * 2;   // the box of dy
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr int STAGES = RMRT_WG_STAGES;
-  static constexpr int OFF_BAR = STAGES * STAGE;
+  static constexpr int OFF_ZERO = STAGES * STAGE;
+  static constexpr int ZERO = NARROW ? 256 : 0;         // two zero core matrices (channels 8..15)
+  static constexpr int OFF_BAR = OFF_ZERO + ZERO;
   static constexpr int NBAR = 2 * STAGES + 1;
   static constexpr int SMEM = OFF_BAR + NBAR * 8 + 16 + 1024;
 };
 
-template <int CIN>
+template <int CIN, int COUT>
 __global__ void __launch_bounds__(kTmaThreads) conv_wgrad_tma_kernel(const __grid_constant__ CUtensorMap tx,
                                                                      const __grid_constant__ CUtensorMap tdy, Vol g,
                                                                      int bw, int bh, float* __restrict__ part) {
-  using S = WgTmaShape<CIN>;
+  using S = WgTmaShape<CIN, COUT>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::OFF_BAR);
@@ -753,6 +773,8 @@ __global__ void __launch_bounds__(kTmaThreads) conv_wgrad_tma_kernel(const __gri
   for (int st = 0; st < S::STAGES; ++st)
     for (int i = tid; i < (S::TPG - ntap) * S::A_TAP / 16; i += kTmaThreads)
       reinterpret_cast<uint4*>(smem + st * S::STAGE + ntap * S::A_TAP)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < S::ZERO / 16; i += kTmaThreads)
+    reinterpret_cast<uint4*>(smem + S::OFF_ZERO)[i] = make_uint4(0, 0, 0, 0);
   if (warp == 5) tc::tmem_alloc(tslot, 32);
   if (tid == 0) {
     for (int k = 0; k < S::STAGES; ++k) {
@@ -806,7 +828,8 @@ __global__ void __launch_bounds__(kTmaThreads) conv_wgrad_tma_kernel(const __gri
     }
   } else if (warp == 5) {
     if (lane == 0) {                       // MMAs
-      const uint32_t idesc = tc::idesc_bf16(32, true);
+      const uint32_t idesc = tc::idesc_bf16(S::NP, true);
+      const uint32_t zbase = tc::smem_u32(smem + S::OFF_ZERO);
       bool ok = true;
       int done = 0;
       for (int kt = 0; kt < nk; ++kt) {
@@ -825,8 +848,11 @@ __global__ void __launch_bounds__(kTmaThreads) conv_wgrad_tma_kernel(const __gri
             ad = tc::smem_desc_sw64_mn(abase + kk * 1024, S::A_TAP, 512);
           else
             ad = tc::smem_desc(abase + kk * 256, 128, S::A_TAP);
-          // N = 32 is one swizzle atom wide: the M-direction stride is never used
-          const uint64_t bd = tc::smem_desc_sw64_mn(bbase + kk * 1024, 512, 512);
+          uint64_t bd;
+          if constexpr (S::NARROW)   // channels 0..7 from the copy, 8..15 from the zero block
+            bd = tc::smem_desc(bbase + kk * 256, 128, zbase - (bbase + kk * 256));
+          else   // N = 32 is one swizzle atom wide: the N-direction stride is never used
+            bd = tc::smem_desc_sw64_mn(bbase + kk * 1024, 512, 512);
           tc::mma_bf16(taddr, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
         }
         tc::mma_commit(&empty[st]);
@@ -848,13 +874,13 @@ __global__ void __launch_bounds__(kTmaThreads) conv_wgrad_tma_kernel(const __gri
     if (have) {
       const uint32_t lane_base = uint32_t(warp * 32) << 16;
       tc::tmem_ld16(taddr + lane_base, *reinterpret_cast<float(*)[16]>(acc));
-      tc::tmem_ld16(taddr + lane_base + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+      if constexpr (S::NP == 32) tc::tmem_ld16(taddr + lane_base + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
     }
     const int m = tid, tl = m / CIN, ci = m % CIN, t = group * S::TPG + tl;
     if (tl < ntap) {
-      float* out = part + (size_t(chunk) * 27 + t) * CIN * 32 + size_t(ci) * 32;
+      float* out = part + (size_t(chunk) * 27 + t) * CIN * COUT + size_t(ci) * COUT;
 #pragma unroll
-      for (int co = 0; co < 32; ++co) out[co] = have ? acc[co] : 0.0f;
+      for (int co = 0; co < COUT; ++co) out[co] = have ? acc[co] : 0.0f;
     }
   }
   tc::fence_before();
@@ -864,13 +890,14 @@ __global__ void __launch_bounds__(kTmaThreads) conv_wgrad_tma_kernel(const __gri
 
 // Bias gradient partials, bpart[c * COUT + co] = sum of dy[v, co] over the
 // kBiasChunk voxels of chunk c, and with BF16 the copy of dy rounded to
-// BF16 (nearest even) that the copy-fed kernels read.  256 threads read the
+// BF16 (nearest even) that the copy-fed kernels read (4 channels padded to
+// rows of 8).  256 threads read the
 // chunk's dy as consecutive float4 (COUT a multiple of 4 dividing 1024, so a
 // thread always meets the same four channels); the 256 / (COUT / 4) partial
 // sums of a channel are then added in a fixed order.
 template <int COUT, bool BF16>
 __global__ void __launch_bounds__(256) bias_grad_kernel(Vol g, const float* __restrict__ dy,
-                                                        float* __restrict__ bpart, uint2* __restrict__ dy16) {
+                                                        float* __restrict__ bpart, void* __restrict__ dy16) {
   static_assert(COUT % 4 == 0 && 1024 % COUT == 0, "four channels per float4, fixed per thread");
   __shared__ float4 red[256];
   const int tid = threadIdx.x;
@@ -887,9 +914,14 @@ __global__ void __launch_bounds__(256) bias_grad_kernel(Vol g, const float* __re
     acc.y += v.y;
     acc.z += v.z;
     acc.w += v.w;
-    if constexpr (BF16)
-      dy16[i] = make_uint2(uint32_t(f2bf(v.x)) | (uint32_t(f2bf(v.y)) << 16),
-                           uint32_t(f2bf(v.z)) | (uint32_t(f2bf(v.w)) << 16));
+    if constexpr (BF16) {
+      const uint32_t lo = uint32_t(f2bf(v.x)) | (uint32_t(f2bf(v.y)) << 16);
+      const uint32_t hi = uint32_t(f2bf(v.z)) | (uint32_t(f2bf(v.w)) << 16);
+      if constexpr (COUT == 4)   // one voxel: a row of 8 channels, 4..7 zero (16-byte rows for the copy engine)
+        static_cast<uint4*>(dy16)[i] = make_uint4(lo, hi, 0u, 0u);
+      else
+        static_cast<uint2*>(dy16)[i] = make_uint2(lo, hi);
+    }
   }
   red[tid] = acc;
   __syncthreads();
@@ -1103,14 +1135,16 @@ bool pick_box(const Vol& g, int& bw, int& bh) {
 }
 
 // Tensor map of a channels-last BF16 tensor (c, x, y, z, image) for boxes
-// of all 32 channels (64-byte swizzle) or of 8 channels, BW x BH voxels.
+// of all 32 channels (64-byte swizzle) or of 8 channels, BW x BH voxels; a
+// 4-channel operand is read from a copy padded to 8 channels.
 template <int KIN>
 bool make_tmap(CUtensorMap* tm, const Vol& g, const uint16_t* x, int bw, int bh) {
   const EncodeTiledFn enc = encode_tiled();
   if (!enc) return false;
   constexpr bool sw64 = TmaShape<KIN, 32>::SW64;
-  const cuuint64_t dims[5] = {cuuint64_t(KIN), cuuint64_t(g.w), cuuint64_t(g.h), cuuint64_t(g.d), cuuint64_t(g.n)};
-  const cuuint64_t row = cuuint64_t(KIN) * 2;
+  constexpr int C = KIN < 8 ? 8 : KIN;
+  const cuuint64_t dims[5] = {cuuint64_t(C), cuuint64_t(g.w), cuuint64_t(g.h), cuuint64_t(g.d), cuuint64_t(g.n)};
+  const cuuint64_t row = cuuint64_t(C) * 2;
   const cuuint64_t strides[4] = {row, row * cuuint64_t(g.w), row * cuuint64_t(g.w) * g.h,
                                  row * cuuint64_t(g.w) * g.h * g.d};
   const cuuint32_t box[5] = {sw64 ? 32u : 8u, cuuint32_t(bw), cuuint32_t(bh), 1, 1};
@@ -1162,12 +1196,23 @@ __global__ void to_bf16_kernel(long long count4, const float4* __restrict__ in, 
   }
 }
 
-// Scratch of the copy-fed input gradient: a BF16 copy of dy (32 channels,
-// planes that hold a 128-voxel box), else none.
+// FP32 -> BF16 (nearest even) of a 4-channel tensor into rows of 8
+// channels, channels 4..7 zero (16-byte rows for the copy engine).
+__global__ void to_bf16_pad8_kernel(long long voxels, const float4* __restrict__ in, uint4* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < voxels;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = in[i];
+    out[i] = make_uint4(uint32_t(f2bf(v.x)) | (uint32_t(f2bf(v.y)) << 16),
+                        uint32_t(f2bf(v.z)) | (uint32_t(f2bf(v.w)) << 16), 0u, 0u);
+  }
+}
+
+// Scratch of the copy-fed input gradient, on planes that hold a 128-voxel
+// box: a BF16 copy of dy (32 channels, or 4 padded to 8), else none.
 size_t bwd_data_scratch(const Vol& g, int cout) {
   int bw = 0, bh = 0;
-  if (cout != 32 || !pick_box(g, bw, bh)) return 0;
-  return size_t(g.voxels()) * 32 * 2;
+  if ((cout != 32 && cout != 4) || !pick_box(g, bw, bh)) return 0;
+  return size_t(g.voxels()) * (cout == 32 ? 32 : 8) * 2;
 }
 
 int chunks_of(Vol g) { return int((g.voxels() + kWeightChunk - 1) / kWeightChunk); }
@@ -1186,7 +1231,8 @@ WgScratch wgrad_scratch(const Vol& g, int cin, int cout) {
   WgScratch w{};
   const long long flat = chunks_of(g);
   int bw = 0, bh = 0;
-  if (cout == 32 && (cin == 8 || cin == 32) && pick_box(g, bw, bh)) {
+  const bool copy_fed = (cout == 32 && (cin == 8 || cin == 32)) || (cin == 32 && cout == 4);
+  if (copy_fed && pick_box(g, bw, bh)) {
     const long long tiles = (long long)g.n * g.d * ((g.h + bh - 1) / bh) * ((g.w + bw - 1) / bw);
     w.box_chunks = (tiles + kWgTiles - 1) / kWgTiles;
   }
@@ -1194,7 +1240,7 @@ WgScratch wgrad_scratch(const Vol& g, int cin, int cout) {
   w.part = size_t(parts) * 27 * size_t(cin) * cout * sizeof(float);
   w.bpart = size_t(bias_chunks_of(g)) * cout * sizeof(float);
   w.dy16_off = (w.part + w.bpart + 15) / 16 * 16;
-  w.total = w.box_chunks > 0 ? w.dy16_off + size_t(g.voxels()) * 32 * 2 : w.part + w.bpart;
+  w.total = w.box_chunks > 0 ? w.dy16_off + size_t(g.voxels()) * (cout == 4 ? 8 : 32) * 2 : w.part + w.bpart;
   return w;
 }
 
@@ -1218,23 +1264,23 @@ int wgrad_tc(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, fl
   return status_of(cudaGetLastError());
 }
 
-// The copy-fed weight gradient (32 output channels).  Returns false, having
-// launched nothing, where it does not apply (no box fits the plane, the
-// scratch is short, or a tensor map cannot be made); else true with the
-// status in *status.
-template <int CIN>
+// The copy-fed weight gradient (32 output channels, or 4 after 32 inputs).
+// Returns false, having launched nothing, where it does not apply (no box
+// fits the plane, the scratch is short, or a tensor map cannot be made);
+// else true with the status in *status.
+template <int CIN, int COUT>
 bool wgrad_tma(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, char* scratch, size_t scratch_bytes,
                cudaStream_t s, int* status) {
-  using S = WgTmaShape<CIN>;
-  const WgScratch w = wgrad_scratch(g, CIN, 32);
+  using S = WgTmaShape<CIN, COUT>;
+  const WgScratch w = wgrad_scratch(g, CIN, COUT);
   int bw = 0, bh = 0;
   if (w.box_chunks == 0 || scratch_bytes < w.total || !pick_box(g, bw, bh)) return false;
   uint16_t* dy16 = reinterpret_cast<uint16_t*>(scratch + w.dy16_off);
   CUtensorMap tx, tdy;
-  if (!make_tmap<CIN>(&tx, g, x, bw, bh) || !make_tmap<32>(&tdy, g, dy16, bw, bh)) return false;
+  if (!make_tmap<CIN>(&tx, g, x, bw, bh) || !make_tmap<COUT>(&tdy, g, dy16, bw, bh)) return false;
   // the opt-in to more than 48 KB of shared memory holds per device: set it on every call
-  if (cudaFuncSetAttribute(conv_wgrad_tma_kernel<CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM) !=
-      cudaSuccess) {
+  if (cudaFuncSetAttribute(conv_wgrad_tma_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           S::SMEM) != cudaSuccess) {
     *status = RMRTLB_ECUDA;
     return true;
   }
@@ -1242,16 +1288,16 @@ bool wgrad_tma(Vol g, const uint16_t* x, const float* dy, float* dw, float* db, 
   float* bpart = reinterpret_cast<float*>(scratch + w.part);
   const int bchunks = bias_chunks_of(g);
   // one pass over dy: the bias partials and the BF16 copy the copies read
-  bias_grad_kernel<32, true><<<bchunks, 256, 0, s>>>(g, dy, bpart, reinterpret_cast<uint2*>(dy16));
-  conv_wgrad_tma_kernel<CIN><<<dim3(unsigned(w.box_chunks), S::GROUPS), kTmaThreads, S::SMEM, s>>>(tx, tdy, g, bw,
-                                                                                                  bh, part);
+  bias_grad_kernel<COUT, true><<<bchunks, 256, 0, s>>>(g, dy, bpart, dy16);
+  conv_wgrad_tma_kernel<CIN, COUT><<<dim3(unsigned(w.box_chunks), S::GROUPS), kTmaThreads, S::SMEM, s>>>(
+      tx, tdy, g, bw, bh, part);
   if (cudaGetLastError() != cudaSuccess) {
     *status = RMRTLB_ECUDA;
     return true;
   }
-  const int nw = 27 * CIN * 32;
+  const int nw = 27 * CIN * COUT;
   sum_chunks_kernel<<<blocks_for(nw, 256), 256, 0, s>>>(part, int(w.box_chunks), size_t(nw), nw, dw);
-  sum_chunks_kernel<<<1, 256, 0, s>>>(bpart, bchunks, size_t(32), 32, db);
+  sum_chunks_kernel<<<1, 256, 0, s>>>(bpart, bchunks, size_t(COUT), COUT, db);
   *status = status_of(cudaGetLastError());
   return true;
 }
@@ -1292,7 +1338,8 @@ size_t rmrtlb_conv3d_backward_data_scratch(int n, int d, int h, int w, int cin, 
 int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout, const float* dy,
                                 const uint16_t* weight, const float* z_in, float* dx, void* scratch,
                                 size_t scratch_bytes, void* stream) {
-  if (!vol_ok(n, d, h, w) || !aligned16(dy) || !weight || !aligned16(dx)) return RMRTLB_EINVAL;
+  if (!vol_ok(n, d, h, w) || !aligned16(dy) || !weight || !aligned16(dx) || (z_in && !aligned16(z_in)))
+    return RMRTLB_EINVAL;
   const Vol g{n, d, h, w};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cin == 32 && cout == 32) {
@@ -1310,7 +1357,21 @@ int rmrtlb_conv3d_backward_data(int n, int d, int h, int w, int cin, int cout, c
     }
     return launch_tc<32, 32, 1>(g, dy, weight, nullptr, z_in, 0, dx, nullptr, s);
   }
-  if (cin == 32 && cout == 4) return launch_tc<4, 32, 1>(g, dy, weight, nullptr, z_in, 0, dx, nullptr, s);
+  if (cin == 32 && cout == 4) {
+    const size_t need = bwd_data_scratch(g, cout);
+    int bw = 0, bh = 0;
+    CUtensorMap tm;
+    uint16_t* dy16 = static_cast<uint16_t*>(scratch);
+    if (need && scratch && aligned16(scratch) && scratch_bytes >= need && pick_box(g, bw, bh) &&
+        make_tmap<4>(&tm, g, dy16, bw, bh)) {
+      const long long v = g.voxels();
+      const unsigned grid = blocks_for(v, 256) < 8192u ? blocks_for(v, 256) : 8192u;
+      to_bf16_pad8_kernel<<<grid, 256, 0, s>>>(v, reinterpret_cast<const float4*>(dy), reinterpret_cast<uint4*>(dy16));
+      if (cudaGetLastError() != cudaSuccess) return RMRTLB_ECUDA;
+      return run_tma<4, 32, 1>(tm, g, bw, bh, weight, nullptr, 0, z_in, dx, nullptr, s);
+    }
+    return launch_tc<4, 32, 1>(g, dy, weight, nullptr, z_in, 0, dx, nullptr, s);
+  }
   return RMRTLB_EINVAL;
 }
 
@@ -1330,14 +1391,17 @@ int rmrtlb_conv3d_backward_weight(int n, int d, int h, int w, int cin, int cout,
   char* raw = static_cast<char*>(scratch);
   int status = RMRTLB_OK;
   if (cin == 8 && cout == 32) {
-    if (wgrad_tma<8>(g, x, dy, dweight, dbias, raw, scratch_bytes, s, &status)) return status;
+    if (wgrad_tma<8, 32>(g, x, dy, dweight, dbias, raw, scratch_bytes, s, &status)) return status;
     return wgrad_tc<8, 32>(g, x, dy, dweight, dbias, sc, s);
   }
   if (cin == 32 && cout == 32) {
-    if (wgrad_tma<32>(g, x, dy, dweight, dbias, raw, scratch_bytes, s, &status)) return status;
+    if (wgrad_tma<32, 32>(g, x, dy, dweight, dbias, raw, scratch_bytes, s, &status)) return status;
     return wgrad_tc<32, 32>(g, x, dy, dweight, dbias, sc, s);
   }
-  if (cin == 32 && cout == 4) return wgrad_tc<32, 4>(g, x, dy, dweight, dbias, sc, s);
+  if (cin == 32 && cout == 4) {
+    if (wgrad_tma<32, 4>(g, x, dy, dweight, dbias, raw, scratch_bytes, s, &status)) return status;
+    return wgrad_tc<32, 4>(g, x, dy, dweight, dbias, sc, s);
+  }
   return RMRTLB_EINVAL;
 }
 

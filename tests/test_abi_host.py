@@ -146,9 +146,9 @@ def test_bgk_limit_constants(B):
 def test_convolution_scratch_bytes(B):
     """Scratch of the weight gradient: FP32 partial sums of dweight per
     4096-voxel chunk or per 32 boxes of 128 voxels (whichever are more),
-    of dbias per 1024 voxels, and for 32 output channels on a plane that
-    holds a box a 16-byte aligned BF16 copy of dy; the input gradient's
-    scratch is that copy alone."""
+    of dbias per 1024 voxels, and on a plane that holds a box a 16-byte
+    aligned BF16 copy of dy (4 output channels padded to 8); the input gradient's
+    scratch is that copy alone (4 output channels: padded to 8)."""
     ceil = lambda a, b: -(-a // b)
     # 5 x 6 planes hold no 128-voxel box: the threads gather, no dy copy
     n, d, h, w = 2, 5, 6, 13
@@ -163,9 +163,10 @@ def test_convolution_scratch_bytes(B):
     for cin in (8, 32):
         parts = 4 * (max(ceil(v, 4096), 128) * 27 * cin * 32 + ceil(v, 1024) * 32)
         assert B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, 32) == ceil(parts, 16) * 16 + v * 64
-    assert B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, 32, 4) == \
-        4 * (ceil(v, 4096) * 27 * 32 * 4 + ceil(v, 1024) * 4)
+    parts = 4 * (max(ceil(v, 4096), 128) * 27 * 32 * 4 + ceil(v, 1024) * 4)
+    assert B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, 32, 4) == ceil(parts, 16) * 16 + v * 16
     assert B.rmrtlb_conv3d_backward_data_scratch(n, d, h, w, 32, 32) == v * 64
+    assert B.rmrtlb_conv3d_backward_data_scratch(n, d, h, w, 32, 4) == v * 16
     assert B.rmrtlb_conv3d_backward_weight_scratch(0, d, h, w, 32, 32) == 0
 
 

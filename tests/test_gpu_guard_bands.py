@@ -167,18 +167,17 @@ def test_convolution_writes_stay_in_their_outputs(cin, cout):
         B.rmrtlb_cnn_check()
         assert_bands(sd_t, max(sd, 16))
         assert_bands(dx2_t, v2 * cin * 4)
-    if cout == 32:
-        # the copy-fed weight gradient: partials, bias partials and dy's BF16 copy inside the scratch
-        dy2 = torch.tensor(rng.normal(size=(v2, cout)), dtype=torch.float32, device="cuda")
-        sw = B.rmrtlb_conv3d_backward_weight_scratch(n2, d2, h2, w2, cin, cout)
-        sw_t, sw_p = guarded(sw)
-        dw2_t, dw2_p = guarded(27 * cin * cout * 4)
-        db2_t, db2_p = guarded(cout * 4)
-        B.rmrtlb_conv3d_backward_weight(n2, d2, h2, w2, cin, cout, x2.data_ptr(), dy2.data_ptr(), dw2_p, db2_p,
-                                        sw_p, sw)
-        B.rmrtlb_cnn_check()
-        for t, nb in [(sw_t, sw), (dw2_t, 27 * cin * cout * 4), (db2_t, cout * 4)]:
-            assert_bands(t, nb)
+    # the copy-fed weight gradient: partials, bias partials and dy's BF16 copy inside the scratch
+    dy2 = torch.tensor(rng.normal(size=(v2, cout)), dtype=torch.float32, device="cuda")
+    sw = B.rmrtlb_conv3d_backward_weight_scratch(n2, d2, h2, w2, cin, cout)
+    sw_t, sw_p = guarded(sw)
+    dw2_t, dw2_p = guarded(27 * cin * cout * 4)
+    db2_t, db2_p = guarded(cout * 4)
+    B.rmrtlb_conv3d_backward_weight(n2, d2, h2, w2, cin, cout, x2.data_ptr(), dy2.data_ptr(), dw2_p, db2_p,
+                                    sw_p, sw)
+    B.rmrtlb_cnn_check()
+    for t, nb in [(sw_t, sw), (dw2_t, 27 * cin * cout * 4), (db2_t, cout * 4)]:
+        assert_bands(t, nb)
     dy = torch.tensor(rng.normal(size=(v, cout)), dtype=torch.float32, device="cuda")
     sb = B.rmrtlb_conv3d_backward_weight_scratch(n, d, h, w, cin, cout)
     sc_t, sc_p = guarded(sb)
