@@ -83,12 +83,12 @@ __global__ void plane_kernel(ST* __restrict__ f, double* __restrict__ plane, int
 // Grid-stride over the nodes (1-D grid of CHECK_THREADS-thread blocks);
 // sums per block: [0] sum drho, [1..3] momentum, [4] kinetic energy,
 // [5] sum |u - u_prev|^2, [6] sum |u|^2, [7] unused.  A thread takes
-// several nodes of its stride at a time (four on rD2Q9, two on the 3-D
-// lattices; half that in FP64) and issues all their population and
-// snapshot loads before using any or storing the new snapshot (loads
-// behind the snapshot stores, which the compiler cannot move past them,
-// made the check four times slower).  Per-node arithmetic is in the compute type CT,
-// and so are a thread's running sums over at most CHECK_RUN nodes; each
+// several nodes of its stride at a time (two; one on the 3-D lattices in
+// FP64) and issues all their population and snapshot loads before using
+// any or storing the new snapshot (loads behind the snapshot stores, which
+// the compiler cannot move past them, made the check four times slower).
+// Per-node arithmetic is in the compute type CT, and so are a thread's
+// running sums over at most CHECK_RUN nodes; each
 // run is then added into FP64 sums, and threads, warps and blocks are
 // reduced in FP64 in a fixed order.  (FP64 accumulation per node made the
 // check FP64-pipe bound on GB300: about 20 FP64 operations per node.)  The
@@ -96,13 +96,27 @@ __global__ void plane_kernel(ST* __restrict__ f, double* __restrict__ plane, int
 constexpr int CHECK_THREADS = 256;
 constexpr int CHECK_MAX_BLOCKS = 4096;
 constexpr int CHECK_RUN = 16;
+// Nodes per thread at a time and resident blocks per SM, per lattice size
+// (measured on the 8.4 M-node FP32 workloads: rD2Q9 two nodes and four
+// blocks 0.153 ms a check, four nodes and two blocks 0.197 ms; rD3Q27 two
+// and two 0.30 ms, two and four 0.59 ms).
+#ifndef RMRT_CHECK_BATCH_Q9
+#define RMRT_CHECK_BATCH_Q9 2
+#endif
+#ifndef RMRT_CHECK_MINB_Q9
+#define RMRT_CHECK_MINB_Q9 4
+#endif
 template <int LAT, typename CT>
 __host__ __device__ constexpr int check_batch() {
-  return sizeof(CT) == 8 ? (Lat<LAT>::Q <= 9 ? 2 : 1) : (Lat<LAT>::Q <= 9 ? 4 : 2);
+  return sizeof(CT) == 8 ? (Lat<LAT>::Q <= 9 ? 2 : 1) : (Lat<LAT>::Q <= 9 ? RMRT_CHECK_BATCH_Q9 : 2);
+}
+template <int LAT, typename CT>
+__host__ __device__ constexpr int check_min_blocks() {
+  return sizeof(CT) == 4 && Lat<LAT>::Q <= 9 ? RMRT_CHECK_MINB_Q9 : 2;
 }
 
 template <int LAT, typename ST, typename CT>
-__global__ void __launch_bounds__(CHECK_THREADS, 2) check_kernel(
+__global__ void __launch_bounds__(CHECK_THREADS, check_min_blocks<LAT, CT>()) check_kernel(
     const ST* __restrict__ fin, double* __restrict__ rho_out, double* __restrict__ u_out,
     double* __restrict__ uprev, int use_prev, int write_prev, double* __restrict__ partials,
     int* __restrict__ flags, const KParams<CT> p) {
