@@ -273,12 +273,17 @@ class SlabRun:
         self.solver.init_equilibrium(rho, u)            # this slab's part of the stacked field
 
     def step(self, n=1):
-        self.slab.step(n)
+        self.slab.step(n)              # the last step's exchange stays in flight (lands in the next step)
+
+    def finish(self):
+        self.slab.finish()
 
     def moments(self, rho=None, u=None):
+        self.finish()
         return self.solver.moments(rho, u)
 
     def last_check(self):
+        self.finish()
         return self.solver.last_check()
 
 
@@ -355,6 +360,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         solver.step(1)
+    solver.finish()
     torch.cuda.synchronize()
     # timed region: barrier + synchronize on both sides, events on the solver's stream
     if world > 1:
@@ -366,6 +372,8 @@ def run_ours(args):
         ev[0].record(stream)
         for i in range(args.steps):
             solver.step(1)
+            if i == args.steps - 1:
+                solver.finish()        # the last exchange lands inside the region
             ev[i + 1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -386,6 +394,7 @@ def run_ours(args):
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     c0.record(stream)
     solver.step(1)
+    solver.finish()                    # the check runs once the step's exchange has landed
     c1.record(stream)
     torch.cuda.synchronize()
     check_ms = max(0.0, c0.elapsed_time(c1) - kern_ms)

@@ -120,6 +120,7 @@ class Slab:
         self.check_every = int(p.get("check_every", 0))
         p["check_every"] = 0
         self.steps = 0
+        self._pending = None            # requests of the exchange in flight
         self.solver = B.Solver(lattice, local, spacing, dt, p, eq_kind, basis, storage, device=device)
         nbytes = B.rmrtlb_halo_bytes(self.solver.h)
         self.bufs = [torch.empty(nbytes, dtype=torch.uint8, device=device) for _ in range(4)]
@@ -133,6 +134,7 @@ class Slab:
 
     def init_equilibrium(self, rho, u=None):
         """f = f^eq of the global fields' slab part (numpy or CUDA tensors)."""
+        self.finish()
         lr = np.ascontiguousarray(self.local(rho)) if isinstance(rho, np.ndarray) else self.local(rho).contiguous()
         lu = None
         if u is not None:
@@ -155,9 +157,11 @@ class Slab:
         B.rmrtlb_halo_unpack(self.solver.h, from_below.data_ptr(), from_above.data_ptr())
 
     def step(self, n=1):
-        """n steps, each followed by the exchange of the crossing planes; the
-        exchange of one step runs beside the interior of the next, and the
-        last one is complete when this returns."""
+        """n steps, each followed by the exchange of the crossing planes.  The
+        exchange of one step runs beside the interior of the next, also
+        across calls: the last exchange is left in flight and lands at the
+        next step, or at finish() (which every method that reads or replaces
+        the state calls first)."""
         import torch
         if self.world == 1:
             for _ in range(n):
@@ -165,24 +169,34 @@ class Slab:
                 self.after_exchange()
             return
         h = self.solver.h
-        pending = None
         # the library's kernels run on the solver's stream, and the exchange is ordered against it
         with torch.cuda.stream(self.solver.stream):
             for _ in range(n):
                 B.rmrtlb_step_interior(h)
-                if pending is not None:
-                    finish_exchange(pending)
-                    self.unpack(self.bufs[2], self.bufs[3])
-                    self.after_exchange()
+                self._land()
                 B.rmrtlb_step_boundary(h)
                 up, down = self.pack()
-                pending = start_exchange(up, down, self.bufs[2], self.bufs[3], self.rank, self.world, self.group)
-            if pending is not None:
-                finish_exchange(pending)
-                self.unpack(self.bufs[2], self.bufs[3])
-                self.after_exchange()
+                self._pending = start_exchange(up, down, self.bufs[2], self.bufs[3], self.rank, self.world,
+                                               self.group)
+
+    def _land(self):
+        """Completes the exchange in flight: wait, unpack, count the step."""
+        if self._pending is not None:
+            finish_exchange(self._pending)
+            self._pending = None
+            self.unpack(self.bufs[2], self.bufs[3])
+            self.after_exchange()
+
+    def finish(self):
+        """Lands the exchange in flight (the slabs then hold the whole grid's
+        state); a no-op when none is."""
+        import torch
+        if self._pending is not None:
+            with torch.cuda.stream(self.solver.stream):
+                self._land()
 
     def moments(self, rho=None, u=None):
+        self.finish()
         return self.solver.moments(rho, u)
 
     def check(self):
@@ -190,6 +204,7 @@ class Slab:
         allreduce of the slabs' raw sums)."""
         import torch
         import torch.distributed as dist
+        self.finish()
         s = B.rmrtlb_check_sums(self.solver.h)
         if self.world == 1:
             return global_check([s])

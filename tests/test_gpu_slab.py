@@ -139,3 +139,81 @@ def test_interior_and_boundary_parts_equal_the_step(lattice, shape, kind, basis,
     B.rmrtlb_step_boundary(split.h)
     whole.step(1)
     np.testing.assert_array_equal(split.get_populations(), whole.get_populations())
+
+
+class _FakeRing:
+    """A stand-in for the process group of slab.start_exchange and
+    finish_exchange, for several Slab objects in one process on one GPU:
+    each rank's n-th posting joins round n, and the first wait on a round
+    whose ranks have all posted delivers every rank's buffers to its
+    neighbours (device copies), as the ring exchange would."""
+
+    def __init__(self, world):
+        self.world, self.rounds, self.count = world, {}, [0] * world
+
+    def start(self, send_up, send_down, recv_from_below, recv_from_above, rank, world, group=None):
+        n = self.count[rank]
+        self.count[rank] += 1
+        self.rounds.setdefault(n, {"posted": {}, "done": False})["posted"][rank] = (
+            send_up, send_down, recv_from_below, recv_from_above)
+        return [(self, n)]
+
+    @staticmethod
+    def finish(reqs):
+        import torch
+        for ring, n in reqs:
+            r = ring.rounds[n]
+            if r["done"]:
+                continue
+            assert len(r["posted"]) == ring.world, "a rank waited before every rank posted"
+            torch.cuda.synchronize()
+            for k, (_, _, below, above) in r["posted"].items():
+                below.copy_(r["posted"][(k - 1) % ring.world][0])
+                above.copy_(r["posted"][(k + 1) % ring.world][1])
+            torch.cuda.synchronize()
+            r["done"] = True
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("lattice,shape,spacing,kind,basis,storage", [
+    ("D2Q9", (48, 30, 1), (1.0, 0.6, 1.0), "nse", "raw", "f32"),
+    ("D3Q27", (16, 12, 15), (1.0, 0.8, 0.5), "nse", "central", "f16")])
+def test_slab_ranks_with_the_exchange_in_flight(monkeypatch, lattice, shape, spacing, kind, basis, storage, world):
+    """Slab objects of every rank of a ring driven in turn, one step per call,
+    so that each step's exchange is still in flight when the next call
+    starts (it lands after that call's interior part): after the last
+    finish() the slabs hold the single grid's run bit for bit, and their
+    reduced check equals the grid's."""
+    from paper_2206_00366_gb300 import slab as SL
+    from paper_2206_00366_gb300.rmrtlb import Solver
+    ring = _FakeRing(world)
+    monkeypatch.setattr(SL, "start_exchange", ring.start)
+    monkeypatch.setattr(SL, "finish_exchange", _FakeRing.finish)
+    params = dict(nu=0.02, nu_bulk=0.03, s_free=1.1, rho0=1.0, check_every=4)
+    nx, ny, nz = shape
+    d = 2 if lattice == "D2Q9" else 3
+    rho, u = W.random_fields((nz, ny, nx), d, seed=17, umax=0.03)
+    whole = Solver(lattice, shape, spacing, 1.0, params, kind, basis, storage)
+    whole.init_equilibrium(rho, u)
+    whole.step(9)
+    slabs = [SL.Slab(lattice, shape, spacing, 1.0, params, kind, basis, storage, rank=r, world=world)
+             for r in range(world)]
+    for s in slabs:
+        s.init_equilibrium(rho, u)
+    for _ in range(9):
+        for s in slabs:
+            s.step(1)
+    for s in slabs:
+        s.finish()
+    ax = SL.field_axis(d) + 1
+    got = np.concatenate([s.solver.get_populations() for s in slabs], axis=ax)
+    np.testing.assert_array_equal(got, whole.get_populations())
+    g = SL.global_check([B_sums(s) for s in slabs])
+    w = whole.last_check()
+    assert abs(g[0] - w[0]) <= 1e-12 * abs(w[0])
+    assert abs(g[5] - w[5]) <= 1e-9 * abs(w[5])
+
+
+def B_sums(s):
+    from paper_2206_00366_gb300 import rmrtlb as B
+    return B.rmrtlb_check_sums(s.solver.h)
