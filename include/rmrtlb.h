@@ -467,7 +467,8 @@ int rmrtlb_check_sums(rmrtlb_t solver, double out[8]);
  * rmrtlb_load_state: restores the state from src (host or device memory);
  * RMRTLB_EINVAL, with the solver unchanged, if the blob is not a state
  * blob, is shorter than its sections, or was saved from a solver with
- * another lattice, grid, storage, basis, kind or any other constant;
+ * another lattice, grid, storage, basis, kind, node_offset or any other
+ * constant;
  * synchronises the stream. */
 int rmrtlb_state_bytes(rmrtlb_t solver, size_t* bytes);
 int rmrtlb_save_state(rmrtlb_t solver, void* dst, size_t bytes);

@@ -646,7 +646,8 @@ struct StateHeader {
   unsigned version, header_bytes;
   int lattice, nx, ny, nz, storage, basis, eq_kind, has_prev;
   long long step;
-  int hist_fresh, slot_valid, slot_prev, pad_;
+  int hist_fresh, slot_valid, slot_prev;
+  unsigned node_base;                  // rmrtlb_params.node_offset: where the rounding bits are drawn
   long long slot_step;
   double fp[kFingerprint];
   unsigned long long pop_bytes, prev_bytes, hist_bytes, stats_bytes, flags_bytes;
@@ -711,6 +712,7 @@ int rmrtlb_save_state(rmrtlb_t s, void* dst, size_t bytes) {
   h.slot_valid = s->slot_valid[0] ? 1 : 0;
   h.slot_prev = s->slot_prev[0] ? 1 : 0;
   h.slot_step = s->slot_step[0];
+  h.node_base = s->kp32.node_base;
   fingerprint(s->k, h.fp);
   h.pop_bytes = pop; h.prev_bytes = prev; h.hist_bytes = hist; h.stats_bytes = stats; h.flags_bytes = flags;
   char* d = static_cast<char*>(dst);
@@ -742,7 +744,7 @@ int rmrtlb_load_state(rmrtlb_t s, const void* src, size_t bytes) {
   if (memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1 || h.header_bytes != sizeof(StateHeader) ||
       h.lattice != s->k.lat || h.nx != s->k.nx || h.ny != s->k.ny || h.nz != s->k.nz ||
       h.storage != s->k.storage || h.basis != s->k.central || h.eq_kind != s->k.kind ||
-      memcmp(h.fp, fp, sizeof(fp)) != 0 || h.step < 0)
+      memcmp(h.fp, fp, sizeof(fp)) != 0 || h.node_base != s->kp32.node_base || h.step < 0)
     return RMRTLB_EINVAL;
   // the section sizes this solver expects with the blob's snapshot flag
   const bool had_prev = s->has_prev;

@@ -6,7 +6,8 @@ stochastic rounding draws its bits from the restored step counter), a
 central basis, forcing, and the simplified NCDE with its B(t - dt)
 history; blobs in host and in device memory; a blob from a solver with
 other parameters, a truncated blob and a corrupted one are rejected and
-leave the solver as it was."""
+leave the solver as it was, as is one saved at another node offset (the
+random bits of the rounding would differ)."""
 import numpy as np
 import pytest
 
@@ -86,9 +87,14 @@ def test_load_rejects_foreign_truncated_and_corrupted_blobs():
     before = a.get_populations()
     other = make(lattice, shape, kind, basis, "f32", forced, nu=0.021)       # another viscosity
     other_storage = make(lattice, shape, kind, basis, "f64", forced)
+    from paper_2206_00366_gb300.rmrtlb import Solver
+    other_offset = Solver(lattice, shape, (1.0, 0.7, 1.0), 1.0,
+                          dict(nu=0.02, nu_bulk=0.03, s_free=1.1, rho0=1.0, diffusivity=0.02,
+                               adv=(0.04, -0.02, 0.01), check_every=5, node_offset=4096), kind, basis, "f32")
     bad = blob.copy()
     bad[0] ^= 0xFF
-    for target, b in ((other, blob), (other_storage, blob), (a, blob[: blob.size // 2].copy()), (a, bad)):
+    for target, b in ((other, blob), (other_storage, blob), (other_offset, blob), (a, blob[: blob.size // 2].copy()),
+                      (a, bad)):
         with pytest.raises(B.RmrtlbError) as ei:
             target.load_state(b)
         assert ei.value.status == B.EINVAL
