@@ -67,7 +67,7 @@ def gather(lat, B):
     return out
 
 
-def _worker(rank, world, port, lattice, steps, out):
+def _worker(rank, world, port, lattice, steps, out, pipelined=False):
     import torch
     import torch.distributed as dist
     sys.path.insert(0, ROOT)
@@ -83,31 +83,46 @@ def _worker(rank, world, port, lattice, steps, out):
         idx = [slice(None)] * a.ndim
         idx[ax - 1] = i
         return tuple(idx)
+    n = f.shape[ax]
     for _ in range(steps):
         B = collide_nodes(R, lat, m, S, f)                                # post-collision, at the node
         up = torch.from_numpy(np.stack([B[j][plane(B[j], -1)] for j in up_dirs]).copy())
         down = torch.from_numpy(np.stack([B[j][plane(B[j], 0)] for j in down_dirs]).copy())
         from_below, from_above = torch.empty_like(up), torch.empty_like(down)
-        SL.ring_exchange(up, down, from_below, from_above, rank, world)
+        reqs = SL.start_exchange(up, down, from_below, from_above, rank, world)
+        if pipelined:
+            # the interior planes 2 .. n - 3 pull only from planes 1 .. n - 2,
+            # none of which the exchange replaces: gather them while it is in flight
+            inner = np.take(gather(lat, B), np.arange(2, n - 2), axis=ax) if n >= 5 else None
+        SL.finish_exchange(reqs)
         for k, j in enumerate(up_dirs):
             B[j][plane(B[j], -1)] = from_below[k].numpy()
         for k, j in enumerate(down_dirs):
             B[j][plane(B[j], 0)] = from_above[k].numpy()
         f = gather(lat, B)
+        if pipelined and inner is not None:
+            idx = [slice(None)] * f.ndim
+            idx[ax] = slice(2, n - 2)
+            f[tuple(idx)] = inner
     out.put((rank, off, f))
     dist.barrier()
     dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("pipelined", [False, True])
 @pytest.mark.parametrize("world", [2, 3])
 @pytest.mark.parametrize("lattice", ["D2Q9", "D3Q27"])
-def test_slabs_reproduce_the_single_grid(lattice, world):
+def test_slabs_reproduce_the_single_grid(lattice, world, pipelined):
+    """pipelined: each rank gathers its interior planes 2 .. n - 3 while the
+    exchange is in flight (posted by start_exchange, waited by
+    finish_exchange), the split the GPU path makes with
+    rmrtlb_step_interior / rmrtlb_step_boundary."""
     import torch.multiprocessing as mp
     steps = 5
     ctx = mp.get_context("spawn")
     q = ctx.SimpleQueue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, lattice, steps, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, lattice, steps, q, pipelined)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
