@@ -459,30 +459,30 @@ int axis_planes(const rmrtlb_solver* s) { return s->k.d == 2 ? s->k.ny : s->k.nz
 cudaError_t launch_step_planes(rmrtlb_solver* s, int first, int count) {
   if (count <= 0) return cudaSuccess;
   LaunchArgs a = base_args(s, OP_STEP);
-    if (s->quads) {
-      const int quarter = s->k.nx / 4;
-      const int bx = block_x(quarter);
-      a.quads = 1;
-      a.block = dim3(bx, 1, 1);
-      a.grid = dim3((quarter + bx - 1) / bx, s->k.ny, s->k.nz);
-    } else if (s->pairs) {
-      const int half = s->k.nx / 2;
-      const int bx = block_x(half);
-      a.pairs = 1;
-      a.block = dim3(bx, 1, 1);
-      a.grid = dim3((half + bx - 1) / bx, s->k.ny, s->k.nz);
-    }
-    a.fin = pop_ptr(s, s->cur);
-    a.fout = pop_ptr(s, 1 - s->cur);
-    if (s->k.d == 2) a.grid.y = unsigned(count);
-    else a.grid.z = unsigned(count);
-    // seed of the stochastic rounding of 16-bit stores: a function of the
-    // step index only, so a run is reproducible
-    s->kp32.seed = unsigned((unsigned long long)s->step * 0x9E3779B97F4A7C15ull >> 32);
-    s->kp64.plane0 = s->kp32.plane0 = first;
-    const cudaError_t e = launch(s, a);   // the parameters are copied at launch
-    s->kp64.plane0 = s->kp32.plane0 = 0;
-    return e;
+  if (s->quads) {
+    const int quarter = s->k.nx / 4;
+    const int bx = block_x(quarter);
+    a.quads = 1;
+    a.block = dim3(bx, 1, 1);
+    a.grid = dim3((quarter + bx - 1) / bx, s->k.ny, s->k.nz);
+  } else if (s->pairs) {
+    const int half = s->k.nx / 2;
+    const int bx = block_x(half);
+    a.pairs = 1;
+    a.block = dim3(bx, 1, 1);
+    a.grid = dim3((half + bx - 1) / bx, s->k.ny, s->k.nz);
+  }
+  a.fin = pop_ptr(s, s->cur);
+  a.fout = pop_ptr(s, 1 - s->cur);
+  if (s->k.d == 2) a.grid.y = unsigned(count);
+  else a.grid.z = unsigned(count);
+  // seed of the stochastic rounding of 16-bit stores: a function of the
+  // step index only, so a run is reproducible
+  s->kp32.seed = unsigned((unsigned long long)s->step * 0x9E3779B97F4A7C15ull >> 32);
+  s->kp64.plane0 = s->kp32.plane0 = first;
+  const cudaError_t e = launch(s, a);   // the parameters are copied at launch
+  s->kp64.plane0 = s->kp32.plane0 = 0;
+  return e;
 }
 
 // Completes a step whose planes have all been stepped: swaps the lattices,
