@@ -278,7 +278,8 @@ def time_to_steady(dom, re, net=None, coarse=None, tol=1e-6, max_steps=2_000_000
 
 def main(argv=None):
     """Train on solver-generated steady states and save the weights:
-    python -m paper_2206_00366_gb300.warmstart --states 2000 --epochs 20 --out W.npz"""
+    python -m paper_2206_00366_gb300.warmstart --states 2000 --epochs 30 --out W.npz
+    (the arguments the committed weights were trained with)"""
     import argparse
 
     import torch
@@ -287,7 +288,7 @@ def main(argv=None):
     ap.add_argument("--shape", type=int, nargs=3, default=(32, 64, 64), help="nz ny nx of the training cavities")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-steps", type=int, default=60000)
-    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=5)
